@@ -1,0 +1,291 @@
+"""Deterministic reference solutions that pin the Monte Carlo oracle.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/oracle.py``).
+
+* ``slab_solution``: the gray slab between black walls (the steady limit of
+  Eq. 1 with isotropic scattering, Eq. 4 estimators) is the classical
+  conservative-scattering slab of radiative transfer.  With optical
+  coordinate tau = x / Lambda and thickness tau_L = L / Lambda, the
+  non-dimensional emissive function phi = (T - T_cold) / (T_hot - T_cold)
+  obeys
+
+      phi(tau) = 1/2 [ E2(tau) + int_0^tau_L phi(t) E1(|tau - t|) dt ]
+
+  and the non-dimensional heat flux is Psi = 1 - 2 int_0^tau_L phi E2 dt.
+  It is solved here by product-integration collocation with piecewise-linear
+  phi (exact panel integrals through E2, E3, E4) and Richardson
+  extrapolation in the panel count.
+* ``fuchs_sondheimer``: in-plane conductivity suppression of a film with
+  diffuse walls (the analytic thin-film solution, last section of the paper),
+  S(delta) = 1 - 3/(2 delta) int_1^inf (t^-3 - t^-5)(1 - exp(-delta t)) dt,
+  delta = L / Lambda, evaluated in closed form through E3 and E5 and
+  independently by quadrature of the first-flight integral over directions.
+* ``mode_table``: per-mode (omega, v, tau, C) of the isotropic quadratic
+  dispersion, written with numpy independently of the C oracle.
+* ``kappa_bulk`` and ``kappa_film``: (1/3) sum_b C_b v_b^2 tau_b [S(L/Lambda_b)].
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import integrate, special
+
+HBAR = 1.054571817e-34
+KB = 1.380649e-23
+
+
+def En(n, x):
+    return special.expn(n, np.asarray(x, dtype=np.float64))
+
+
+# --------------------------------------------------------------------------
+# Gray slab
+# --------------------------------------------------------------------------
+def _F0(s):  # antiderivative of E1
+    return -En(2, s)
+
+
+def _F1(s):  # antiderivative of s E1(s)
+    return -s * En(2, s) - En(3, s)
+
+
+def _lin_E1(a, b, alpha, beta, ti):
+    """int_a^b (alpha + beta t) E1(|ti - t|) dt for a <= b (vectorised in ti)."""
+    ti = np.asarray(ti, dtype=np.float64)
+    out = np.zeros_like(ti)
+    c = alpha + beta * ti
+    # part of [a, b] right of ti
+    ra = np.maximum(a, ti)
+    rb = np.maximum(b, ti)
+    sa, sb = ra - ti, rb - ti
+    out += c * (_F0(sb) - _F0(sa)) + beta * (_F1(sb) - _F1(sa))
+    # part of [a, b] left of ti
+    la = np.minimum(a, ti)
+    lb = np.minimum(b, ti)
+    sa, sb = ti - la, ti - lb
+    out += c * (_F0(sa) - _F0(sb)) - beta * (_F1(sa) - _F1(sb))
+    return out
+
+
+def _solve_slab(tau_L, M):
+    h = tau_L / M
+    nodes = np.linspace(0.0, tau_L, M + 1)
+    W = np.zeros((M + 1, M + 1))
+    for j in range(M + 1):
+        if j > 0:  # rising part on [t_{j-1}, t_j]: (t - t_{j-1}) / h
+            a, b = nodes[j - 1], nodes[j]
+            W[:, j] += _lin_E1(a, b, -a / h, 1.0 / h, nodes)
+        if j < M:  # falling part on [t_j, t_{j+1}]: (t_{j+1} - t) / h
+            a, b = nodes[j], nodes[j + 1]
+            W[:, j] += _lin_E1(a, b, b / h, -1.0 / h, nodes)
+    A = np.eye(M + 1) - 0.5 * W
+    rhs = 0.5 * En(2, nodes)
+    phi = np.linalg.solve(A, rhs)
+    return nodes, phi
+
+
+def _int_lin_E2(a, b, alpha, beta, shift=0.0, sign=1.0):
+    """int_a^b (alpha + beta t) E2(sign (t - shift)) dt with sign (t - shift) >= 0."""
+    if sign > 0:
+        sa, sb = a - shift, b - shift
+        G0 = lambda s: -En(3, s)
+        G1 = lambda s: -s * En(3, s) - En(4, s)
+        c = alpha + beta * shift
+        return c * (G0(sb) - G0(sa)) + beta * (G1(sb) - G1(sa))
+    sa, sb = shift - a, shift - b  # sa >= sb
+    G0 = lambda s: -En(3, s)
+    G1 = lambda s: -s * En(3, s) - En(4, s)
+    c = alpha + beta * shift
+    return c * (G0(sa) - G0(sb)) - beta * (G1(sa) - G1(sb))
+
+
+def _flux_at(nodes, phi, tau):
+    """Non-dimensional flux q*(tau) = 2 E3(tau) + 2 int_0^tau phi E2(tau-t) dt
+    - 2 int_tau^tau_L phi E2(t - tau) dt (cold wall phi = 0)."""
+    tau_L = nodes[-1]
+    q = 2.0 * float(En(3, tau))
+    for j in range(len(nodes) - 1):
+        a, b = nodes[j], nodes[j + 1]
+        h = b - a
+        beta = (phi[j + 1] - phi[j]) / h
+        alpha = phi[j] - beta * a
+        if b <= tau:
+            q += 2.0 * float(_int_lin_E2(a, b, alpha, beta, shift=tau, sign=-1.0))
+        elif a >= tau:
+            q -= 2.0 * float(_int_lin_E2(a, b, alpha, beta, shift=tau, sign=+1.0))
+        else:
+            q += 2.0 * float(_int_lin_E2(a, tau, alpha, beta, shift=tau, sign=-1.0))
+            q -= 2.0 * float(_int_lin_E2(tau, b, alpha, beta, shift=tau, sign=+1.0))
+    return q
+
+
+def _psi(nodes, phi):
+    return _flux_at(nodes, phi, 0.0)
+
+
+def _bin_means(nodes, phi, n_bins):
+    """Bin averages of the piecewise-linear phi over n_bins equal bins."""
+    tau_L = nodes[-1]
+    edges = np.linspace(0.0, tau_L, n_bins + 1)
+    out = np.zeros(n_bins)
+    for k in range(n_bins):
+        xs = np.linspace(edges[k], edges[k + 1], 2001)
+        out[k] = np.trapezoid(np.interp(xs, nodes, phi), xs) / (edges[k + 1] - edges[k])
+    return out
+
+
+def slab_solution(tau_L, n_bins=50, M=400, richardson=True):
+    """Psi and the bin-averaged phi of the gray slab of optical thickness tau_L.
+
+    Returns dict(psi, phi_bins, T_bins) with T_bins = 2 phi - 1, the
+    temperature in units of the wall excess (walls at T_eq +/- dT)."""
+    M1 = max(M - M % n_bins, n_bins)
+    n1, p1 = _solve_slab(tau_L, M1)
+    psi1 = _psi(n1, p1)
+    b1 = _bin_means(n1, p1, n_bins)
+    if not richardson:
+        return {"psi": psi1, "phi_bins": b1, "T_bins": 2 * b1 - 1, "nodes": n1, "phi": p1}
+    n2, p2 = _solve_slab(tau_L, 2 * M1)
+    psi2 = _psi(n2, p2)
+    b2 = _bin_means(n2, p2, n_bins)
+    psi = (4 * psi2 - psi1) / 3
+    b = (4 * b2 - b1) / 3
+    return {"psi": psi, "phi_bins": b, "T_bins": 2 * b - 1, "nodes": n2, "phi": p2,
+            "psi_coarse": psi1, "psi_fine": psi2}
+
+
+def slab_flux_profile(tau_L, taus, M=400):
+    """q*(tau) at interior points; constant (= Psi) for the exact solution."""
+    nodes, phi = _solve_slab(tau_L, M)
+    return np.array([_flux_at(nodes, phi, t) for t in taus])
+
+
+# --------------------------------------------------------------------------
+# Thin film with diffuse walls
+# --------------------------------------------------------------------------
+def fuchs_sondheimer(delta):
+    """S(delta) in closed form: int_1^inf t^-n exp(-delta t) dt = E_n(delta)."""
+    d = np.asarray(delta, dtype=np.float64)
+    return 1.0 - 1.5 / d * (0.25 - En(3, d) + En(5, d))
+
+
+def fuchs_sondheimer_quadrature(delta):
+    """S(delta) from the first-flight integral of a particle emitted uniformly
+    across the film with a |cos| law about the in-plane axis z:
+    S = 3/2 int_0^1 (1 - mu^2) g(mu) dmu, mu = |Omega_x|,
+    g(mu) = 1 - (mu/delta)(1 - exp(-delta/mu))."""
+    def g(mu):
+        if mu <= 0.0:
+            return 1.0
+        return 1.0 - (mu / delta) * (-math.expm1(-delta / mu))
+    val, _ = integrate.quad(lambda mu: (1 - mu * mu) * g(mu), 0.0, 1.0, limit=400, epsabs=1e-14)
+    return 1.5 * val
+
+
+def mode_table(mat):
+    """(omega, v, tau, C) per mode from a workload material dict (numpy)."""
+    T = mat["T_eq"]
+    if mat["kind"] == "gray":
+        return (np.zeros(1), np.array([mat["v"]]), np.array([mat["tau"]]), np.array([mat["C"]]))
+    om, vs, ts, cs = [], [], [], []
+    for br in mat["branches"]:
+        c1, c2, g = br["c1"], br["c2"], br["degeneracy"]
+        kmax = 2 * math.pi / mat["a_lattice"]
+        if c2 < 0:
+            kmax = min(kmax, c1 / (2 * abs(c2)))
+        wmax = c1 * kmax + c2 * kmax ** 2
+        nb = mat["n_bins"]
+        dw = wmax / nb
+        w = (np.arange(nb) + 0.5) * dw
+        v = np.sqrt(c1 * c1 + 4 * c2 * w)
+        k = 2 * w / (c1 + v)
+        dos = k * k / (2 * math.pi ** 2 * v)
+        x = HBAR * w / (KB * T)
+        dfdT = x * np.exp(x) / (np.expm1(x) ** 2 * T)
+        om.append(w)
+        vs.append(v)
+        cs.append(g * dos * HBAR * w * dfdT * dw)
+        ts.append(1.0 / (mat["A"] * w ** 4 + mat["B"] * w * w * T * math.exp(-mat["C"] / T)))
+    return tuple(np.concatenate(a) for a in (om, vs, ts, cs))
+
+
+def kappa_bulk(mat):
+    _, v, tau, C = mode_table(mat)
+    return float(np.sum(C * v * v * tau) / 3.0)
+
+
+def kappa_film(mat, L):
+    _, v, tau, C = mode_table(mat)
+    lam = v * tau
+    return float(np.sum(C * v * v * tau / 3.0 * fuchs_sondheimer(L / lam)))
+
+
+# --------------------------------------------------------------------------
+# Multi-mode slab between black walls: collision-density integral equation
+# --------------------------------------------------------------------------
+def slab_multimode_psi(Lambda, q_emit, p_scat, L, M=200, richardson=True):
+    """Psi of a black-walled slab for a non-gray medium.
+
+    Particles leave the hot wall with mode probabilities ``q_emit`` (the wall
+    source weights C_b v_b) and a cosine law; every relaxation event redraws
+    the mode with probabilities ``p_scat`` (normalised Eq. 2, C_b / tau_b) and
+    an isotropic direction.  With equal and opposite wall excesses Psi equals
+    the probability that a wall particle is absorbed by the opposite wall.
+
+    The collision density F(x) obeys F = f0 + K F with
+      f0(x)   = sum_b q_b (2/Lambda_b) E2(x/Lambda_b)         (first collisions)
+      K(x,x') = sum_b p_b (1/(2 Lambda_b)) E1(|x-x'|/Lambda_b)  (isotropic re-emission)
+    and Psi = sum_b q_b 2 E3(L/Lambda_b) + int F(x) sum_b p_b E2((L-x)/Lambda_b)/2 dx.
+    Solved with piecewise-linear F (exact panel integrals), Richardson in M.
+    This is a different formulation from ``slab_solution`` (collision density
+    instead of emissive power), so for a gray medium the two cross-check."""
+    Lam = np.asarray(Lambda, dtype=np.float64)
+    q = np.asarray(q_emit, dtype=np.float64) / np.sum(q_emit)
+    p = np.asarray(p_scat, dtype=np.float64) / np.sum(p_scat)
+
+    def solve(Mn):
+        h = L / Mn
+        nodes = np.linspace(0.0, L, Mn + 1)
+        K = np.zeros((Mn + 1, Mn + 1))
+        for lam, pb in zip(Lam, p):
+            if pb == 0.0:
+                continue
+            t = nodes / lam
+            Wb = np.zeros_like(K)
+            for j in range(Mn + 1):
+                if j > 0:
+                    a, b = t[j - 1], t[j]
+                    Wb[:, j] += _lin_E1(a, b, -a / (b - a), 1.0 / (b - a), t)
+                if j < Mn:
+                    a, b = t[j], t[j + 1]
+                    Wb[:, j] += _lin_E1(a, b, b / (b - a), -1.0 / (b - a), t)
+            K += pb * 0.5 * Wb  # dx'/(2 Lambda) = dtau'/2
+        f0 = np.zeros(Mn + 1)
+        for lam, qb in zip(Lam, q):
+            f0 += qb * 2.0 / lam * En(2, nodes / lam)
+        F = np.linalg.solve(np.eye(Mn + 1) - K, f0)
+        # escape-to-far-wall integral, exact per panel for linear F:
+        # int_a^b F(x) E2((L-x)/lam)/2 dx, with s = (L-x)/lam
+        psi = float(np.sum(q * 2.0 * En(3, L / Lam)))
+        for lam, pb in zip(Lam, p):
+            if pb == 0.0:
+                continue
+            acc = 0.0
+            for j in range(Mn):
+                xa, xb = nodes[j], nodes[j + 1]
+                beta = (F[j + 1] - F[j]) / h
+                alpha = F[j] - beta * xa
+                sa, sb = (L - xa) / lam, (L - xb) / lam  # sa > sb
+                # x = L - lam s, dx = -lam ds: int_{sb}^{sa} (alpha + beta (L - lam s)) E2(s) lam ds
+                G0 = lambda s: -En(3, s)
+                G1 = lambda s: -s * En(3, s) - En(4, s)
+                acc += lam * ((alpha + beta * L) * (G0(sa) - G0(sb)) - beta * lam * (G1(sa) - G1(sb)))
+            psi += pb * 0.5 * acc
+        return psi
+
+    p1 = solve(M)
+    if not richardson:
+        return p1
+    p2 = solve(2 * M)
+    return (4 * p2 - p1) / 3

@@ -1,0 +1,110 @@
+"""Oracle pins for the periodic porous film and the transient estimator.
+
+* ray / boundary distances against brute-force marching with bisection;
+* a porous film with zero pore radius is a plain film: its conductivity
+  must equal the Fuchs-Sondheimer value, so the periodic unit-cell faces
+  (which end segments and re-insert particles) change nothing;
+* pores only lower the conductivity (kappa_eff below the pore-free film);
+* Eq. 3 transient counts conserve energy exactly: every adiabatic-walled
+  particle alive at a sample time sits in exactly one grid cell.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _inside(prob, pos):
+    g = prob["geometry"]
+    x, y, z = pos
+    if not (0.0 <= x <= g["L"] and 0.0 <= y <= g["pitch"] and 0.0 <= z <= g["pitch"]):
+        return False
+    dy, dz = y - 0.5 * g["pitch"], z - 0.5 * g["pitch"]
+    return dy * dy + dz * dz >= g["radius"] ** 2
+
+
+def _march(prob, pos, d, step):
+    """Distance to the first exit of the solid unit cell, by marching + bisection."""
+    t = 0.0
+    while _inside(prob, pos + (t + step) * d):
+        t += step
+        if t > 10.0 * prob["geometry"]["L"]:
+            return np.inf
+    lo, hi = t, t + step
+    for _ in range(80):
+        mid = 0.5 * (lo + hi)
+        if _inside(prob, pos + mid * d):
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_first_boundary_against_marching(oracle):
+    prob = W.porous_film(n_particles=1)
+    g = prob["geometry"]
+    rng = np.random.default_rng(3)
+    n_done = 0
+    kinds = set()
+    while n_done < 300:
+        pos = np.array([rng.uniform(0, g["L"]), rng.uniform(0, g["pitch"]), rng.uniform(0, g["pitch"])])
+        if not _inside(prob, pos):
+            continue
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        t, kind = oracle.first_boundary(prob, pos, d)
+        ref = _march(prob, pos, d, step=g["pitch"] / 200)
+        assert t == pytest.approx(ref, rel=1e-9, abs=1e-9 * g["pitch"]), (pos, d, kind)
+        kinds.add(kind)
+        n_done += 1
+    assert kinds == {1, 2, 3, 4, 5, 6, 7}
+
+
+def test_zero_radius_porous_film_equals_film(oracle, analytic):
+    L = 300e-9
+    pin = analytic.kappa_film(W.SILICON_LIKE, L)
+    p = W.porous_film(n_particles=2_000_000, radius=0.0, precision="fp64", max_events=1 << 16)
+    r = oracle.run(p)
+    assert r["periodic"] > 0
+    assert abs(r["kappa"] - pin) < 4.0 * r["kappa_se"], (r["kappa"], pin, r["kappa_se"])
+
+
+def test_pores_lower_conductivity(oracle, analytic):
+    p = W.porous_film(n_particles=400_000, precision="fp64")
+    r = oracle.run(p)
+    film = analytic.kappa_film(W.SILICON_LIKE, 300e-9)
+    porosity = np.pi * 0.3 ** 2
+    assert 0.0 < r["kappa"] + 4 * r["kappa_se"]
+    assert r["kappa"] + 4 * r["kappa_se"] < film * (1 - porosity)
+    assert r["kappa_solid"] == pytest.approx(r["kappa"] / (1 - porosity), rel=1e-12)
+    assert r["wall_hits"] > 0 and r["periodic"] > 0
+
+
+def test_pulse_emission_in_solid(oracle):
+    p = W.porous_pulse(n_particles=20_000, grid=(4, 8, 8), n_samples=10)
+    st, _ = oracle.emit(p, 0, 20_000)
+    g = p["geometry"]
+    assert np.all(st[:, 0] == 1)
+    assert np.all(st[:, 1] == g["L"]) and np.all(st[:, 4] < 0)
+    yl = np.mod(st[:, 2], g["pitch"]) - 0.5 * g["pitch"]
+    zl = np.mod(st[:, 3], g["pitch"]) - 0.5 * g["pitch"]
+    assert np.all(yl * yl + zl * zl >= g["radius"] ** 2)
+    assert np.all(st[:, 7] >= 0)
+    t0 = st[:, 7]
+    src = p["source"]
+    assert abs(np.mean(t0) - src["t_center"]) < 5 * src["sigma_t"] / np.sqrt(t0.size) + 1e-13
+
+
+def test_transient_energy_conservation(oracle):
+    # all walls adiabatic, all particles positive: at every sample time the grid
+    # holds exactly the particles already emitted (step VI only ends them at t_final)
+    n = 3000
+    p = W.porous_pulse(n_particles=n, grid=(4, 12, 12), n_samples=40, sample_dt=25e-12, t_final=1e-9)
+    r = oracle.run(p, record_particles=True)
+    grid = r["grid"]
+    rec = r["particles_rec"]
+    ts = (np.arange(40) + 0.5) * 25e-12
+    emitted = np.array([(rec["t0"] <= t).sum() for t in ts])
+    assert np.array_equal(grid.reshape(40, -1).sum(axis=1), emitted)
+    assert np.all(grid >= 0)
+    assert np.all(rec["fate"] == 3)
