@@ -1,0 +1,271 @@
+/*
+ * le_mc.h -- C ABI of the GB300 (sm_103a) trajectory tracer for the
+ * linearized energy-based deviational Monte Carlo method (Peraud and
+ * Hadjiconstantinou, "An alternative approach to efficient simulation of
+ * micro/nanoscale phonon transport", arXiv:1206.3316).
+ *
+ * Under the linearized collision operator (Eq. 2) deviational particles do
+ * not interact, so each trajectory is traced alone from emission to
+ * termination (trajectory algorithm, steps I-VI) and contributes to
+ * path-integrated (Eq. 4) or time-sampled (Eq. 3) estimators.  This library
+ * runs that loop on one GPU.
+ *
+ * Conventions for every function below:
+ *  - All functions return an le_mc_status; none aborts, exits or prints.
+ *    A failed call leaves a thread-local message in le_mc_last_error().
+ *  - Pointers are HOST pointers unless a comment says "device pointer".
+ *    Descriptors are read during the call only; the caller keeps ownership.
+ *  - Handles are opaque and owned by the caller until the matching destroy.
+ *    Materials and geometries are immutable after creation and may be used
+ *    by any number of runs, including concurrent ones; the library keeps them
+ *    alive (reference count) until the last run using them is destroyed.
+ *  - Device memory is allocated by the library from the stream-ordered pool
+ *    of the current device; results are copied into caller-owned buffers.
+ *  - `stream` arguments are cudaStream_t values passed as void* (NULL = the
+ *    legacy default stream).
+ *  - SI units (m, s, K, J, W) throughout; the gray material may be
+ *    non-dimensional as long as it is used consistently.
+ */
+#ifndef LE_MC_H
+#define LE_MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define LE_MC_API __attribute__((visibility("default")))
+#else
+#define LE_MC_API
+#endif
+
+#define LE_MC_ABI_VERSION 1
+#define LE_MC_MAX_BRANCHES 4
+#define LE_MC_MAX_MODES 4096        /* mode tables live in shared memory       */
+#define LE_MC_MAX_BINS_X 256        /* slab profile bins                       */
+#define LE_MC_MAX_BATCH 64          /* batch groups for profile error bars     */
+#define LE_MC_MAX_HJ 128            /* per-scattering-index flux tallies       */
+
+typedef enum {
+    LE_MC_OK = 0,
+    LE_MC_ERR_INVALID = 1, /* a descriptor field or argument is out of range     */
+    LE_MC_ERR_NOMEM = 2,   /* a host or device allocation failed                 */
+    LE_MC_ERR_CUDA = 3,    /* a CUDA runtime call failed                         */
+    LE_MC_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up                 */
+    LE_MC_ERR_BUDGET = 5,  /* a device-side bound was hit that invalidates output */
+    LE_MC_ERR_STATE = 6,   /* the handle is unusable (earlier failure) or busy    */
+    LE_MC_ERR_NODEV = 7    /* no usable CUDA device                              */
+} le_mc_status;
+
+/* ---- material (Eq. 1 ingredients at the control temperature T_eq) ---------
+ * Per mode b (branch p, frequency bin): C_b = g_p D_p(w_b) hbar w_b
+ * d f_BE/dT(w_b, T_eq) dw (J m^-3 K^-1), group velocity v_b, relaxation time
+ * tau_b = tau(w_b, p, T_eq) (material properties at T_0, as in the linear
+ * regime paragraph after Eq. 5), mean free path Lambda_b = v_b tau_b.       */
+enum { LE_MC_MAT_GRAY = 0, LE_MC_MAT_QUADRATIC = 1, LE_MC_MAT_TABULATED = 2 };
+
+typedef struct {
+    int32_t kind;          /* LE_MC_MAT_*                                        */
+    int32_t n_branch;      /* QUADRATIC: number of branches, 1..4                */
+    int32_t n_bins;        /* QUADRATIC: equal-width frequency bins per branch   */
+    int32_t n_modes;       /* TABULATED: number of modes, 1..LE_MC_MAX_MODES     */
+    double T_eq;           /* control temperature [K] (> 0)                      */
+    double gray_v, gray_tau, gray_C; /* GRAY: one mode                           */
+    /* QUADRATIC: omega(k) = c1 k + c2 k^2 per branch, degeneracy g_p, k up to
+     * min(2 pi / a_lattice, c1 / (2|c2|)) (the group velocity stays > 0),
+     * 1/tau = A omega^4 + B omega^2 T exp(-C_exp / T) for every branch.         */
+    double c1[LE_MC_MAX_BRANCHES], c2[LE_MC_MAX_BRANCHES], degeneracy[LE_MC_MAX_BRANCHES];
+    double a_lattice, A, B, C_exp;
+    /* TABULATED: host arrays of n_modes values (copied during the call)        */
+    const double* tab_v;
+    const double* tab_tau;
+    const double* tab_C;
+} le_mc_material_desc;
+
+typedef struct le_mc_material_s* le_mc_material;
+
+/* Builds the per-mode tables in FP64 on the host, the alias tables of the
+ * emission law (weights C_b v_b: boundary source after the algorithm, Eq. 6)
+ * and of the post-scattering law (weights C_b / tau_b: normalised Eq. 2), and
+ * uploads them to the current device.  Synchronous.
+ * Errors: LE_MC_ERR_INVALID (bad field, zero total weight, > MAX_MODES),
+ * LE_MC_ERR_NOMEM, LE_MC_ERR_CUDA, LE_MC_ERR_NODEV. */
+LE_MC_API le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_material* out);
+LE_MC_API le_mc_status le_mc_destroy_material(le_mc_material m);
+
+/* Host-only: the FP64 mode table the material would hold, without touching a
+ * GPU.  Arrays of `capacity` doubles (NULL to query); *n_modes receives the
+ * count.  Errors: LE_MC_ERR_INVALID. */
+LE_MC_API le_mc_status le_mc_material_table(const le_mc_material_desc* desc, double* omega, double* v,
+                                  double* tau, double* C, int32_t capacity, int32_t* n_modes);
+
+/* Host-only: Vose alias table of n weights (n <= LE_MC_MAX_MODES) in the
+ * library's sampling format: a draw of a uniform 32-bit word r picks column
+ * j = floor(r n / 2^32) and returns j if (r n mod 2^32) < threshold[j], else
+ * alias[j].  Errors: LE_MC_ERR_INVALID (n out of range, negative or all-zero
+ * weights). */
+LE_MC_API le_mc_status le_mc_alias_table(const double* weights, int32_t n, uint32_t* threshold, uint32_t* alias);
+
+/* ---- geometry (step III boundary search, step IVa wall response) --------- */
+enum { LE_MC_GEOM_PLANES = 0, LE_MC_GEOM_BULK = 1, LE_MC_GEOM_POROUS = 2 };
+enum { LE_MC_WALL_BLACK = 0, LE_MC_WALL_DIFFUSE = 1, LE_MC_WALL_SPECULAR = 2 };
+
+typedef struct {
+    int32_t kind;      /* PLANES: walls at x = 0 and x = L, unbounded in y, z (slab, film)
+                        * BULK:   no boundaries
+                        * POROUS: PLANES plus cylindrical pores along x centred in
+                        *         each pitch x pitch unit cell of the (y, z) plane;
+                        *         the domain is cells_y x cells_z unit cells,
+                        *         periodic in y and z (particles crossing a face are
+                        *         re-inserted on the opposite face)               */
+    int32_t wall_lo;   /* wall type at x = 0 (LE_MC_WALL_*)                     */
+    int32_t wall_hi;   /* wall type at x = L                                   */
+    int32_t pore_wall; /* POROUS: pore surface type (DIFFUSE or SPECULAR)       */
+    double L;          /* thickness along x [m] (> 0 unless BULK)               */
+    double pitch;      /* POROUS: lattice pitch [m]                            */
+    double radius;     /* POROUS: pore radius [m], 0 <= 2 radius < pitch         */
+    int32_t cells_y, cells_z; /* POROUS: periodic domain in unit cells (>= 1)   */
+} le_mc_geometry_desc;
+
+typedef struct le_mc_geometry_s* le_mc_geometry;
+
+/* Validates and stores the geometry.  Errors: LE_MC_ERR_INVALID. */
+LE_MC_API le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le_mc_geometry* out);
+LE_MC_API le_mc_status le_mc_destroy_geometry(le_mc_geometry g);
+
+/* ---- run: sources (step I), termination (step VI), estimators (step V) ---- */
+enum { LE_MC_SRC_WALLS = 0, LE_MC_SRC_GRADIENT = 1, LE_MC_SRC_PULSE = 2 };
+enum { LE_MC_PREC_FP64 = 0, LE_MC_PREC_FP32 = 1 };
+
+typedef struct {
+    int32_t source;    /* WALLS (PLANES only): isothermal walls at T_eq + dT_lo
+                        *   (x = 0) and T_eq + dT_hi (x = L) emit V_g cos C |dT|
+                        *   into the domain; black walls absorb (boundary source
+                        *   after the algorithm).
+                        * GRADIENT: the volumetric source of Eq. 5 / Eq. 6 for a
+                        *   uniform dT/dz, equal numbers of each sign.
+                        * PULSE (POROUS only): surface heat pulse on x = L,
+                        *   Gaussian in (y, z) and in time, all signs positive.   */
+    int32_t precision; /* FP64: every step in FP64.  FP32: trajectory geometry and
+                        *   times in FP32, per-particle sums carried compensated,
+                        *   tally accumulation in FP64.                          */
+    double dT_lo, dT_hi;            /* WALLS [K]                                  */
+    double dTdz;                    /* GRADIENT [K/m], nonzero                    */
+    double pulse_sigma_x;           /* PULSE: lateral standard deviation [m]     */
+    double pulse_sigma_t;           /* PULSE: temporal standard deviation [s]    */
+    double pulse_t_center;          /* PULSE: centre time [s] (times < 0 redrawn) */
+    double pulse_energy;            /* PULSE: deviational energy [J]             */
+    double pulse_y0, pulse_z0;      /* PULSE: centre in the periodic domain [m]  */
+    uint64_t n_particles;           /* N, 0 .. 2^32 - 1 (2^31 - 1 for PULSE)     */
+    uint64_t seed;                  /* Philox4x32-10 key                         */
+    uint32_t instance_id;           /* 4th counter word: independent streams     */
+    uint32_t max_scatter;           /* terminate at this scattering event (0 = none) */
+    uint32_t max_events;            /* terminate after this many segments (>= 1) */
+    int32_t n_bins_x;               /* WALLS: T(x), q(x) profile bins (0 = off)   */
+    int32_t n_batch;                /* profile batch groups (particle id mod n_batch) */
+    int32_t grid_nx, grid_ny, grid_nz; /* PULSE: counting grid over L x domain   */
+    int32_t n_samples;              /* PULSE: sample times (k + 1/2) sample_dt    */
+    double t_final;                 /* PULSE: end of the simulation [s]          */
+    double sample_dt;               /* PULSE: sample spacing [s]                 */
+    int32_t n_hj;                   /* flux split by scattering index j (0 = off) */
+    int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
+    int32_t blocks_per_sm;          /* launch shape (0 = library default)        */
+    int32_t threads_per_block;      /* 0 = default; multiple of 32, <= 512       */
+} le_mc_run_desc;
+
+typedef struct le_mc_run_s* le_mc_run_handle;
+
+/* Enqueues one simulation on `stream` and returns at once: device tallies are
+ * allocated and zeroed, the persistent trace kernel (steps I-VI with the
+ * estimators of step V) is launched, and the run's completion is recorded.
+ * The particle stream is fixed by (seed, instance_id, particle id), so the
+ * tallies do not depend on the launch shape up to FP64 summation order.
+ * Errors: LE_MC_ERR_INVALID (descriptor out of range or inconsistent with the
+ * geometry), LE_MC_ERR_NOMEM, LE_MC_ERR_CUDA. */
+LE_MC_API le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc* desc,
+                       void* stream, le_mc_run_handle* out);
+
+/* Blocks until the run's device work is complete. */
+LE_MC_API le_mc_status le_mc_wait(le_mc_run_handle h);
+
+typedef struct {
+    double P_total;     /* source power: W per m^2 of wall (WALLS), W over the solid
+                         * part of the reference volume (GRADIENT)                */
+    double E_eff_dot;   /* steady: effective deviational power per particle (Eq. 4) */
+    double E_eff;       /* PULSE: deviational energy per particle (Eq. 3)          */
+    double C_tot;       /* sum_b C_b                                               */
+    double sum_sL, sum_sL2; /* sum over particles of s L and (s L)^2, L the total
+                             * algebraic length along the flux axis (x for WALLS,
+                             * z otherwise)                                        */
+    double flux, flux_se;   /* heat flux along that axis [W/m^2] and its std error  */
+    double kappa, kappa_se; /* GRADIENT: -flux / (dT/dz)                           */
+    double kappa_solid;     /* POROUS: flux averaged over the solid only           */
+    double psi, psi_se;     /* WALLS: flux / (sum_b C_b v_b / 4 (dT_lo - dT_hi))   */
+    uint64_t particles, segments, scatters, wall_hits, periodic, truncated, absorbed;
+    double kernel_ms;       /* device time of the trace kernel                    */
+    uint32_t kernel_launches; /* kernels this run launched                        */
+    uint32_t device_flags;  /* device-side warning bits (0 = none)                */
+} le_mc_tallies;
+
+/* Waits for the run, copies the tallies to the host and normalises them
+ * (N = energy / E_eff after the algorithm; Eq. 4 for steady runs).
+ * Errors: LE_MC_ERR_STATE (failed run), LE_MC_ERR_CUDA. */
+LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out);
+
+/* Arrays of a finished run, copied into caller memory of `capacity` bytes
+ * (*written receives the byte count; call with dst = NULL to query it):
+ *   T, T_SE, Q, Q_SE : double[n_bins_x]  slab temperature T - T_eq (energy
+ *                      temperature) and heat flux per bin, batch-mean errors
+ *   H, H_SE          : double[n_hj]      flux carried between scattering
+ *                      events j and j+1 (j = 0: emission to first scattering)
+ *   GRID             : int32[n_samples][grid_nz][grid_ny][grid_nx] signed
+ *                      particle counts of Eq. 3 (times E_eff = energy per cell)
+ *   PARTICLES        : le_mc_particle[n_particles] (record_particles = 1)
+ * Errors: LE_MC_ERR_INVALID (array not produced by this run, capacity too
+ * small), LE_MC_ERR_STATE, LE_MC_ERR_CUDA. */
+enum { LE_MC_ARRAY_T = 0, LE_MC_ARRAY_T_SE = 1, LE_MC_ARRAY_Q = 2, LE_MC_ARRAY_Q_SE = 3,
+       LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7 };
+LE_MC_API le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity,
+                              size_t* written);
+
+typedef struct {
+    int8_t sign;        /* +1 / -1                                                 */
+    int8_t fate;        /* 0 absorbed, 1 scattering cap, 2 segment cap, 3 t_final   */
+    int16_t pad;
+    uint32_t n_seg, n_scat, n_wall, n_periodic;
+    uint32_t mode0;     /* emitted mode                                            */
+    double L_axis;      /* algebraic length along the flux axis                    */
+    double x0, t0;      /* emission position along x and emission time             */
+} le_mc_particle;
+
+LE_MC_API le_mc_status le_mc_destroy_run(le_mc_run_handle h);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+/* Philox4x32-10 of n counters (4 words each) under one key, computed by a GPU
+ * kernel; host arrays in and out.  Synchronous. */
+LE_MC_API le_mc_status le_mc_philox(const uint32_t* counters, uint32_t key0, uint32_t key1, uint32_t* out,
+                          size_t n);
+
+/* Mode draws of the device alias tables (which = 0 emission, 1 scattering)
+ * for n uniform 32-bit words; host arrays.  Synchronous. */
+LE_MC_API le_mc_status le_mc_sample_modes(le_mc_material m, int32_t which, const uint32_t* words,
+                                int32_t* modes, size_t n);
+
+/* Current device: SM count and name (NULL-safe). */
+LE_MC_API le_mc_status le_mc_device_info(int32_t* sm_count, char* name, size_t name_capacity);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+/* sizeof of the ABI structs, for binding checks: which = 0 material_desc,
+ * 1 geometry_desc, 2 run_desc, 3 tallies, 4 particle; -1 if unknown. */
+LE_MC_API int32_t le_mc_struct_size(int32_t which);
+
+LE_MC_API const char* le_mc_last_error(void);
+LE_MC_API int32_t le_mc_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LE_MC_H */

@@ -1,0 +1,308 @@
+"""ctypes binding of the le_mc C ABI (``include/le_mc.h``).
+
+Argument marshalling only: every step of the trajectory tracing runs in the
+CUDA library.  Functions keep the C names; a non-OK status raises
+``LeMcError`` carrying the status and ``le_mc_last_error()``.  The library is
+loaded from the package directory; if it is missing, importing this module
+fails loudly (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libLeMC.so")
+
+LE_MC_OK, LE_MC_ERR_INVALID, LE_MC_ERR_NOMEM, LE_MC_ERR_CUDA = 0, 1, 2, 3
+LE_MC_ERR_TIMEOUT, LE_MC_ERR_BUDGET, LE_MC_ERR_STATE, LE_MC_ERR_NODEV = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "TIMEOUT", 5: "BUDGET", 6: "STATE", 7: "NODEV"}
+
+MAT = {"gray": 0, "quadratic": 1, "tabulated": 2}
+GEOM = {"planes": 0, "bulk": 1, "porous": 2}
+WALL = {"black": 0, "diffuse": 1, "specular": 2}
+SRC = {"walls": 0, "gradient": 1, "pulse": 2}
+PREC = {"fp64": 0, "fp32": 1}
+ARRAY = {"T": 0, "T_se": 1, "q": 2, "q_se": 3, "H": 4, "H_se": 5, "grid": 6, "particles": 7}
+MAX_BRANCHES = 4
+
+
+class LeMcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"le_mc status {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class MaterialDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_branch", C.c_int32), ("n_bins", C.c_int32), ("n_modes", C.c_int32),
+                ("T_eq", C.c_double), ("gray_v", C.c_double), ("gray_tau", C.c_double), ("gray_C", C.c_double),
+                ("c1", C.c_double * MAX_BRANCHES), ("c2", C.c_double * MAX_BRANCHES),
+                ("degeneracy", C.c_double * MAX_BRANCHES),
+                ("a_lattice", C.c_double), ("A", C.c_double), ("B", C.c_double), ("C_exp", C.c_double),
+                ("tab_v", C.POINTER(C.c_double)), ("tab_tau", C.POINTER(C.c_double)),
+                ("tab_C", C.POINTER(C.c_double))]
+
+
+class GeometryDesc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("wall_lo", C.c_int32), ("wall_hi", C.c_int32), ("pore_wall", C.c_int32),
+                ("L", C.c_double), ("pitch", C.c_double), ("radius", C.c_double),
+                ("cells_y", C.c_int32), ("cells_z", C.c_int32)]
+
+
+class RunDesc(C.Structure):
+    _fields_ = [("source", C.c_int32), ("precision", C.c_int32),
+                ("dT_lo", C.c_double), ("dT_hi", C.c_double), ("dTdz", C.c_double),
+                ("pulse_sigma_x", C.c_double), ("pulse_sigma_t", C.c_double), ("pulse_t_center", C.c_double),
+                ("pulse_energy", C.c_double), ("pulse_y0", C.c_double), ("pulse_z0", C.c_double),
+                ("n_particles", C.c_uint64), ("seed", C.c_uint64),
+                ("instance_id", C.c_uint32), ("max_scatter", C.c_uint32), ("max_events", C.c_uint32),
+                ("n_bins_x", C.c_int32), ("n_batch", C.c_int32),
+                ("grid_nx", C.c_int32), ("grid_ny", C.c_int32), ("grid_nz", C.c_int32), ("n_samples", C.c_int32),
+                ("t_final", C.c_double), ("sample_dt", C.c_double),
+                ("n_hj", C.c_int32), ("record_particles", C.c_int32),
+                ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32)]
+
+
+class Tallies(C.Structure):
+    _fields_ = [(n, C.c_double) for n in (
+        "P_total", "E_eff_dot", "E_eff", "C_tot", "sum_sL", "sum_sL2", "flux", "flux_se", "kappa",
+        "kappa_se", "kappa_solid", "psi", "psi_se")] + [
+        (n, C.c_uint64) for n in ("particles", "segments", "scatters", "wall_hits", "periodic",
+                                  "truncated", "absorbed")] + [
+        ("kernel_ms", C.c_double), ("kernel_launches", C.c_uint32), ("device_flags", C.c_uint32)]
+
+
+class Particle(C.Structure):
+    _fields_ = [("sign", C.c_int8), ("fate", C.c_int8), ("pad", C.c_int16),
+                ("n_seg", C.c_uint32), ("n_scat", C.c_uint32), ("n_wall", C.c_uint32),
+                ("n_periodic", C.c_uint32), ("mode0", C.c_uint32),
+                ("L_axis", C.c_double), ("x0", C.c_double), ("t0", C.c_double)]
+
+
+PARTICLE_DTYPE = np.dtype([("sign", np.int8), ("fate", np.int8), ("pad", np.int16),
+                           ("n_seg", np.uint32), ("n_scat", np.uint32), ("n_wall", np.uint32),
+                           ("n_periodic", np.uint32), ("mode0", np.uint32),
+                           ("L_axis", np.float64), ("x0", np.float64), ("t0", np.float64)])
+
+_STATUS = C.c_int
+_H = C.c_void_p
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "le_mc_create_material": (_STATUS, [C.POINTER(MaterialDesc), C.POINTER(_H)]),
+    "le_mc_destroy_material": (_STATUS, [_H]),
+    "le_mc_material_table": (_STATUS, [C.POINTER(MaterialDesc), C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
+    "le_mc_alias_table": (_STATUS, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "le_mc_create_geometry": (_STATUS, [C.POINTER(GeometryDesc), C.POINTER(_H)]),
+    "le_mc_destroy_geometry": (_STATUS, [_H]),
+    "le_mc_run": (_STATUS, [_H, _H, C.POINTER(RunDesc), C.c_void_p, C.POINTER(_H)]),
+    "le_mc_wait": (_STATUS, [_H]),
+    "le_mc_read_tallies": (_STATUS, [_H, C.POINTER(Tallies)]),
+    "le_mc_read_array": (_STATUS, [_H, C.c_int32, C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "le_mc_destroy_run": (_STATUS, [_H]),
+    "le_mc_philox": (_STATUS, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_size_t]),
+    "le_mc_sample_modes": (_STATUS, [_H, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t]),
+    "le_mc_device_info": (_STATUS, [C.POINTER(C.c_int32), C.c_char_p, C.c_size_t]),
+    "le_mc_struct_size": (C.c_int32, [C.c_int32]),
+    "le_mc_last_error": (C.c_char_p, []),
+    "le_mc_abi_version": (C.c_int32, []),
+}
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"le_mc CUDA library not built ({LIB_PATH}); run __graft_entry__.build() "
+                      "or python -m paper_1206_3316_gb300.build")
+lib = C.CDLL(LIB_PATH)
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+for _i, _cls in enumerate((MaterialDesc, GeometryDesc, RunDesc, Tallies, Particle)):
+    if lib.le_mc_struct_size(_i) != C.sizeof(_cls):
+        raise ImportError(f"ABI mismatch: {_cls.__name__} is {C.sizeof(_cls)} bytes in Python, "
+                          f"{lib.le_mc_struct_size(_i)} in libLeMC.so")
+
+
+def _check(status, what):
+    if status != LE_MC_OK:
+        raise LeMcError(status, f"{what}: {lib.le_mc_last_error().decode(errors='replace')}")
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+# ---- descriptors from workload dicts -------------------------------------
+def material_desc(mat):
+    d = MaterialDesc()
+    d.kind = MAT[mat["kind"]]
+    d.T_eq = float(mat.get("T_eq", 300.0))
+    keep = []
+    if mat["kind"] == "gray":
+        d.gray_v, d.gray_tau, d.gray_C = mat["v"], mat["tau"], mat["C"]
+    elif mat["kind"] == "quadratic":
+        br = mat["branches"]
+        d.n_branch = len(br)
+        for i, b in enumerate(br):
+            d.c1[i], d.c2[i], d.degeneracy[i] = b["c1"], b["c2"], b["degeneracy"]
+        d.n_bins = int(mat["n_bins"])
+        d.a_lattice, d.A, d.B, d.C_exp = mat["a_lattice"], mat["A"], mat["B"], mat["C"]
+    else:
+        arrs = [np.ascontiguousarray(mat[k], dtype=np.float64) for k in ("v", "tau", "C")]
+        keep = arrs
+        d.n_modes = arrs[0].size
+        d.tab_v, d.tab_tau, d.tab_C = (a.ctypes.data_as(C.POINTER(C.c_double)) for a in arrs)
+    d._keep = keep
+    return d
+
+
+def geometry_desc(geo):
+    g = GeometryDesc()
+    g.kind = GEOM[geo["kind"]]
+    g.wall_lo = WALL[geo.get("wall_lo", "diffuse")]
+    g.wall_hi = WALL[geo.get("wall_hi", "diffuse")]
+    g.pore_wall = WALL[geo.get("pore_wall", "diffuse")]
+    g.L = float(geo.get("L", 0.0))
+    g.pitch = float(geo.get("pitch", 0.0))
+    g.radius = float(geo.get("radius", 0.0))
+    g.cells_y = int(geo.get("cells_y", 1))
+    g.cells_z = int(geo.get("cells_z", 1))
+    return g
+
+
+def run_desc(src, run, launch=None):
+    r = RunDesc()
+    r.source = SRC[src["kind"]]
+    r.precision = PREC[run.get("precision", "fp64")]
+    r.dT_lo, r.dT_hi, r.dTdz = src.get("dT_lo", 0.0), src.get("dT_hi", 0.0), src.get("dTdz", 0.0)
+    r.pulse_sigma_x, r.pulse_sigma_t = src.get("sigma_x", 0.0), src.get("sigma_t", 0.0)
+    r.pulse_t_center, r.pulse_energy = src.get("t_center", 0.0), src.get("energy", 0.0)
+    r.pulse_y0, r.pulse_z0 = src.get("y0", 0.0), src.get("z0", 0.0)
+    r.n_particles, r.seed = int(run["n_particles"]), int(run["seed"])
+    r.instance_id = int(run.get("instance_id", 0))
+    r.max_scatter, r.max_events = int(run.get("max_scatter", 0)), int(run.get("max_events", 1 << 20))
+    r.n_bins_x, r.n_batch = int(run.get("n_bins_x", 0)), int(run.get("n_batch", 32))
+    gx, gy, gz = run.get("grid", (0, 0, 0))
+    r.grid_nx, r.grid_ny, r.grid_nz = int(gx), int(gy), int(gz)
+    r.n_samples = int(run.get("n_samples", 0))
+    r.t_final, r.sample_dt = float(run.get("t_final", 0.0)), float(run.get("sample_dt", 0.0))
+    r.n_hj = int(run.get("n_hj", 0))
+    r.record_particles = 1 if run.get("record_particles", False) else 0
+    launch = launch or {}
+    r.blocks_per_sm = int(launch.get("blocks_per_sm", run.get("blocks_per_sm", 0)))
+    r.threads_per_block = int(launch.get("threads_per_block", run.get("threads_per_block", 0)))
+    return r
+
+
+# ---- thin wrappers with the C names --------------------------------------
+def le_mc_create_material(desc):
+    h = _H()
+    _check(lib.le_mc_create_material(C.byref(desc), C.byref(h)), "le_mc_create_material")
+    return h
+
+
+def le_mc_destroy_material(h):
+    _check(lib.le_mc_destroy_material(h), "le_mc_destroy_material")
+
+
+def le_mc_material_table(desc):
+    n = C.c_int32()
+    _check(lib.le_mc_material_table(C.byref(desc), None, None, None, None, 0, C.byref(n)), "le_mc_material_table")
+    arrs = [np.zeros(n.value) for _ in range(4)]
+    _check(lib.le_mc_material_table(C.byref(desc), *[a.ctypes.data for a in arrs], n.value, C.byref(n)),
+           "le_mc_material_table")
+    return tuple(arrs)
+
+
+def le_mc_alias_table(weights):
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    thr = np.zeros(w.size, dtype=np.uint32)
+    al = np.zeros(w.size, dtype=np.uint32)
+    _check(lib.le_mc_alias_table(w.ctypes.data, w.size, thr.ctypes.data, al.ctypes.data), "le_mc_alias_table")
+    return thr, al
+
+
+def le_mc_create_geometry(desc):
+    h = _H()
+    _check(lib.le_mc_create_geometry(C.byref(desc), C.byref(h)), "le_mc_create_geometry")
+    return h
+
+
+def le_mc_destroy_geometry(h):
+    _check(lib.le_mc_destroy_geometry(h), "le_mc_destroy_geometry")
+
+
+def le_mc_run(mat, geo, desc, stream=None):
+    h = _H()
+    st = lib.le_mc_run(mat, geo, C.byref(desc), _stream_ptr(stream), C.byref(h))
+    if st != LE_MC_OK:
+        msg = lib.le_mc_last_error().decode(errors="replace")
+        if h.value:
+            lib.le_mc_destroy_run(h)
+        raise LeMcError(st, f"le_mc_run: {msg}")
+    return h
+
+
+def le_mc_wait(h):
+    _check(lib.le_mc_wait(h), "le_mc_wait")
+
+
+def le_mc_read_tallies(h):
+    t = Tallies()
+    _check(lib.le_mc_read_tallies(h, C.byref(t)), "le_mc_read_tallies")
+    return {f[0]: getattr(t, f[0]) for f in Tallies._fields_}
+
+
+def le_mc_read_array(h, which):
+    code = ARRAY[which]
+    n = C.c_size_t()
+    _check(lib.le_mc_read_array(h, code, None, 0, C.byref(n)), "le_mc_read_array")
+    if which == "grid":
+        out = np.zeros(n.value // 4, dtype=np.int32)
+    elif which == "particles":
+        out = np.zeros(n.value // PARTICLE_DTYPE.itemsize, dtype=PARTICLE_DTYPE)
+    else:
+        out = np.zeros(n.value // 8, dtype=np.float64)
+    _check(lib.le_mc_read_array(h, code, out.ctypes.data, out.nbytes, C.byref(n)), "le_mc_read_array")
+    return out
+
+
+def le_mc_destroy_run(h):
+    _check(lib.le_mc_destroy_run(h), "le_mc_destroy_run")
+
+
+def le_mc_philox(counters, key0, key1):
+    c = np.ascontiguousarray(counters, dtype=np.uint32).reshape(-1, 4)
+    out = np.zeros_like(c)
+    _check(lib.le_mc_philox(c.ctypes.data, int(key0), int(key1), out.ctypes.data, c.shape[0]), "le_mc_philox")
+    return out
+
+
+def le_mc_sample_modes(mat, which, words):
+    w = np.ascontiguousarray(words, dtype=np.uint32)
+    out = np.zeros(w.size, dtype=np.int32)
+    _check(lib.le_mc_sample_modes(mat, 1 if which in (1, "scatter") else 0, w.ctypes.data, out.ctypes.data, w.size),
+           "le_mc_sample_modes")
+    return out
+
+
+def le_mc_device_info():
+    n = C.c_int32()
+    buf = C.create_string_buffer(256)
+    _check(lib.le_mc_device_info(C.byref(n), buf, 256), "le_mc_device_info")
+    return n.value, buf.value.decode()
+
+
+def le_mc_last_error():
+    return lib.le_mc_last_error().decode(errors="replace")
+
+
+def le_mc_abi_version():
+    return lib.le_mc_abi_version()

@@ -1,0 +1,91 @@
+// Device helpers of the trace kernels: the Philox4x32-10 counter-based
+// generator and per-precision maths (uniforms, -ln u, sqrt, sincos(2 pi u)).
+#pragma once
+
+#include <stdint.h>
+
+namespace lemc {
+
+// Philox4x32-10 from its published definition (Salmon, Moraes, Dror, Shaw,
+// SC'11): ten rounds; each multiplies word 0 by 0xD2511F53 and word 2 by
+// 0xCD9E8D57 (32x32 -> 64 bits) and mixes the high halves with the other
+// words and the round key.  The ten round keys (k0 + r 0x9E3779B9,
+// k1 + r 0xBB67AE85) are precomputed on the host and passed as kernel
+// parameters, so they are read from the constant bank by the XORs.
+struct RoundKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+    }
+    return c;
+}
+
+template <typename R>
+struct DMath;
+
+// FP32 trajectories.  Uniform u = ((r >> 9) + 1/2) 2^-23 in ]0,1[ (built
+// from the bit pattern 1.m - (1 - 2^-24), exact); -ln u through the MUFU
+// base-2 logarithm; sincos of 2 pi u evaluated on [-pi, pi[ and reflected.
+template <>
+struct DMath<float> {
+    static __device__ __forceinline__ float uniform(uint32_t r)
+    {
+        return __int_as_float(0x3F800000u | (r >> 9)) - 0.99999994f;
+    }
+    static __device__ __forceinline__ float neg_log(float u) { return -0.693147180559945f * __log2f(u); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float div(float a, float b) { return __fdividef(a, b); }
+    static __device__ __forceinline__ float rcp(float a) { return __frcp_rn(a); }
+    static __device__ __forceinline__ void sincos_2pi(float u, float* s, float* c)
+    {
+        float sn, cs;
+        __sincosf(fmaf(u, 6.28318530717958648f, -3.14159265358979324f), &sn, &cs);
+        *s = -sn;
+        *c = -cs;
+    }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+    static __device__ __forceinline__ float big() { return 3.0e38f; }
+};
+
+// FP64 trajectories: u = (r + 1/2) 2^-32 and the libm functions.
+template <>
+struct DMath<double> {
+    static __device__ __forceinline__ double uniform(uint32_t r)
+    {
+        return ((double)r + 0.5) * (1.0 / 4294967296.0);
+    }
+    static __device__ __forceinline__ double neg_log(double u) { return -log(u); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+    static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+    static __device__ __forceinline__ void sincos_2pi(double u, double* s, double* c)
+    {
+        const double phi = 6.283185307179586 * u;
+        *c = cos(phi);
+        *s = sin(phi);
+    }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+    static __device__ __forceinline__ double big() { return 1.0e300; }
+};
+
+// Mode draw from an alias table: column j = floor(r n / 2^32), kept when the
+// low word of r n is below its threshold, else its alias.
+__device__ __forceinline__ uint32_t alias_draw(const uint2* table, uint32_t n, uint32_t r)
+{
+    const unsigned long long m = (unsigned long long)r * n;
+    const uint32_t j = (uint32_t)(m >> 32);
+    const uint2 e = table[j];
+    return ((uint32_t)m < e.x) ? j : e.y;
+}
+
+}  // namespace lemc

@@ -1,0 +1,558 @@
+// C ABI of the le_mc library (declared in include/le_mc.h): handle
+// lifetimes, device memory, launches, read-back and normalisation.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "le_mc_internal.h"
+#include "trace_kernel.cuh"
+
+namespace lemc {
+cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
+                             size_t smem, cudaStream_t st);
+cudaError_t launch_trace_f64(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
+                             size_t smem, cudaStream_t st);
+cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
+cudaError_t occupancy_trace_f64(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
+size_t smem_trace_f32(int n_modes, int threads, int prof_len, int hj_len);
+size_t smem_trace_f64(int n_modes, int threads, int prof_len, int hj_len);
+cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n, cudaStream_t st);
+cudaError_t launch_sample_modes(const uint2* table, int n_modes, const uint32_t* words, int32_t* out, size_t n,
+                                cudaStream_t st);
+}  // namespace lemc
+
+using namespace lemc;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+le_mc_status fail(le_mc_status s, const char* fmt, const char* detail = nullptr)
+{
+    if (detail) snprintf(g_err, sizeof(g_err), "%s: %s", fmt, detail);
+    else snprintf(g_err, sizeof(g_err), "%s", fmt);
+    return s;
+}
+
+le_mc_status cuda_fail(cudaError_t e, const char* where)
+{
+    if (e == cudaErrorMemoryAllocation) return fail(LE_MC_ERR_NOMEM, where, cudaGetErrorString(e));
+    if (e == cudaErrorNoDevice || e == cudaErrorInsufficientDriver)
+        return fail(LE_MC_ERR_NODEV, where, cudaGetErrorString(e));
+    return fail(LE_MC_ERR_CUDA, where, cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(call, where)                               \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+    } while (0)
+
+}  // namespace
+
+struct le_mc_material_s {
+    std::atomic<int> refs{1};
+    le_mc_material_desc desc{};
+    int n_modes = 0;
+    int device = 0;
+    MaterialSums sums{};
+    std::vector<double> omega, v, tau, C;
+    void* d_props32 = nullptr;   // float2[n]
+    void* d_props64 = nullptr;   // double2[n]
+    uint2* d_alias_scat = nullptr;
+    uint2* d_alias_emit = nullptr;
+};
+
+struct le_mc_geometry_s {
+    std::atomic<int> refs{1};
+    le_mc_geometry_desc desc{};
+};
+
+struct le_mc_run_s {
+    le_mc_material mat = nullptr;
+    le_mc_geometry geo = nullptr;
+    le_mc_run_desc desc{};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    unsigned char* dev = nullptr;  // one stream-ordered allocation
+    size_t dev_bytes = 0;
+    size_t off_sums = 0, off_counters = 0, off_queue = 0, off_flags = 0;
+    size_t off_prof = 0, off_hj = 0, off_grid = 0, off_records = 0;
+    size_t prof_len = 0, hj_len = 0, grid_len = 0;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    bool failed = false;
+    bool have_header = false;
+    double sums[2] = {0, 0};
+    unsigned long long counters[CNT_N] = {};
+    unsigned int flags = 0;
+    uint32_t launches = 0;
+};
+
+namespace {
+
+void material_release(le_mc_material m)
+{
+    if (!m) return;
+    if (m->refs.fetch_sub(1) != 1) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(m->device);
+    cudaFree(m->d_props32);
+    cudaFree(m->d_props64);
+    cudaFree(m->d_alias_scat);
+    cudaFree(m->d_alias_emit);
+    cudaSetDevice(cur);
+    delete m;
+}
+
+void geometry_release(le_mc_geometry g)
+{
+    if (!g) return;
+    if (g->refs.fetch_sub(1) != 1) return;
+    delete g;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+extern "C" {
+
+const char* le_mc_last_error(void) { return g_err; }
+int32_t le_mc_abi_version(void) { return LE_MC_ABI_VERSION; }
+
+int32_t le_mc_struct_size(int32_t which)
+{
+    switch (which) {
+    case 0: return (int32_t)sizeof(le_mc_material_desc);
+    case 1: return (int32_t)sizeof(le_mc_geometry_desc);
+    case 2: return (int32_t)sizeof(le_mc_run_desc);
+    case 3: return (int32_t)sizeof(le_mc_tallies);
+    case 4: return (int32_t)sizeof(le_mc_particle);
+    default: return -1;
+    }
+}
+
+le_mc_status le_mc_material_table(const le_mc_material_desc* desc, double* omega, double* v, double* tau,
+                                  double* C, int32_t capacity, int32_t* n_modes)
+{
+    const char* why = "";
+    int n = 0;
+    if (!n_modes) return fail(LE_MC_ERR_INVALID, "n_modes output is null");
+    const int st = build_mode_table(desc, nullptr, nullptr, nullptr, nullptr, 0, &n, &why);
+    if (st != LE_MC_OK) return fail((le_mc_status)st, "le_mc_material_table", why);
+    *n_modes = n;
+    if (omega && v && tau && C) {
+        if (capacity < n) return fail(LE_MC_ERR_INVALID, "le_mc_material_table: capacity too small");
+        build_mode_table(desc, omega, v, tau, C, capacity, &n, &why);
+    }
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_alias_table(const double* weights, int32_t n, uint32_t* threshold, uint32_t* alias)
+{
+    const char* why = "";
+    if (!weights || !threshold || !alias) return fail(LE_MC_ERR_INVALID, "le_mc_alias_table: null pointer");
+    const int st = build_alias(weights, n, threshold, alias, &why);
+    if (st != LE_MC_OK) return fail((le_mc_status)st, "le_mc_alias_table", why);
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_material* out)
+{
+    if (!out) return fail(LE_MC_ERR_INVALID, "le_mc_create_material: out is null");
+    *out = nullptr;
+    const char* why = "";
+    int n = 0;
+    int st = build_mode_table(desc, nullptr, nullptr, nullptr, nullptr, 0, &n, &why);
+    if (st != LE_MC_OK) return fail((le_mc_status)st, "le_mc_create_material", why);
+    le_mc_material m = new (std::nothrow) le_mc_material_s();
+    if (!m) return fail(LE_MC_ERR_NOMEM, "le_mc_create_material: host allocation");
+    m->desc = *desc;
+    m->desc.tab_v = m->desc.tab_tau = m->desc.tab_C = nullptr;
+    m->n_modes = n;
+    m->omega.resize(n); m->v.resize(n); m->tau.resize(n); m->C.resize(n);
+    build_mode_table(desc, m->omega.data(), m->v.data(), m->tau.data(), m->C.data(), n, &n, &why);
+    std::vector<double> w_emit(n), w_scat(n);
+    std::vector<float> props32(2 * (size_t)n);
+    std::vector<double> props64(2 * (size_t)n);
+    m->sums.C_tot = 0.0;
+    m->sums.Cv_sum = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const double lam = m->v[i] * m->tau[i];
+        w_emit[i] = m->C[i] * m->v[i];  // boundary / gradient / pulse emission
+        w_scat[i] = m->C[i] / m->tau[i];  // normalised Eq. 2
+        m->sums.C_tot += m->C[i];
+        m->sums.Cv_sum += w_emit[i];
+        props64[2 * i] = lam;
+        props64[2 * i + 1] = m->v[i];
+        props32[2 * i] = (float)lam;
+        props32[2 * i + 1] = (float)m->v[i];
+    }
+    std::vector<uint32_t> thr_e(n), al_e(n), thr_s(n), al_s(n);
+    st = build_alias(w_emit.data(), n, thr_e.data(), al_e.data(), &why);
+    if (st == LE_MC_OK) st = build_alias(w_scat.data(), n, thr_s.data(), al_s.data(), &why);
+    if (st != LE_MC_OK) { delete m; return fail((le_mc_status)st, "le_mc_create_material", why); }
+    std::vector<uint2> ae(n), as(n);
+    for (int i = 0; i < n; ++i) {
+        ae[i] = make_uint2(thr_e[i], al_e[i]);
+        as[i] = make_uint2(thr_s[i], al_s[i]);
+    }
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_props32, props32.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&m->d_props64, props64.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_alias_scat, n * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_alias_emit, n * sizeof(uint2));
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_props32, props32.data(), props32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_props64, props64.data(), props64.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_alias_scat, as.data(), n * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->d_alias_emit, ae.data(), n * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        material_release(m);
+        return cuda_fail(e, "le_mc_create_material");
+    }
+    *out = m;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_destroy_material(le_mc_material m)
+{
+    material_release(m);
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le_mc_geometry* out)
+{
+    if (!out) return fail(LE_MC_ERR_INVALID, "le_mc_create_geometry: out is null");
+    *out = nullptr;
+    const char* why = "";
+    const int st = check_geometry(desc, &why);
+    if (st != LE_MC_OK) return fail((le_mc_status)st, "le_mc_create_geometry", why);
+    le_mc_geometry g = new (std::nothrow) le_mc_geometry_s();
+    if (!g) return fail(LE_MC_ERR_NOMEM, "le_mc_create_geometry: host allocation");
+    g->desc = *desc;
+    *out = g;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_destroy_geometry(le_mc_geometry g)
+{
+    geometry_release(g);
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc* desc, void* stream,
+                       le_mc_run_handle* out)
+{
+    if (!out) return fail(LE_MC_ERR_INVALID, "le_mc_run: out is null");
+    *out = nullptr;
+    if (!m || !g || !desc) return fail(LE_MC_ERR_INVALID, "le_mc_run: null handle or descriptor");
+    const char* why = "";
+    int st = check_run(&g->desc, desc, m->n_modes, &why);
+    if (st != LE_MC_OK) return fail((le_mc_status)st, "le_mc_run", why);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "le_mc_run: cudaGetDevice");
+    if (dev != m->device) return fail(LE_MC_ERR_INVALID, "le_mc_run: material lives on another device");
+
+    le_mc_run_handle h = new (std::nothrow) le_mc_run_s();
+    if (!h) return fail(LE_MC_ERR_NOMEM, "le_mc_run: host allocation");
+    h->desc = *desc;
+    h->stream = (cudaStream_t)stream;
+    h->device = dev;
+    const le_mc_run_desc& r = h->desc;
+    const bool profile = r.n_bins_x > 0;
+    h->prof_len = profile ? (size_t)4 * r.n_batch * (r.n_bins_x + 1) : 0;
+    h->hj_len = (size_t)2 * r.n_hj;
+    h->grid_len = r.n_samples > 0 ? (size_t)r.n_samples * r.grid_nx * r.grid_ny * r.grid_nz : 0;
+    size_t off = 0;
+    h->off_sums = off; off += 2 * sizeof(double);
+    h->off_counters = off; off += CNT_N * sizeof(unsigned long long);
+    h->off_queue = off; off += sizeof(unsigned long long);
+    h->off_flags = off; off += sizeof(unsigned long long);
+    off = align_up(off, 256);
+    h->off_prof = off; off += h->prof_len * sizeof(double);
+    off = align_up(off, 256);
+    h->off_hj = off; off += h->hj_len * sizeof(double);
+    off = align_up(off, 256);
+    h->off_grid = off; off += h->grid_len * sizeof(int32_t);
+    off = align_up(off, 256);
+    h->off_records = off;
+    if (r.record_particles) off += (size_t)r.n_particles * sizeof(le_mc_particle);
+    h->dev_bytes = align_up(off, 256);
+
+    cudaError_t e = cudaEventCreate(&h->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_stop);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->dev, h->dev_bytes, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->dev, 0, h->dev_bytes, h->stream);
+    if (e != cudaSuccess) {
+        le_mc_destroy_run(h);
+        return cuda_fail(e, "le_mc_run: allocation");
+    }
+    m->refs.fetch_add(1);
+    g->refs.fetch_add(1);
+    h->mat = m;
+    h->geo = g;
+
+    KernelArgs a;
+    memset(&a, 0, sizeof(a));
+    TraceParams& P = a.p;
+    const bool fp32 = r.precision == LE_MC_PREC_FP32;
+    P.props = fp32 ? m->d_props32 : m->d_props64;
+    P.alias_scat = m->d_alias_scat;
+    P.alias_emit = m->d_alias_emit;
+    P.n_modes = m->n_modes;
+    const le_mc_geometry_desc& G = g->desc;
+    P.geom = G.kind;
+    P.wall_lo = G.wall_lo;
+    P.wall_hi = G.wall_hi;
+    P.pore_wall = G.pore_wall;
+    P.cells_y = G.kind == LE_MC_GEOM_POROUS ? G.cells_y : 1;
+    P.cells_z = G.kind == LE_MC_GEOM_POROUS ? G.cells_z : 1;
+    P.L = G.kind == LE_MC_GEOM_BULK ? 1.0 : G.L;
+    P.pitch = G.kind == LE_MC_GEOM_POROUS ? G.pitch : 1.0;
+    P.radius = G.kind == LE_MC_GEOM_POROUS ? G.radius : 0.0;
+    P.src = r.source;
+    P.dT_lo = r.dT_lo;
+    P.dT_hi = r.dT_hi;
+    P.dTdz = r.dTdz;
+    P.p_sx = r.pulse_sigma_x;
+    P.p_st = r.pulse_sigma_t;
+    P.p_tc = r.pulse_t_center;
+    P.p_y0 = r.pulse_y0;
+    P.p_z0 = r.pulse_z0;
+    P.n_particles = (uint32_t)r.n_particles;
+    P.key0 = (uint32_t)r.seed;
+    P.key1 = (uint32_t)(r.seed >> 32);
+    P.inst = r.instance_id;
+    P.max_scatter = r.max_scatter;
+    P.max_events = r.max_events;
+    P.n_bins_x = r.n_bins_x;
+    P.n_batch = profile ? r.n_batch : 1;
+    P.prof = reinterpret_cast<double*>(h->dev + h->off_prof);
+    P.n_hj = r.n_hj;
+    P.hj = reinterpret_cast<double*>(h->dev + h->off_hj);
+    P.gx = r.grid_nx;
+    P.gy = r.grid_ny;
+    P.gz = r.grid_nz;
+    P.n_samples = r.n_samples;
+    P.sample_dt = r.sample_dt;
+    P.t_final = r.source == LE_MC_SRC_PULSE ? r.t_final : 0.0;
+    P.grid = reinterpret_cast<int32_t*>(h->dev + h->off_grid);
+    P.records = r.record_particles ? reinterpret_cast<le_mc_particle*>(h->dev + h->off_records) : nullptr;
+    P.sums = reinterpret_cast<double*>(h->dev + h->off_sums);
+    P.counters = reinterpret_cast<unsigned long long*>(h->dev + h->off_counters);
+    P.queue = reinterpret_cast<unsigned int*>(h->dev + h->off_queue);
+    P.flags = reinterpret_cast<unsigned int*>(h->dev + h->off_flags);
+    for (int i = 0; i < 10; ++i) {
+        a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
+        a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
+    }
+
+    // launch shape: persistent grid of (SMs x resident blocks)
+    int threads = r.threads_per_block > 0 ? r.threads_per_block : 256;
+    if (threads > 512) threads = 512;
+    const size_t smem = fp32 ? smem_trace_f32(m->n_modes, threads, (int)h->prof_len, (int)h->hj_len)
+                             : smem_trace_f64(m->n_modes, threads, (int)h->prof_len, (int)h->hj_len);
+    int sms = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 0;
+    if (e == cudaSuccess)
+        e = fp32 ? occupancy_trace_f32(G.kind, r.source, profile, threads, smem, &per_sm)
+                 : occupancy_trace_f64(G.kind, r.source, profile, threads, smem, &per_sm);
+    if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
+    if (e == cudaSuccess && r.blocks_per_sm > 0 && r.blocks_per_sm < per_sm) per_sm = r.blocks_per_sm;
+    int blocks = sms * per_sm;
+    // no more warps than batches of 32 particles (tiny runs)
+    const long long max_blocks = ((long long)r.n_particles + 32LL * (threads / 32) - 1) / (32LL * (threads / 32));
+    if (blocks > max_blocks) blocks = (int)max_blocks;
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_start, h->stream);
+    if (e == cudaSuccess && blocks > 0) {
+        e = fp32 ? launch_trace_f32(a, G.kind, r.source, profile, blocks, threads, smem, h->stream)
+                 : launch_trace_f64(a, G.kind, r.source, profile, blocks, threads, smem, h->stream);
+        h->launches = 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_stop, h->stream);
+    if (e != cudaSuccess) {
+        h->failed = true;
+        *out = h;  // caller destroys; the handle reports STATE from now on
+        return cuda_fail(e, "le_mc_run: launch");
+    }
+    *out = h;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_wait(le_mc_run_handle h)
+{
+    if (!h) return fail(LE_MC_ERR_INVALID, "le_mc_wait: null handle");
+    if (h->failed) return fail(LE_MC_ERR_STATE, "le_mc_wait: run failed earlier");
+    cudaError_t e = cudaEventSynchronize(h->ev_stop);
+    if (e != cudaSuccess) {
+        h->failed = true;
+        return cuda_fail(e, "le_mc_wait");
+    }
+    return LE_MC_OK;
+}
+
+static le_mc_status fetch_header(le_mc_run_handle h)
+{
+    if (h->have_header) return LE_MC_OK;
+    le_mc_status s = le_mc_wait(h);
+    if (s != LE_MC_OK) return s;
+    unsigned char tmp[2 * sizeof(double) + CNT_N * sizeof(unsigned long long) + 2 * sizeof(unsigned long long)];
+    cudaError_t e = cudaMemcpy(tmp, h->dev, sizeof(tmp), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        h->failed = true;
+        return cuda_fail(e, "le_mc_read_tallies: copy");
+    }
+    memcpy(h->sums, tmp + h->off_sums, sizeof(h->sums));
+    memcpy(h->counters, tmp + h->off_counters, sizeof(h->counters));
+    memcpy(&h->flags, tmp + h->off_flags, sizeof(h->flags));
+    h->have_header = true;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out)
+{
+    if (!h || !out) return fail(LE_MC_ERR_INVALID, "le_mc_read_tallies: null argument");
+    le_mc_status s = fetch_header(h);
+    if (s != LE_MC_OK) return s;
+    memset(out, 0, sizeof(*out));
+    normalize(&h->geo->desc, &h->desc, h->mat->sums, h->sums, h->counters, out);
+    float ms = 0.0f;
+    if (h->launches) cudaEventElapsedTime(&ms, h->ev_start, h->ev_stop);
+    out->kernel_ms = ms;
+    out->kernel_launches = h->launches;
+    out->device_flags = h->flags;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity, size_t* written)
+{
+    if (!h) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: null handle");
+    const le_mc_run_desc& r = h->desc;
+    size_t bytes = 0;
+    switch (which) {
+    case LE_MC_ARRAY_T: case LE_MC_ARRAY_T_SE: case LE_MC_ARRAY_Q: case LE_MC_ARRAY_Q_SE:
+        if (r.n_bins_x <= 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no profile");
+        bytes = (size_t)r.n_bins_x * sizeof(double);
+        break;
+    case LE_MC_ARRAY_H: case LE_MC_ARRAY_H_SE:
+        if (r.n_hj <= 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no H_j tally");
+        bytes = (size_t)r.n_hj * sizeof(double);
+        break;
+    case LE_MC_ARRAY_GRID:
+        if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
+        bytes = h->grid_len * sizeof(int32_t);
+        break;
+    case LE_MC_ARRAY_PARTICLES:
+        if (!r.record_particles) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run kept no records");
+        bytes = (size_t)r.n_particles * sizeof(le_mc_particle);
+        break;
+    default:
+        return fail(LE_MC_ERR_INVALID, "le_mc_read_array: unknown array");
+    }
+    if (written) *written = bytes;
+    if (!dst) return LE_MC_OK;
+    if (capacity < bytes) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: capacity too small");
+    le_mc_status s = fetch_header(h);
+    if (s != LE_MC_OK) return s;
+    cudaError_t e = cudaSuccess;
+    if (which == LE_MC_ARRAY_GRID) {
+        e = cudaMemcpy(dst, h->dev + h->off_grid, bytes, cudaMemcpyDeviceToHost);
+    } else if (which == LE_MC_ARRAY_PARTICLES) {
+        e = cudaMemcpy(dst, h->dev + h->off_records, bytes, cudaMemcpyDeviceToHost);
+    } else if (which <= LE_MC_ARRAY_Q_SE) {
+        std::vector<double> raw(h->prof_len), T(r.n_bins_x), Tse(r.n_bins_x), q(r.n_bins_x), qse(r.n_bins_x);
+        e = cudaMemcpy(raw.data(), h->dev + h->off_prof, raw.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            finalize_profile(&h->geo->desc, &r, h->mat->sums, raw.data(), T.data(), Tse.data(), q.data(), qse.data());
+            const double* src = which == LE_MC_ARRAY_T ? T.data() : which == LE_MC_ARRAY_T_SE ? Tse.data()
+                              : which == LE_MC_ARRAY_Q ? q.data() : qse.data();
+            memcpy(dst, src, bytes);
+        }
+    } else {
+        std::vector<double> raw(h->hj_len), H(r.n_hj), Hse(r.n_hj);
+        e = cudaMemcpy(raw.data(), h->dev + h->off_hj, raw.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            const double scale = flux_scale(&h->geo->desc, &r, h->mat->sums, nullptr, nullptr, nullptr);
+            finalize_hj(&r, scale, raw.data(), H.data(), Hse.data());
+            memcpy(dst, which == LE_MC_ARRAY_H ? H.data() : Hse.data(), bytes);
+        }
+    }
+    if (e != cudaSuccess) {
+        h->failed = true;
+        return cuda_fail(e, "le_mc_read_array: copy");
+    }
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_destroy_run(le_mc_run_handle h)
+{
+    if (!h) return LE_MC_OK;
+    if (h->dev) {
+        // stream-ordered free after the run's work
+        if (cudaFreeAsync(h->dev, h->stream) != cudaSuccess) cudaFree(h->dev);
+    }
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_stop) cudaEventDestroy(h->ev_stop);
+    material_release(h->mat);
+    geometry_release(h->geo);
+    delete h;
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_philox(const uint32_t* counters, uint32_t key0, uint32_t key1, uint32_t* out, size_t n)
+{
+    if (!counters || !out) return fail(LE_MC_ERR_INVALID, "le_mc_philox: null pointer");
+    if (n == 0) return LE_MC_OK;
+    uint4 *d_in = nullptr, *d_out = nullptr;
+    CUDA_TRY(cudaMalloc(&d_in, n * sizeof(uint4)), "le_mc_philox: cudaMalloc");
+    cudaError_t e = cudaMalloc(&d_out, n * sizeof(uint4));
+    if (e == cudaSuccess) e = cudaMemcpy(d_in, counters, n * sizeof(uint4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_philox(d_in, key0, key1, d_out, n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(out, d_out, n * sizeof(uint4), cudaMemcpyDeviceToHost);
+    cudaFree(d_in);
+    cudaFree(d_out);
+    if (e != cudaSuccess) return cuda_fail(e, "le_mc_philox");
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_sample_modes(le_mc_material m, int32_t which, const uint32_t* words, int32_t* modes, size_t n)
+{
+    if (!m || !words || !modes) return fail(LE_MC_ERR_INVALID, "le_mc_sample_modes: null argument");
+    if (which != 0 && which != 1) return fail(LE_MC_ERR_INVALID, "le_mc_sample_modes: which must be 0 or 1");
+    if (n == 0) return LE_MC_OK;
+    uint32_t* d_w = nullptr;
+    int32_t* d_m = nullptr;
+    CUDA_TRY(cudaMalloc(&d_w, n * sizeof(uint32_t)), "le_mc_sample_modes: cudaMalloc");
+    cudaError_t e = cudaMalloc(&d_m, n * sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMemcpy(d_w, words, n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = launch_sample_modes(which ? m->d_alias_scat : m->d_alias_emit, m->n_modes, d_w, d_m, n, nullptr);
+    if (e == cudaSuccess) e = cudaMemcpy(modes, d_m, n * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    cudaFree(d_w);
+    cudaFree(d_m);
+    if (e != cudaSuccess) return cuda_fail(e, "le_mc_sample_modes");
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_device_info(int32_t* sm_count, char* name, size_t name_capacity)
+{
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev), "le_mc_device_info");
+    cudaDeviceProp prop;
+    CUDA_TRY(cudaGetDeviceProperties(&prop, dev), "le_mc_device_info");
+    if (sm_count) *sm_count = prop.multiProcessorCount;
+    if (name && name_capacity) {
+        strncpy(name, prop.name, name_capacity - 1);
+        name[name_capacity - 1] = '\0';
+    }
+    return LE_MC_OK;
+}
+
+}  // extern "C"

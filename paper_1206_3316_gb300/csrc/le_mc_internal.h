@@ -1,0 +1,93 @@
+// Internal definitions shared by the host code and the CUDA kernels of the
+// le_mc library.  Not part of the public ABI (see include/le_mc.h).
+#pragma once
+
+#include <stdint.h>
+#include <vector_types.h>
+
+#include "le_mc.h"
+
+namespace lemc {
+
+// Device-side warning bits (OR-ed into a status word, never a trap).
+enum : uint32_t {
+    FLAG_REJECTION_EXHAUSTED = 1u,  // a rejection loop used all its tries
+    FLAG_INDEX_CLAMPED = 2u,        // a bin / cell / mode index was clamped into range
+    FLAG_BAD_LAUNCH = 4u,           // kernel launched with an unexpected shape
+};
+
+// Global counters produced by a run (u64 each).
+enum { CNT_PARTICLES = 0, CNT_SEGMENTS, CNT_SCATTERS, CNT_WALL, CNT_PERIODIC, CNT_TRUNCATED,
+       CNT_ABSORBED, CNT_N };
+
+// Fates recorded per particle (same meaning as le_mc_particle::fate).
+enum { FATE_ABSORBED = 0, FATE_MAX_SCATTER = 1, FATE_MAX_EVENTS = 2, FATE_T_FINAL = 3 };
+
+// Random-stream layout: Philox4x32-10 with key = seed and counter
+// (event, block, particle id, instance id).  Event 0 is emission (block 0:
+// source-specific word, mode, polar cosine, azimuth; blocks 1..64: position
+// rejection loop; blocks 65..128: pulse emission time); flight k >= 1 uses
+// (k, 0, pid, inst) for (flight length, mode redraw, polar cosine, azimuth).
+constexpr uint32_t kMaxTries = 64;
+constexpr uint32_t kTimeBlock0 = 65;
+
+struct TraceParams {
+    // material tables (device pointers)
+    const void* props;        // float2 or double2 [n_modes]: (Lambda_b, v_b)
+    const uint2* alias_scat;  // [n_modes] (threshold, alias) for C_b / tau_b
+    const uint2* alias_emit;  // [n_modes] (threshold, alias) for C_b v_b
+    int32_t n_modes;
+    // geometry
+    int32_t geom, wall_lo, wall_hi, pore_wall;
+    int32_t cells_y, cells_z;
+    double L, pitch, radius;
+    // source
+    int32_t src;
+    double dT_lo, dT_hi, dTdz;
+    double p_sx, p_st, p_tc, p_y0, p_z0;
+    // run
+    uint32_t n_particles, key0, key1, inst, max_scatter, max_events;
+    // slab profile: [4][n_batch][n_bins_x + 1] (T direct, T difference,
+    // q direct, q difference), FP64
+    int32_t n_bins_x, n_batch;
+    double* prof;
+    // flux by scattering index: [2][n_hj] (sum s h, sum h^2)
+    int32_t n_hj;
+    double* hj;
+    // transient counting grid [n_samples][gz][gy][gx], int32
+    int32_t gx, gy, gz, n_samples;
+    double sample_dt, t_final;
+    int32_t* grid;
+    // per-particle records (le_mc_particle[n_particles]) or null
+    le_mc_particle* records;
+    // outputs
+    double* sums;                  // [2]: sum s L, sum (s L)^2
+    unsigned long long* counters;  // [CNT_N]
+    unsigned int* queue;           // [1]: next particle id
+    unsigned int* flags;           // [1]
+};
+
+// Host helpers (le_mc_host.cpp).
+int build_mode_table(const le_mc_material_desc* d, double* omega, double* v, double* tau, double* C,
+                     int capacity, int* n_modes, const char** why);
+int build_alias(const double* w, int n, uint32_t* thr, uint32_t* alias, const char** why);
+int check_geometry(const le_mc_geometry_desc* g, const char** why);
+int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes, const char** why);
+
+struct MaterialSums {
+    double C_tot, Cv_sum;
+};
+
+// Normalisation of the raw device sums into le_mc_tallies (after the
+// algorithm: N = energy / E_eff; Eq. 4: E_eff_dot = P / N).
+void normalize(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
+               const double sums[2], const unsigned long long counters[CNT_N], le_mc_tallies* out);
+
+// Batch-mean slab profiles from the raw [4][B][nb+1] arrays.
+void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
+                      const double* raw, double* T, double* T_se, double* q, double* q_se);
+void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, double* H, double* H_se);
+double flux_scale(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
+                  double* P_out, double* Vref_out, double* Vsolid_out);
+
+}  // namespace lemc

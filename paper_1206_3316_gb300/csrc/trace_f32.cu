@@ -1,0 +1,64 @@
+// Instantiations and launcher of the float trace kernels (one translation
+// unit per trajectory precision so the two compile in parallel).
+#include <cuda_runtime.h>
+
+#include "trace_kernel.cuh"
+
+namespace lemc {
+
+namespace {
+template <int G, int S, bool PR>
+cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem, cudaStream_t st)
+{
+    auto k = trace_kernel<float, G, S, PR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (blocks <= 0) return cudaSuccess;
+    k<<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int G, int S, bool PR>
+cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
+{
+    auto k = trace_kernel<float, G, S, PR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
+}
+}  // namespace
+
+// Valid (geometry, source, profile) combinations; anything else is rejected
+// by the host validation before a launch is attempted.
+#define LEMC_DISPATCH(FN, ...)                                                                      \
+    if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_WALLS && profile)                              \
+        return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, true>(__VA_ARGS__);                            \
+    if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_WALLS)                                         \
+        return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false>(__VA_ARGS__);                           \
+    if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_GRADIENT)                                      \
+        return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false>(__VA_ARGS__);                        \
+    if (geom == LE_MC_GEOM_BULK && src == LE_MC_SRC_GRADIENT)                                        \
+        return FN<LE_MC_GEOM_BULK, LE_MC_SRC_GRADIENT, false>(__VA_ARGS__);                          \
+    if (geom == LE_MC_GEOM_POROUS && src == LE_MC_SRC_GRADIENT)                                      \
+        return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_GRADIENT, false>(__VA_ARGS__);                        \
+    if (geom == LE_MC_GEOM_POROUS && src == LE_MC_SRC_PULSE)                                         \
+        return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_PULSE, false>(__VA_ARGS__);                           \
+    return cudaErrorInvalidValue;
+
+cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
+                              size_t smem, cudaStream_t st)
+{
+    LEMC_DISPATCH(launch_one, a, blocks, threads, smem, st)
+}
+
+cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm)
+{
+    LEMC_DISPATCH(occupancy_one, threads, smem, per_sm)
+}
+
+size_t smem_trace_f32(int n_modes, int threads, int prof_len, int hj_len)
+{
+    return trace_smem_bytes<float>(n_modes, threads, prof_len, hj_len);
+}
+
+}  // namespace lemc

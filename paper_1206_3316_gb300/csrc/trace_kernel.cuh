@@ -1,0 +1,564 @@
+// Persistent trajectory kernel of the le_mc library: steps I-VI of the
+// paper's trajectory algorithm for independent deviational particles, with
+// the estimators of step V (Eq. 3 time samples, Eq. 4 path integrals).
+//
+// Work distribution.  Each lane traces one particle at a time; all state
+// stays in registers.  A warp owns a 64-entry emission buffer in shared
+// memory: when lanes run dry, the whole warp emits a batch of 32 new
+// particles at once (step I, converged), then the dead lanes pop states from
+// the buffer.  Lanes are therefore refilled as soon as their particle ends,
+// whatever the spread of lifetimes, and emission never runs with a partial
+// warp.  Particle ids come from a 64-bit global counter bumped once per
+// batch.  Each flight k of particle pid draws its four uniforms from
+// Philox4x32-10 at counter (k, 0, pid, instance), so the result does not
+// depend on which lane or block traced the particle.
+//
+// Tallies.  Per particle the algebraic length along the flux axis is
+// accumulated in the trajectory precision; per lane the sums over particles
+// are kept as FP64 (FP64 runs) or compensated FP32 pairs (FP32 runs); each
+// warp reduces them with shuffles before one FP64 atomic per quantity.
+// Slab profiles (batch groups x bins, difference arrays for whole-bin runs)
+// and the scattering-index split live in shared memory and are flushed once
+// per block.  The transient grid takes int32 red-adds in global memory.
+#pragma once
+
+#include <stdint.h>
+
+#include "device_math.cuh"
+#include "le_mc_internal.h"
+
+namespace lemc {
+
+struct KernelArgs {
+    TraceParams p;
+    RoundKeys rk;
+};
+
+enum { HIT_NONE = 0, HIT_XLO = 1, HIT_XHI = 2, HIT_CYL = 3, HIT_YLO = 4, HIT_YHI = 5, HIT_ZLO = 6, HIT_ZHI = 7 };
+
+constexpr int kBufSlots = 64;  // emission buffer entries per warp
+
+// Emission buffer of one warp, structure of arrays.
+template <typename R>
+struct EmitBuffer {
+    R x[kBufSlots], y[kBufSlots], z[kBufSlots];
+    R ox[kBufSlots], oy[kBufSlots], oz[kBufSlots];
+    R t[kBufSlots];
+    uint32_t pid[kBufSlots];
+    uint32_t mode_sign[kBufSlots];  // mode | (sign < 0) << 31
+    uint32_t cell[kBufSlots];       // cy | cz << 16 (POROUS)
+};
+
+// Compensated FP32 sum (Neumaier); plain sum for FP64.
+template <typename R>
+struct Acc {
+    R s = 0, c = 0;
+    __device__ __forceinline__ void add(R v)
+    {
+        const R t = s + v;
+        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <>
+struct Acc<double> {
+    double s = 0;
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <typename R>
+__device__ __forceinline__ void load_props(const void* props, uint32_t mode, R& lam, R& vg)
+{
+    if constexpr (sizeof(R) == 4) {
+        const float2 e = reinterpret_cast<const float2*>(props)[mode];
+        lam = e.x;
+        vg = e.y;
+    } else {
+        const double2 e = reinterpret_cast<const double2*>(props)[mode];
+        lam = e.x;
+        vg = e.y;
+    }
+}
+
+// Step I for one particle; returns false if a rejection loop ran out.  The
+// emission alias table is read from global memory (once per particle, cached
+// in L1), which leaves shared memory to the per-flight tables.
+template <typename R, int GEOM, int SRC>
+__device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundKeys& rk, const uint2* alias_emit,
+                                              uint32_t pid, R& x, R& y, R& z, R& ox, R& oy, R& oz, R& t,
+                                              uint32_t& mode, int& sign, uint32_t& cy, uint32_t& cz)
+{
+    using M = DMath<R>;
+    const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, P.inst), rk);
+    mode = alias_draw(alias_emit, (uint32_t)P.n_modes, r.y);
+    const R u0 = M::uniform(r.x), u2 = M::uniform(r.z), u3 = M::uniform(r.w);
+    R sn, cs;
+    M::sincos_2pi(u3, &sn, &cs);
+    y = z = t = R(0);
+    cy = cz = 0;
+    bool ok = true;
+    if constexpr (SRC == LE_MC_SRC_WALLS) {
+        // isothermal walls: wall picked by |T_b - T_eq|, cosine law into the domain
+        const R wlo = (R)fabs(P.dT_lo), whi = (R)fabs(P.dT_hi);
+        const bool lo = u0 * (wlo + whi) < wlo;
+        const R mu = M::sqrt_(u2);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        ox = lo ? mu : -mu;
+        oy = st * cs;
+        oz = st * sn;
+        x = lo ? R(0) : (R)P.L;
+        sign = lo ? (P.dT_lo >= 0.0 ? 1 : -1) : (P.dT_hi >= 0.0 ? 1 : -1);
+    } else if constexpr (SRC == LE_MC_SRC_GRADIENT) {
+        // Eq. 6: |cos| law about z, sign sgn(-cos dT/dz), even ids positive
+        sign = (pid & 1u) ? -1 : 1;
+        const R dir = (R)sign * (P.dTdz > 0.0 ? R(-1) : R(1));
+        const R mu = dir * M::sqrt_(u2);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        ox = st * cs;
+        oy = st * sn;
+        oz = mu;
+        x = (GEOM == LE_MC_GEOM_BULK) ? R(0) : u0 * (R)P.L;
+        if constexpr (GEOM == LE_MC_GEOM_POROUS) {
+            const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
+            ok = false;
+            for (uint32_t b = 1; b <= kMaxTries; ++b) {
+                const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+                const R Y = M::uniform(q.x) * pitch * (R)P.cells_y;
+                const R Z = M::uniform(q.y) * pitch * (R)P.cells_z;
+                int iy = (int)M::floor_(Y / pitch), iz = (int)M::floor_(Z / pitch);
+                iy = min(max(iy, 0), P.cells_y - 1);
+                iz = min(max(iz, 0), P.cells_z - 1);
+                y = Y - (R)iy * pitch;
+                z = Z - (R)iz * pitch;
+                cy = (uint32_t)iy;
+                cz = (uint32_t)iz;
+                const R dy = y - half, dz = z - half;
+                if (!(dy * dy + dz * dz < r2)) { ok = true; break; }
+            }
+        }
+    } else {  // PULSE on the top face x = L, all signs positive
+        sign = 1;
+        const R mu = M::sqrt_(u2);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        ox = -mu;
+        oy = st * cs;
+        oz = st * sn;
+        x = (R)P.L;
+        const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
+        const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
+        ok = false;
+        for (uint32_t b = 1; b <= kMaxTries; ++b) {
+            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+            const R rad = (R)P.p_sx * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x)));
+            R s2, c2;
+            M::sincos_2pi(M::uniform(q.y), &s2, &c2);
+            R Y = (R)P.p_y0 + rad * c2;
+            R Z = (R)P.p_z0 + rad * s2;
+            Y -= Dy * M::floor_(Y / Dy);
+            Z -= Dz * M::floor_(Z / Dz);
+            int iy = (int)M::floor_(Y / pitch), iz = (int)M::floor_(Z / pitch);
+            iy = min(max(iy, 0), P.cells_y - 1);
+            iz = min(max(iz, 0), P.cells_z - 1);
+            y = Y - (R)iy * pitch;
+            z = Z - (R)iz * pitch;
+            cy = (uint32_t)iy;
+            cz = (uint32_t)iz;
+            const R dy = y - half, dz = z - half;
+            if (!(dy * dy + dz * dz < r2)) { ok = true; break; }
+        }
+        t = (R)P.p_tc;
+        bool tok = false;
+        for (uint32_t b = kTimeBlock0; b < kTimeBlock0 + kMaxTries; ++b) {
+            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+            R s2, c2;
+            M::sincos_2pi(M::uniform(q.y), &s2, &c2);
+            const R t0 = (R)P.p_tc + (R)P.p_st * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x))) * c2;
+            if (t0 >= R(0)) { t = t0; tok = true; break; }
+        }
+        ok = ok && tok;
+    }
+    return ok;
+}
+
+template <typename R, int GEOM, int SRC, bool PROFILE>
+__global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
+{
+    using M = DMath<R>;
+    constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE);
+    constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
+    const TraceParams& P = args.p;
+    const RoundKeys& rk = args.rk;
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_modes = P.n_modes;
+    R* s_props = reinterpret_cast<R*>(smem);
+    uint2* s_scat = reinterpret_cast<uint2*>(smem + (size_t)n_modes * 2 * sizeof(R));
+    size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
+    off = (off + 15) & ~(size_t)15;
+    EmitBuffer<R>* s_buf = reinterpret_cast<EmitBuffer<R>*>(smem + off);
+    const int n_warps = blockDim.x >> 5;
+    off += (size_t)n_warps * sizeof(EmitBuffer<R>);
+    double* s_prof = reinterpret_cast<double*>(smem + off);
+    const int prof_len = PROFILE ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
+    off += (size_t)prof_len * sizeof(double);
+    double* s_hj = reinterpret_cast<double*>(smem + off);
+    const int hj_len = 2 * P.n_hj;
+
+    // mode tables and block tallies
+    for (int i = threadIdx.x; i < n_modes; i += blockDim.x) {
+        R lam, vg;
+        load_props<R>(P.props, (uint32_t)i, lam, vg);
+        s_props[2 * i] = lam;
+        s_props[2 * i + 1] = vg;
+        s_scat[i] = P.alias_scat[i];
+    }
+    for (int i = threadIdx.x; i < prof_len; i += blockDim.x) s_prof[i] = 0.0;
+    for (int i = threadIdx.x; i < hj_len; i += blockDim.x) s_hj[i] = 0.0;
+    __syncthreads();
+
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    EmitBuffer<R>& buf = s_buf[threadIdx.x >> 5];
+    const uint32_t N = P.n_particles;
+    const R L = (R)P.L;
+    const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, rad = (R)P.radius, rad2 = (R)(P.radius * P.radius);
+    const R big = M::big();
+
+    // particle state
+    R x = 0, y = 0, z = 0, ox = 0, oy = 0, oz = 1, t = 0, lam = 1, vg = 1;
+    R Lacc = 0, hrun = 0, x0 = 0, t0 = 0;
+    uint32_t pid = 0, n_seg = 0, n_scat = 0, n_wall = 0, n_per = 0, mode0 = 0;
+    int cy = 0, cz = 0, sign = 1, fate = FATE_MAX_EVENTS;
+    bool alive = false, pending = false;
+
+    // lane accumulators
+    Acc<R> acc_sL, acc_sL2;
+    uint32_t c_part = 0, c_seg = 0, c_scat = 0, c_wall = 0, c_per = 0, c_trunc = 0, c_abs = 0;
+    uint32_t flags = 0;
+
+    int cnt = 0;         // emission buffer fill (warp-uniform)
+    bool qdone = false;  // particle queue exhausted (warp-uniform)
+
+    for (;;) {
+        const unsigned dead = __ballot_sync(FULL, !alive);
+        if (dead) {
+            if (pending) {  // flush the finished particle (step V totals)
+                const R sL = (R)sign * Lacc;
+                acc_sL.add(sL);
+                acc_sL2.add(sL * sL);
+                c_part += 1;
+                c_seg += n_seg;
+                c_scat += n_scat;
+                c_wall += n_wall;
+                c_per += n_per;
+                c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS) ? 1u : 0u;
+                c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
+                if (P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
+                    atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
+                    atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
+                }
+                if (P.records) {
+                    le_mc_particle rec;
+                    rec.sign = (int8_t)sign;
+                    rec.fate = (int8_t)fate;
+                    rec.pad = 0;
+                    rec.n_seg = n_seg;
+                    rec.n_scat = n_scat;
+                    rec.n_wall = n_wall;
+                    rec.n_periodic = n_per;
+                    rec.mode0 = mode0;
+                    rec.L_axis = (double)Lacc;
+                    rec.x0 = (double)x0;
+                    rec.t0 = (double)t0;
+                    P.records[pid] = rec;
+                }
+                pending = false;
+            }
+            const int need = __popc(dead);
+            if (cnt < need && !qdone) {
+                // step I for a batch of 32 consecutive particle ids, whole warp
+                unsigned long long base = 0;
+                if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), 32ull);
+                base = __shfl_sync(FULL, base, 0);
+                int n_new = 0;
+                if (base < N) n_new = (int)min((unsigned long long)32, (unsigned long long)N - base);
+                if (base + 32ull >= N) qdone = true;
+                if (lane < n_new) {
+                    const uint32_t id = (uint32_t)base + (uint32_t)lane;
+                    R ex, ey, ez, eox, eoy, eoz, et;
+                    uint32_t em, ecy, ecz;
+                    int es;
+                    if (!emit_particle<R, GEOM, SRC>(P, rk, P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es, ecy, ecz))
+                        flags |= FLAG_REJECTION_EXHAUSTED;
+                    const int slot = cnt + lane;
+                    buf.x[slot] = ex; buf.y[slot] = ey; buf.z[slot] = ez;
+                    buf.ox[slot] = eox; buf.oy[slot] = eoy; buf.oz[slot] = eoz;
+                    buf.t[slot] = et;
+                    buf.pid[slot] = id;
+                    buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
+                    buf.cell[slot] = ecy | (ecz << 16);
+                }
+                cnt += n_new;
+                __syncwarp();
+            }
+            if (!alive) {
+                const int rank = __popc(dead & lanemask_lt);
+                if (rank < cnt) {
+                    const int slot = cnt - 1 - rank;
+                    x = buf.x[slot]; y = buf.y[slot]; z = buf.z[slot];
+                    ox = buf.ox[slot]; oy = buf.oy[slot]; oz = buf.oz[slot];
+                    t = buf.t[slot];
+                    pid = buf.pid[slot];
+                    const uint32_t ms = buf.mode_sign[slot];
+                    mode0 = ms & 0x7FFFFFFFu;
+                    sign = (ms >> 31) ? -1 : 1;
+                    const uint32_t cell = buf.cell[slot];
+                    cy = (int)(cell & 0xFFFFu);
+                    cz = (int)(cell >> 16);
+                    lam = s_props[2 * mode0];
+                    vg = s_props[2 * mode0 + 1];
+                    x0 = x;
+                    t0 = t;
+                    Lacc = 0;
+                    hrun = 0;
+                    n_seg = n_scat = n_wall = n_per = 0;
+                    alive = true;
+                }
+            }
+            cnt -= min(cnt, need);
+            __syncwarp();
+            if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
+        }
+        if (!alive) continue;
+
+        // ---- one segment: steps II-VI ------------------------------------
+        const uint4 r = philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, P.inst), rk);
+        // step II: flight to the next relaxation event (as a length)
+        const R ell = lam * M::neg_log(M::uniform(r.x));
+        // step III: first boundary along the ray
+        R d_b = big;
+        int kind = HIT_NONE;
+        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            if (ox > R(0)) { d_b = M::div(L - x, ox); kind = HIT_XHI; }
+            else if (ox < R(0)) { d_b = M::div(x, -ox); kind = HIT_XLO; }
+        }
+        if constexpr (GEOM == LE_MC_GEOM_POROUS) {
+            if (rad > R(0)) {
+                const R ry = y - half, rz = z - half;
+                const R a = oy * oy + oz * oz;
+                const R b = ry * oy + rz * oz;
+                const R c = ry * ry + rz * rz - rad2;
+                if (a > R(0) && b < R(0)) {
+                    const R disc = b * b - a * c;
+                    if (disc >= R(0)) {
+                        R tc = M::div(c, M::sqrt_(disc) - b);
+                        tc = fmax(tc, R(0));
+                        if (tc < d_b) { d_b = tc; kind = HIT_CYL; }
+                    }
+                }
+            }
+            if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
+            else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
+            if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
+            else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
+        }
+        const bool hit = (kind != HIT_NONE) && (d_b <= ell);
+        const R seg = hit ? d_b : ell;
+        R x_new = x + ox * seg;
+        if (hit && kind == HIT_XLO) x_new = R(0);
+        if (hit && kind == HIT_XHI) x_new = L;
+
+        // step V: contribution of the segment
+        if constexpr (TRANSIENT) {
+            const R dts = (R)P.sample_dt;
+            const R t_b = t + seg / vg;
+            const R t_end = fmin(t_b, (R)P.t_final);
+            int k = (int)ceil(t / dts - R(0.5));
+            k = max(k, 0);
+            const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
+            const int wy = cy % P.cells_y, wz = cz % P.cells_z;
+            const R Yc = (R)(wy < 0 ? wy + P.cells_y : wy) * pitch;
+            const R Zc = (R)(wz < 0 ? wz + P.cells_z : wz) * pitch;
+            for (; k < P.n_samples; ++k) {
+                const R ts = ((R)k + R(0.5)) * dts;
+                if (ts < t) continue;
+                if (ts >= t_b || ts > t_end) break;
+                const R d = vg * (ts - t);
+                const R px = x + ox * d, py = Yc + (y + oy * d), pz = Zc + (z + oz * d);
+                int ix = (int)M::floor_(px / L * (R)P.gx);
+                int iy = (int)M::floor_(py / Dy * (R)P.gy);
+                int iz = (int)M::floor_(pz / Dz * (R)P.gz);
+                ix = min(max(ix, 0), P.gx - 1);
+                iy = min(max(iy, 0), P.gy - 1);
+                iz = min(max(iz, 0), P.gz - 1);
+                const size_t cell = (((size_t)k * P.gz + iz) * P.gy + iy) * P.gx + ix;
+                atomicAdd(&P.grid[cell], sign);
+            }
+        }
+        if constexpr (PROFILE) {
+            // time and x-displacement spent in each bin along x (slab)
+            const int nb = P.n_bins_x;
+            const R dx = L / (R)nb;
+            const int g = (int)(pid % (uint32_t)P.n_batch);
+            const size_t stride = (size_t)nb + 1;
+            double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
+            double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
+            double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
+            double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
+            const R lo = fmin(x, x_new), hi = fmax(x, x_new);
+            int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
+            k0 = min(max(k0, 0), nb - 1);
+            k1 = min(max(k1, 0), nb - 1);
+            const double s = (double)sign;
+            if (ox == R(0)) {
+                atomicAdd(&Td[k0], s * (double)(seg / vg));
+            } else {
+                const R w = R(1) / (vg * fabs(ox));  // time per unit x
+                const R qs = ox > R(0) ? R(1) : R(-1);
+                if (k0 == k1) {
+                    const R len = hi - lo;
+                    atomicAdd(&Td[k0], s * (double)(len * w));
+                    atomicAdd(&qd[k0], s * (double)(len * qs));
+                } else {
+                    const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
+                    const R lb = hi - (R)k1 * dx;        // partial last bin
+                    atomicAdd(&Td[k0], s * (double)(la * w));
+                    atomicAdd(&qd[k0], s * (double)(la * qs));
+                    atomicAdd(&Td[k1], s * (double)(lb * w));
+                    atomicAdd(&qd[k1], s * (double)(lb * qs));
+                    if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
+                        atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
+                        atomicAdd(&Tr[k1], -s * (double)(dx * w));
+                        atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
+                        atomicAdd(&qr[k1], -s * (double)(dx * qs));
+                    }
+                }
+            }
+        }
+        const R dL = AXIS_X ? (x_new - x) : oz * seg;
+        Lacc += dL;
+        hrun += dL;
+
+        // steps IVa / IVb: move, then wall response or relaxation event
+        x = x_new;
+        if constexpr (GEOM == LE_MC_GEOM_POROUS) {
+            y += oy * seg;
+            z += oz * seg;
+        }
+        if constexpr (TRANSIENT) t += seg / vg;
+        ++n_seg;
+        const R u2 = M::uniform(r.z);
+        R sn, cs;
+        M::sincos_2pi(M::uniform(r.w), &sn, &cs);
+        bool absorbed = false;
+        if (hit) {
+            int wall = -1;
+            if (kind == HIT_XLO) wall = P.wall_lo;
+            else if (kind == HIT_XHI) wall = P.wall_hi;
+            else if (kind == HIT_CYL) wall = P.pore_wall;
+            if (wall >= 0) {
+                ++n_wall;
+                if (wall == LE_MC_WALL_BLACK) {
+                    absorbed = true;
+                } else if (kind != HIT_CYL) {
+                    if (wall == LE_MC_WALL_SPECULAR) {
+                        ox = -ox;
+                    } else {  // Lambertian about the inward normal +-x
+                        const R mu = M::sqrt_(u2);
+                        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+                        ox = (kind == HIT_XLO) ? mu : -mu;
+                        oy = st * cs;
+                        oz = st * sn;
+                    }
+                } else {
+                    const R ny = (y - half) / rad, nz = (z - half) / rad;
+                    if (wall == LE_MC_WALL_SPECULAR) {
+                        const R dn = oy * ny + oz * nz;
+                        oy -= R(2) * dn * ny;
+                        oz -= R(2) * dn * nz;
+                    } else {  // Lambertian about the normal pointing into the solid
+                        const R mu = M::sqrt_(u2);
+                        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+                        ox = st * cs;
+                        oy = mu * ny - st * sn * nz;
+                        oz = mu * nz + st * sn * ny;
+                    }
+                }
+            } else {  // periodic face of the unit cell: re-insert opposite
+                ++n_per;
+                if (kind == HIT_YHI) { y = R(0); ++cy; }
+                else if (kind == HIT_YLO) { y = pitch; --cy; }
+                else if (kind == HIT_ZHI) { z = R(0); ++cz; }
+                else { z = pitch; --cz; }
+            }
+        } else {
+            // step IVb: (omega, p) from normalised Eq. 2, isotropic direction, sign kept
+            ++n_scat;
+            if (P.n_hj > 0) {
+                if (n_scat - 1u < (uint32_t)P.n_hj) {
+                    atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
+                    atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
+                }
+                hrun = R(0);
+            }
+            const uint32_t mode = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+            lam = s_props[2 * mode];
+            vg = s_props[2 * mode + 1];
+            const R mu = R(2) * u2 - R(1);
+            const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+            ox = st * cs;
+            oy = st * sn;
+            oz = mu;
+        }
+        // step VI and truncation
+        if (absorbed) { fate = FATE_ABSORBED; alive = false; }
+        else if (TRANSIENT && t > (R)P.t_final) { fate = FATE_T_FINAL; alive = false; }
+        else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
+        else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
+        if (!alive) pending = true;
+    }
+
+    // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
+    double v0 = acc_sL.value(), v1 = acc_sL2.value();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        v0 += __shfl_xor_sync(FULL, v0, o);
+        v1 += __shfl_xor_sync(FULL, v1, o);
+    }
+    unsigned long long red[CNT_N] = {c_part, c_seg, c_scat, c_wall, c_per, c_trunc, c_abs};
+#pragma unroll
+    for (int i = 0; i < CNT_N; ++i)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) red[i] += __shfl_xor_sync(FULL, red[i], o);
+    const uint32_t fl = __reduce_or_sync(FULL, flags);
+    if (lane == 0) {
+        atomicAdd(&P.sums[0], v0);
+        atomicAdd(&P.sums[1], v1);
+#pragma unroll
+        for (int i = 0; i < CNT_N; ++i)
+            if (red[i]) atomicAdd(&P.counters[i], red[i]);
+        if (fl) atomicOr(P.flags, fl);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < prof_len; i += blockDim.x)
+        if (s_prof[i] != 0.0) atomicAdd(&P.prof[i], s_prof[i]);
+    for (int i = threadIdx.x; i < hj_len; i += blockDim.x)
+        if (s_hj[i] != 0.0) atomicAdd(&P.hj[i], s_hj[i]);
+}
+
+// Dynamic shared memory of one block.
+template <typename R>
+inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_len)
+{
+    size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
+    off = (off + 15) & ~(size_t)15;
+    off += (size_t)(threads / 32) * sizeof(EmitBuffer<R>);
+    off += (size_t)prof_len * sizeof(double);
+    off += (size_t)hj_len * sizeof(double);
+    return off;
+}
+
+}  // namespace lemc

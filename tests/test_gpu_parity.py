@@ -1,0 +1,249 @@
+"""GPU parity: the CUDA tracer (through the C ABI) against the FP64 oracle.
+
+* FP64 runs of single-mode materials follow the oracle's trajectories exactly
+  (same counter-based random stream, same draw rules, same geometry), so they
+  are compared particle by particle: sign, fate and event counts bit-exact,
+  path lengths to 1e-12, transient grid counts bit-exact.
+* Multi-mode and FP32 runs are compared statistically: |G - O| <= 3 sigma
+  (sigma from both standard errors), and against the closed-form pins with a
+  relative bias below 1e-3 at sizes where 3 sigma < 1e-3.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_1206_3316_gb300 import build as B
+    B.build()
+    import paper_1206_3316_gb300 as pkg
+    return pkg
+
+
+def _z(g, o, key):
+    return abs(g[key] - o[key]) / np.hypot(g[key + "_se"], o[key + "_se"])
+
+
+def _same_particles(gr, orr, atol=1e-12):
+    for f in ("sign", "fate", "n_seg", "n_scat", "n_wall", "n_periodic", "mode0"):
+        assert np.array_equal(gr[f], orr[f]), f
+    np.testing.assert_allclose(gr["L_axis"], orr["L_axis"], rtol=0, atol=atol)
+    np.testing.assert_allclose(gr["x0"], orr["x0"], rtol=0, atol=atol)
+    np.testing.assert_allclose(gr["t0"], orr["t0"], rtol=1e-12, atol=0)
+
+
+# ---------------------------------------------------------------- generator
+def test_philox_bit_exact(P, oracle):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key = (0x12345678, 0x9ABCDEF0)
+    got = P.le_mc_philox(ctr, *key)
+    ref = np.array([oracle.philox(c, key) for c in ctr], dtype=np.uint32)
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("which", ["emit", "scatter"])
+def test_alias_sampling_matches_pdf(P, analytic, which):
+    from scipy import stats
+    mat = W.SILICON_LIKE
+    _, v, tau, C = analytic.mode_table(mat)
+    w = C * v if which == "emit" else C / tau
+    p = w / w.sum()
+    h = P.le_mc_create_material(P.material_desc(mat))
+    try:
+        n = 4_000_000
+        words = np.random.default_rng(2).integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+        modes = P.le_mc_sample_modes(h, which, words)
+    finally:
+        P.le_mc_destroy_material(h)
+    assert modes.min() >= 0 and modes.max() < p.size
+    counts = np.bincount(modes, minlength=p.size)
+    e, o = [], []
+    acc_e = acc_o = 0.0
+    for pe, co in zip(p * n, counts):
+        acc_e += pe
+        acc_o += co
+        if acc_e >= 20:
+            e.append(acc_e)
+            o.append(acc_o)
+            acc_e = acc_o = 0.0
+    e, o = np.array(e), np.array(o)
+    chi2 = ((o - e) ** 2 / e).sum()
+    assert stats.chi2.sf(chi2, len(e) - 1) > 1e-4
+
+
+# ------------------------------------------------ per-particle, FP64, gray
+@pytest.mark.parametrize("n", [1, 33, 5000])
+def test_gray_slab_per_particle(P, oracle, n):
+    prob = W.gray_slab(n_particles=n, n_bins=50)
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"])
+    for k in ("particles", "segments", "scatters", "wall_hits", "absorbed", "truncated"):
+        assert g[k] == o[k], k
+    assert g["psi"] == pytest.approx(o["psi"], abs=1e-12)
+    np.testing.assert_allclose(g["T"], o["T"], rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(g["q"], o["q"], rtol=1e-9, atol=1e-12)
+
+
+def test_gray_slab_mixed_walls_per_particle(P, oracle):
+    for walls in (("black", "diffuse"), ("specular", "black")):
+        prob = W.gray_slab(n_particles=3000, n_bins=0, walls=walls, dT=(1.0, -0.5))
+        prob["run"]["max_events"] = 500
+        g = P.simulate(prob, record_particles=True)
+        o = oracle.run(prob, record_particles=True)
+        _same_particles(g["particles_rec"], o["particles_rec"])
+
+
+def test_gray_film_per_particle(P, oracle):
+    prob = W.silicon_film(n_particles=4000, thickness=0.7, material=dict(W.GRAY_UNIT), precision="fp64",
+                          max_scatter=12, max_events=100, dTdz=-1.0, n_hj=16)
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"])
+    assert g["kappa"] == pytest.approx(o["kappa"], rel=1e-10)
+    np.testing.assert_allclose(g["H"], o["H"], rtol=1e-9, atol=1e-15)
+
+
+def test_gray_porous_per_particle(P, oracle):
+    prob = W.porous_film(n_particles=3000, precision="fp64", material=dict(W.GRAY_UNIT, tau=2e-8, v=1.0),
+                         max_events=300, max_scatter=20)
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"], atol=1e-18)
+    assert g["periodic"] == o["periodic"] > 0
+    assert g["kappa"] == pytest.approx(o["kappa"], rel=1e-9)
+
+
+def test_gray_pulse_grid_bit_exact(P, oracle):
+    prob = W.porous_pulse(n_particles=2000, precision="fp64", grid=(4, 12, 12), n_samples=40,
+                          sample_dt=25e-12, t_final=1e-9, material=dict(W.GRAY_UNIT, tau=1e-11, v=3000.0))
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"], atol=1e-18)
+    assert np.array_equal(g["grid"].astype(np.int64), o["grid"])
+
+
+# ----------------------------------------------------- statistical parity
+def test_silicon_film_fp32_vs_oracle(P, oracle, analytic):
+    prob = W.silicon_film(n_particles=1_000_000, precision="fp32")
+    g = P.simulate(prob)
+    o = oracle.run(W.with_run(prob, precision="fp64"))
+    assert _z(g, o, "kappa") < 3.0
+    assert abs(g["segments"] / o["segments"] - 1) < 0.01
+    pin = analytic.kappa_film(W.SILICON_LIKE, 100e-9)
+    assert abs(g["kappa"] - pin) < 3.0 * g["kappa_se"]
+
+
+def test_silicon_film_fp64_multimode_vs_oracle(P, oracle):
+    prob = W.silicon_film(n_particles=300_000, precision="fp64", n_hj=8)
+    g = P.simulate(prob)
+    o = oracle.run(prob)
+    assert _z(g, o, "kappa") < 3.0
+    z = np.abs(g["H"] - o["H"]) / np.hypot(g["H_se"], o["H_se"])
+    assert np.max(z) < 4.0
+
+
+def test_nongray_slab_fp32_vs_pin(P, analytic):
+    mat = dict(W.SILICON_LIKE, n_bins=10)
+    L = 100e-9
+    _, v, tau, C = analytic.mode_table(mat)
+    pin = analytic.slab_multimode_psi(v * tau, C * v, C / tau, L, M=100)
+    prob = W.gray_slab(n_particles=4_000_000, n_bins=0, precision="fp32")
+    prob["material"] = mat
+    prob["geometry"]["L"] = L
+    g = P.simulate(prob)
+    assert abs(g["psi"] - pin) < 3.0 * g["psi_se"]
+
+
+def test_porous_fp32_vs_oracle(P, oracle):
+    prob = W.porous_film(n_particles=400_000, precision="fp32")
+    g = P.simulate(prob)
+    o = oracle.run(W.with_run(prob, precision="fp64"))
+    assert _z(g, o, "kappa") < 3.0
+    assert abs(g["periodic"] / o["periodic"] - 1) < 0.02
+
+
+def test_pulse_fp32_energy_conservation_and_oracle(P, oracle):
+    prob = W.porous_pulse(n_particles=50_000, grid=(4, 12, 12), n_samples=40, sample_dt=25e-12, t_final=1e-9)
+    g = P.simulate(prob, record_particles=True)
+    t0 = g["particles_rec"]["t0"]
+    ts = (np.arange(40) + 0.5) * 25e-12
+    emitted = np.array([(t0 <= t).sum() for t in ts])
+    assert np.array_equal(g["grid"].reshape(40, -1).sum(axis=1), emitted)
+    o = oracle.run(W.with_run(prob, precision="fp64"))
+    # per-sample depth profile (sum over y, z): Poisson-level agreement
+    gd = g["grid"].sum(axis=(2, 3)).astype(np.float64)
+    od = o["grid"].sum(axis=(2, 3)).astype(np.float64)
+    m = (gd + od) > 50
+    z = np.abs(gd - od)[m] / np.sqrt(gd + od)[m]
+    assert np.mean(z ** 2) < 3.0
+
+
+# ------------------------------------------- full size, launch invariance
+def test_film_full_size_bias_below_one_per_mille(P, analytic):
+    # 3 sigma < 1e-3 kappa needs ~5e8 particles of the 100 nm film
+    prob = W.silicon_film(n_particles=500_000_000, precision="fp32")
+    g = P.simulate(prob)
+    pin = analytic.kappa_film(W.SILICON_LIKE, 100e-9)
+    assert 3.0 * g["kappa_se"] < 1e-3 * pin
+    assert abs(g["kappa"] - pin) < 3.0 * g["kappa_se"]
+    assert g["device_flags"] == 0
+
+
+def test_gray_slab_full_size_bias_below_one_per_mille(P, analytic):
+    pin = analytic.slab_solution(1.0, n_bins=50, M=200)["psi"]
+    for prec in ("fp64", "fp32"):
+        g = P.simulate(W.gray_slab(n_particles=100_000_000, n_bins=0, precision=prec))
+        assert 3.0 * g["psi_se"] < 1e-3 * pin
+        assert abs(g["psi"] - pin) < 3.0 * g["psi_se"], prec
+
+
+def test_launch_shape_does_not_change_results(P):
+    prob = W.silicon_film(n_particles=100_003, precision="fp32")
+    prob["run"]["record_particles"] = True
+    outs = []
+    for launch in ({"threads_per_block": 64, "blocks_per_sm": 1}, {"threads_per_block": 512},
+                   {"threads_per_block": 256, "blocks_per_sm": 2}):
+        outs.append(P.simulate(prob, record_particles=True, launch=launch))
+    for o in outs[1:]:
+        assert np.array_equal(o["particles_rec"], outs[0]["particles_rec"])
+        for k in ("segments", "scatters", "wall_hits", "truncated"):
+            assert o[k] == outs[0][k]
+        assert o["kappa"] == pytest.approx(outs[0]["kappa"], rel=1e-9)
+
+
+def test_empty_run(P):
+    g = P.simulate(W.silicon_film(n_particles=0))
+    assert g["particles"] == 0 and g["segments"] == 0 and g["kernel_launches"] == 0
+    assert g["kappa"] == 0.0
+
+
+def test_invalid_run_rejected(P):
+    mat = P.le_mc_create_material(P.material_desc(W.GRAY_UNIT))
+    geo = P.le_mc_create_geometry(P.geometry_desc({"kind": "planes", "L": 1.0}))
+    try:
+        bad = [W.gray_slab(1, n_bins=0)["source"] | {"dT_lo": 0.0, "dT_hi": 0.0},
+               {"kind": "pulse", "sigma_x": 1, "sigma_t": 1, "energy": 1}]
+        for src in bad:
+            with pytest.raises(P.LeMcError) as e:
+                P.le_mc_run(mat, geo, P.run_desc(src, W.gray_slab(10)["run"]))
+            assert e.value.status == 1
+        run = dict(W.gray_slab(10)["run"], max_events=0)
+        with pytest.raises(P.LeMcError):
+            P.le_mc_run(mat, geo, P.run_desc(W.gray_slab(10)["source"], run))
+        run = dict(W.gray_slab(10)["run"], n_particles=2 ** 32)
+        with pytest.raises(P.LeMcError):
+            P.le_mc_run(mat, geo, P.run_desc(W.gray_slab(10)["source"], run))
+    finally:
+        P.le_mc_destroy_geometry(geo)
+        P.le_mc_destroy_material(mat)

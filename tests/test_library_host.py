@@ -1,0 +1,137 @@
+"""CPU tests of the CUDA library's host side: it loads without a GPU, exports
+every entry point that include/le_mc.h declares, its structs match the
+binding, and its host logic (mode tables, alias tables, validation) agrees
+with the oracle and with exact probabilities.  No compute call needs a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1206_3316_gb300 import build as B
+    B.build()
+    import paper_1206_3316_gb300 as pkg
+    return pkg
+
+
+def _declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            names += re.findall(r"^LE_MC_API\s+[\w\s\*]+?\b(le_mc_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_symbol(P):
+    declared = _declared_functions()
+    assert len(declared) >= 16
+    for name in declared:
+        assert hasattr(P.lib, name), name
+    # and the binding wraps each of them
+    from paper_1206_3316_gb300 import _binding
+    assert set(declared) <= set(_binding.SIGNATURES)
+
+
+def test_struct_layouts(P):
+    from paper_1206_3316_gb300 import _binding as Bd
+    import ctypes
+    for i, cls in enumerate((Bd.MaterialDesc, Bd.GeometryDesc, Bd.RunDesc, Bd.Tallies, Bd.Particle)):
+        assert P.lib.le_mc_struct_size(i) == ctypes.sizeof(cls)
+    assert Bd.PARTICLE_DTYPE.itemsize == ctypes.sizeof(Bd.Particle)
+    assert P.le_mc_abi_version() == 1
+
+
+def test_no_device_is_reported_not_faked(P):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(P.LeMcError) as e:
+        P.le_mc_create_material(P.material_desc(W.GRAY_UNIT))
+    assert e.value.status in (3, 7)
+
+
+def test_mode_table_matches_oracle(P, oracle):
+    for mat in (W.SILICON_LIKE, dict(W.SILICON_LIKE, T_eq=120.0, n_bins=333), W.GRAY_UNIT):
+        om, v, tau, C = P.le_mc_material_table(P.material_desc(mat))
+        prob = {"material": mat, "geometry": {"kind": "bulk"}, "source": {"kind": "gradient", "dTdz": -1.0},
+                "run": W.silicon_film(1)["run"]}
+        o = oracle.material(prob)
+        for a, b in zip((om, v, tau, C), o):
+            np.testing.assert_allclose(a, b, rtol=1e-12, atol=0)
+
+
+def _alias_pdf(thr, al):
+    n = thr.size
+    keep = thr.astype(np.float64) / 2.0 ** 32
+    keep[thr == 0xFFFFFFFF] = 1.0
+    pdf = np.zeros(n)
+    np.add.at(pdf, np.arange(n), keep / n)
+    np.add.at(pdf, al, (1.0 - keep) / n)
+    return pdf
+
+
+@pytest.mark.parametrize("which", ["emit", "scatter", "random", "one", "spiky"])
+def test_alias_table_is_exact(P, analytic, which):
+    rng = np.random.default_rng(5)
+    if which in ("emit", "scatter"):
+        _, v, tau, C = analytic.mode_table(W.SILICON_LIKE)
+        w = C * v if which == "emit" else C / tau
+    elif which == "random":
+        w = rng.exponential(size=777)
+    elif which == "one":
+        w = np.array([3.0])
+    else:
+        w = np.zeros(64)
+        w[[0, 17, 63]] = [1e-12, 1.0, 5.0]
+    thr, al = P.le_mc_alias_table(w)
+    assert np.all(al < w.size)
+    pdf = _alias_pdf(thr, al)
+    np.testing.assert_allclose(pdf, w / w.sum(), rtol=0, atol=2.0 ** -31)
+    assert abs(pdf.sum() - 1.0) < 1e-12
+
+
+def test_alias_draw_rule_reproduces_pdf(P):
+    # the device rule on every (column, low-word) cell of a coarse grid of words
+    w = np.array([0.1, 0.0, 2.5, 1.0, 0.4])
+    thr, al = P.le_mc_alias_table(w)
+    words = (np.arange(1 << 16, dtype=np.uint64) << np.uint64(16)) + np.uint64(0x7FFF)
+    m = words * np.uint64(w.size)
+    j = (m >> np.uint64(32)).astype(np.int64)
+    lo = (m & np.uint64(0xFFFFFFFF)).astype(np.uint64)
+    modes = np.where(lo < thr[j].astype(np.uint64), j, al[j])
+    freq = np.bincount(modes, minlength=w.size) / words.size
+    np.testing.assert_allclose(freq, w / w.sum(), atol=5e-5)
+    assert freq[1] == 0.0
+
+
+def test_invalid_descriptors_rejected(P):
+    bad_geo = [
+        {"kind": "planes", "L": 0.0},
+        {"kind": "planes", "L": float("nan")},
+        {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.6},
+        {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.2, "pore_wall": "black"},
+        {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.2, "cells_y": 0},
+    ]
+    for g in bad_geo:
+        with pytest.raises(P.LeMcError) as e:
+            P.le_mc_create_geometry(P.geometry_desc(g))
+        assert e.value.status == 1, g
+    h = P.le_mc_create_geometry(P.geometry_desc({"kind": "planes", "L": 1e-7}))
+    P.le_mc_destroy_geometry(h)
+    bad_mat = [dict(W.GRAY_UNIT, tau=0.0), dict(W.SILICON_LIKE, n_bins=5000), dict(W.SILICON_LIKE, T_eq=-1.0)]
+    for m in bad_mat:
+        with pytest.raises(P.LeMcError) as e:
+            P.le_mc_material_table(P.material_desc(m))
+        assert e.value.status == 1
+    with pytest.raises(P.LeMcError):
+        P.le_mc_alias_table(np.zeros(4))
+    with pytest.raises(P.LeMcError):
+        P.le_mc_alias_table(np.array([1.0, -1.0]))
