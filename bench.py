@@ -1,0 +1,386 @@
+"""Benchmark: free-flight segments per second of the GB300 tracer.
+
+Workload (one step): the silicon-like thin film, 100 nm, diffuse walls,
+uniform gradient along z, 3 x 1000 modes at 300 K, 1e7 particles, 40
+scattering events / 4096 segments per particle at most, FP32 trajectories
+with FP64 tallies.  One step traces every particle from emission to
+termination (steps I-VI of the trajectory algorithm) in one le_mc_run.
+
+Printed JSON line (rank 0):
+  value        segments/s over the K timed steps, device-timed with CUDA events
+               on the launching stream, material tables resident in HBM
+  e2e          the same metric through the public C ABI with host descriptors:
+               material build + upload, run, read-back, destroy, every step
+  roofline     dominant kernel against the ALU-issue peak (bound "alu")
+  cpu_baseline the FP64 oracle on this host's cores over a bounded sample
+  clocks       nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the FP64 CPU oracle (the reference for this
+method) on the same workload and metric, one bounded sample per step.
+Under torchrun (--gpus N > 1) each rank traces its own independent instance
+(weak scaling, no data-path collective); the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+N_PARTICLES = 10_000_000
+METRIC = "free-flight segments/s per GB300 (plain vs batched); p50/p99 latency at 1% std error"
+UNIT = "segments/s"
+WORKLOAD = ("silicon-like thin film 100 nm, diffuse walls, gradient along z, 3x1000 modes at 300 K, "
+            "1e7 particles, K_s=40, K_e=4096, FP32 trajectories / FP64 tallies")
+
+# Algorithmic lane operations per free-flight segment of the film kernel
+# (counted from the algorithm, not from the compiled code):
+#   Philox4x32-10: 10 rounds x (2 wide multiplies + 2 three-input XORs)  40
+#   three uniforms from the random words (shift/or + add)                   6
+#   flight length -Lambda ln u (log2 + 2 multiplies)                        3
+#   wall distance (select numerator, reciprocal, multiply, compare, min)    7
+#   advance x, snap at walls, accumulate L_z                                4
+#   new direction (sincos, sqrt pair, three components, selects)           14
+#   Eq. 2 mode redraw on scattering (wide multiply, 2 loads, compare,
+#     select), weighted by the scattering share of segments (~0.8)          4
+#   event counters and termination tests                                    6
+OPS_PER_SEGMENT = 84
+LANES_PER_SM = 128  # FP32/INT32 lanes issuing one operation per clock
+
+
+def _sha_kernel_sources():
+    h = hashlib.sha256()
+    for f in ("trace_kernel.cuh", "device_math.cuh"):
+        with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of the film kernel from the committed ncu summary,
+    or None if the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "trace_kernel_film_fp32_1e7.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m_h = re.search(r"kernel_sources_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m_b or not m_h or m_h.group(1) != _sha_kernel_sources():
+        return None
+    return float(m_b.group(1))
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"sm_max_mhz": 2070.0, "hbm_gbs": 6800.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.device_index = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device_index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rank_problem(problem, rank, world):
+    """Weak scaling: rank r traces its own independent instance of the
+    workload (instance id r of the counter-based stream)."""
+    p = W.with_run(problem, instance_id=int(problem["run"].get("instance_id", 0)) * world + rank)
+    return p
+
+
+def max_over_ranks(value, dist):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(value, dist):
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_baseline(problem, seconds=12.0):
+    """The FP64 oracle on this host's cores over a bounded sample of the
+    workload (same film, fewer particles)."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    probe = W.with_run(problem, n_particles=20_000, precision="fp64")
+    t0 = time.perf_counter()
+    r = O.run(probe, n_threads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_particle = dt / 20_000
+    n = int(min(max(seconds / per_particle, 20_000), 2 ** 31))
+    sample = W.with_run(problem, n_particles=n, precision="fp64")
+    t0 = time.perf_counter()
+    r = O.run(sample, n_threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": r["segments"] / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} particles of the same film workload, FP64, {dt:.1f} s on {cores} threads"}
+
+
+def run_reference(args, problem, rank, world):
+    """Reference arm: the FP64 CPU oracle, one bounded sample per step."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    probe = W.with_run(problem, n_particles=10_000, precision="fp64")
+    t0 = time.perf_counter()
+    O.run(probe, n_threads=cores)
+    per_particle = max(time.perf_counter() - t0, 1e-4) / 10_000
+    budget = 150.0 / max(args.steps + args.warmup, 1)  # whole run within a few minutes
+    n = int(min(max(budget / per_particle, 10_000), N_PARTICLES))
+    sample = W.with_run(problem, n_particles=n, precision="fp64")
+    for _ in range(args.warmup):
+        O.run(W.with_run(sample, n_particles=min(n, 10_000)), n_threads=cores)
+    segs, elapsed = 0, 0.0
+    for k in range(args.steps):
+        s = W.with_run(sample, seed=sample["run"]["seed"] + k)
+        t0 = time.perf_counter()
+        r = O.run(s, n_threads=cores)
+        elapsed += time.perf_counter() - t0
+        segs += r["segments"]
+    value = segs / elapsed
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_particles_per_step": n,
+                       "note": "FP64 CPU oracle, bounded sample of the workload per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{n} particles per step, {args.steps} steps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--n-particles", type=int, default=N_PARTICLES)
+    ap.add_argument("--threads-per-block", type=int, default=0)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    problem = W.silicon_film(n_particles=args.n_particles, precision="fp32")
+
+    if args.impl == "reference":
+        run_reference(args, problem, rank, world)
+        return
+
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+        dist = tdist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1206_3316_gb300 as P
+    prob = rank_problem(problem, rank, world)
+    launch = {"threads_per_block": args.threads_per_block, "blocks_per_sm": args.blocks_per_sm}
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
+
+    mat = P.le_mc_create_material(P.material_desc(prob["material"]))
+    geo = P.le_mc_create_geometry(P.geometry_desc(prob["geometry"]))
+    rdesc = P.run_desc(prob["source"], prob["run"], launch)
+
+    def step(seed_offset):
+        rdesc.seed = prob["run"]["seed"] + seed_offset
+        return P.le_mc_run(mat, geo, rdesc, stream)
+
+    for w in range(args.warmup):
+        h = step(10_000 + w)
+        P.le_mc_read_tallies(h)
+        P.le_mc_destroy_run(h)
+    torch.cuda.synchronize(dev)
+
+    # ---- device-timed region: K steps, L2 flushed between steps -----------
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    handles = []
+    sampler = ClockSampler(local_rank if world > 1 else int(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or 0))
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with sampler:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            handles.append(step(k))
+            ev[k][1].record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    segs, kern_ms, launches, flags, kappas = 0, [], 0, 0, []
+    for h in handles:
+        t = P.le_mc_read_tallies(h)
+        segs += t["segments"]
+        kern_ms.append(t["kernel_ms"])
+        launches += t["kernel_launches"]
+        flags |= t["device_flags"]
+        kappas.append(t["kappa"])
+        P.le_mc_destroy_run(h)
+    t_dev = sum(step_ms) / 1e3
+    t_max = max_over_ranks(t_dev, dist)
+    segs_all = sum_over_ranks(segs, dist)
+    value = segs_all / t_max
+
+    # ---- end to end through the C ABI, host descriptors and results -------
+    e2e_steps = max(3, min(args.steps, 10))
+    n_modes = 3000
+    h2d = n_modes * (8 + 16 + 8 + 8)  # FP32 + FP64 mode properties, two alias tables
+    d2h = 2 * 8 + 7 * 8 + 2 * 8       # sums, counters, queue head and flags
+    e2e_segs = 0
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(e2e_steps):
+        m = P.le_mc_create_material(P.material_desc(prob["material"]))
+        g = P.le_mc_create_geometry(P.geometry_desc(prob["geometry"]))
+        rd = P.run_desc(prob["source"], W.with_run(prob, seed=prob["run"]["seed"] + 500 + k)["run"], launch)
+        h = P.le_mc_run(m, g, rd, stream)
+        t = P.le_mc_read_tallies(h)
+        e2e_segs += t["segments"]
+        launches += t["kernel_launches"]
+        P.le_mc_destroy_run(h)
+        P.le_mc_destroy_geometry(g)
+        P.le_mc_destroy_material(m)
+    torch.cuda.synchronize(dev)
+    e2e_t = max_over_ranks(time.perf_counter() - t0, dist)
+    e2e_value = sum_over_ranks(e2e_segs, dist) / e2e_t
+
+    P.le_mc_destroy_geometry(geo)
+    P.le_mc_destroy_material(mat)
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    peaks, peak_src = _peaks()
+    sms, name = P.le_mc_device_info()
+    clocks = sampler.summary()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * LANES_PER_SM * sm_mhz * 1e6
+    per_launch_s = statistics.mean(kern_ms) / 1e3
+    segs_per_launch = segs / args.steps
+    achieved = segs_per_launch * OPS_PER_SEGMENT / per_launch_s
+    traffic = _profiled_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_particles": args.n_particles, "form": "plain",
+                   "tallies": "per-particle FP32 sums, FP64 accumulation",
+                   "l2": "flushed between steps (256 MiB write)",
+                   "launch": {"threads_per_block": args.threads_per_block or 256,
+                              "blocks_per_sm": args.blocks_per_sm or "occupancy"},
+                   "kappa_W_per_mK": statistics.mean(kappas), "device": name, "sms": sms,
+                   "wall_s_timed_region": wall},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
+                     "frac": achieved / peak_ops, "traffic": traffic,
+                     "kernel": "trace_kernel<float, PLANES, GRADIENT>",
+                     "ops_per_segment": OPS_PER_SEGMENT,
+                     "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)"},
+        "clocks": clocks,
+        "device_flags": flags,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(problem)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

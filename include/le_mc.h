@@ -174,6 +174,16 @@ typedef struct {
     int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
     int32_t blocks_per_sm;          /* launch shape (0 = library default)        */
     int32_t threads_per_block;      /* 0 = default; multiple of 32, <= 512       */
+    int32_t schedule;               /* particle order: 0 auto, 1 long-first,
+                                     * 2 natural id order.  Long-first serves
+                                     * particles emitted in modes with a mean
+                                     * free path above long_mfp_cut before the
+                                     * rest, so the longest trajectories overlap
+                                     * the bulk instead of trailing it.  Results
+                                     * do not depend on the order (up to FP64
+                                     * summation order).                       */
+    int32_t pad_schedule;
+    double long_mfp_cut;            /* [m]; 0 = 32 L (PLANES, POROUS)            */
 } le_mc_run_desc;
 
 typedef struct le_mc_run_s* le_mc_run_handle;
@@ -206,6 +216,7 @@ typedef struct {
     double psi, psi_se;     /* WALLS: flux / (sum_b C_b v_b / 4 (dT_lo - dT_hi))   */
     uint64_t particles, segments, scatters, wall_hits, periodic, truncated, absorbed;
     double kernel_ms;       /* device time of the trace kernel                    */
+    double prepass_ms;      /* device time of the long-first classification pass  */
     uint32_t kernel_launches; /* kernels this run launched                        */
     uint32_t device_flags;  /* device-side warning bits (0 = none)                */
 } le_mc_tallies;

@@ -62,7 +62,8 @@ class RunDesc(C.Structure):
                 ("grid_nx", C.c_int32), ("grid_ny", C.c_int32), ("grid_nz", C.c_int32), ("n_samples", C.c_int32),
                 ("t_final", C.c_double), ("sample_dt", C.c_double),
                 ("n_hj", C.c_int32), ("record_particles", C.c_int32),
-                ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32)]
+                ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32),
+                ("schedule", C.c_int32), ("pad_schedule", C.c_int32), ("long_mfp_cut", C.c_double)]
 
 
 class Tallies(C.Structure):
@@ -71,7 +72,8 @@ class Tallies(C.Structure):
         "kappa_se", "kappa_solid", "psi", "psi_se")] + [
         (n, C.c_uint64) for n in ("particles", "segments", "scatters", "wall_hits", "periodic",
                                   "truncated", "absorbed")] + [
-        ("kernel_ms", C.c_double), ("kernel_launches", C.c_uint32), ("device_flags", C.c_uint32)]
+        ("kernel_ms", C.c_double), ("prepass_ms", C.c_double), ("kernel_launches", C.c_uint32),
+        ("device_flags", C.c_uint32)]
 
 
 class Particle(C.Structure):
@@ -198,6 +200,8 @@ def run_desc(src, run, launch=None):
     launch = launch or {}
     r.blocks_per_sm = int(launch.get("blocks_per_sm", run.get("blocks_per_sm", 0)))
     r.threads_per_block = int(launch.get("threads_per_block", run.get("threads_per_block", 0)))
+    r.schedule = {"auto": 0, "long_first": 1, "natural": 2}[launch.get("schedule", run.get("schedule", "auto"))]
+    r.long_mfp_cut = float(launch.get("long_mfp_cut", run.get("long_mfp_cut", 0.0)))
     return r
 
 

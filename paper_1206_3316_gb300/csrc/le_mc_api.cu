@@ -19,8 +19,12 @@ cudaError_t launch_trace_f64(const KernelArgs& a, int geom, int src, bool profil
                              size_t smem, cudaStream_t st);
 cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
 cudaError_t occupancy_trace_f64(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
-size_t smem_trace_f32(int n_modes, int threads, int prof_len, int hj_len);
-size_t smem_trace_f64(int n_modes, int threads, int prof_len, int hj_len);
+cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
+                           size_t* bytes);
+cudaError_t smem_trace_f64(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
+                           size_t* bytes);
+cudaError_t launch_classify_f32(const KernelArgs& a, int blocks, cudaStream_t st);
+cudaError_t launch_classify_f64(const KernelArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_philox(const uint4* ctr, uint32_t k0, uint32_t k1, uint4* out, size_t n, cudaStream_t st);
 cudaError_t launch_sample_modes(const uint2* table, int n_modes, const uint32_t* words, int32_t* out, size_t n,
                                 cudaStream_t st);
@@ -83,8 +87,10 @@ struct le_mc_run_s {
     size_t dev_bytes = 0;
     size_t off_sums = 0, off_counters = 0, off_queue = 0, off_flags = 0;
     size_t off_prof = 0, off_hj = 0, off_grid = 0, off_records = 0;
+    size_t off_long_list = 0, off_long_bits = 0, off_long_count = 0;
+    uint32_t long_cap = 0;
     size_t prof_len = 0, hj_len = 0, grid_len = 0;
-    cudaEvent_t ev_start = nullptr, ev_stop = nullptr;
+    cudaEvent_t ev_start = nullptr, ev_mid = nullptr, ev_stop = nullptr;
     bool failed = false;
     bool have_header = false;
     double sums[2] = {0, 0};
@@ -283,9 +289,22 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     off = align_up(off, 256);
     h->off_records = off;
     if (r.record_particles) off += (size_t)r.n_particles * sizeof(le_mc_particle);
+    // long-first schedule (PLANES and POROUS): list + bitmap of long-lived particles
+    const bool long_first = g->desc.kind != LE_MC_GEOM_BULK &&
+                            (r.schedule == 1 || (r.schedule == 0 && r.n_particles >= 4096));
+    if (long_first && r.n_particles > 0) {
+        h->long_cap = (uint32_t)(r.n_particles < (1ull << 20) ? r.n_particles : (1ull << 20));
+        off = align_up(off, 256);
+        h->off_long_list = off; off += (size_t)h->long_cap * sizeof(uint32_t);
+        off = align_up(off, 256);
+        h->off_long_bits = off; off += (size_t)((r.n_particles + 31) / 32) * sizeof(uint32_t);
+        off = align_up(off, 256);
+        h->off_long_count = off; off += sizeof(unsigned long long);
+    }
     h->dev_bytes = align_up(off, 256);
 
     cudaError_t e = cudaEventCreate(&h->ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->ev_mid);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_stop);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->dev, h->dev_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dev, 0, h->dev_bytes, h->stream);
@@ -352,14 +371,22 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
         a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
         a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
     }
+    if (h->long_cap > 0) {
+        P.long_list = reinterpret_cast<uint32_t*>(h->dev + h->off_long_list);
+        P.long_bits = reinterpret_cast<uint32_t*>(h->dev + h->off_long_bits);
+        P.long_count = reinterpret_cast<unsigned int*>(h->dev + h->off_long_count);
+        P.long_cap = h->long_cap;
+        P.lam_cut = r.long_mfp_cut > 0.0 ? r.long_mfp_cut : 32.0 * G.L;
+    }
 
     // launch shape: persistent grid of (SMs x resident blocks)
-    int threads = r.threads_per_block > 0 ? r.threads_per_block : 256;
+    int threads = r.threads_per_block > 0 ? r.threads_per_block : 512;
     if (threads > 512) threads = 512;
-    const size_t smem = fp32 ? smem_trace_f32(m->n_modes, threads, (int)h->prof_len, (int)h->hj_len)
-                             : smem_trace_f64(m->n_modes, threads, (int)h->prof_len, (int)h->hj_len);
+    size_t smem = 0;
+    e = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, threads, (int)h->prof_len, (int)h->hj_len, &smem)
+             : smem_trace_f64(G.kind, r.source, profile, m->n_modes, threads, (int)h->prof_len, (int)h->hj_len, &smem);
     int sms = 0;
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
     if (e == cudaSuccess)
         e = fp32 ? occupancy_trace_f32(G.kind, r.source, profile, threads, smem, &per_sm)
@@ -371,10 +398,15 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     const long long max_blocks = ((long long)r.n_particles + 32LL * (threads / 32) - 1) / (32LL * (threads / 32));
     if (blocks > max_blocks) blocks = (int)max_blocks;
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_start, h->stream);
+    if (e == cudaSuccess && blocks > 0 && h->long_cap > 0) {
+        e = fp32 ? launch_classify_f32(a, sms * 8, h->stream) : launch_classify_f64(a, sms * 8, h->stream);
+        h->launches += 1;
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(h->ev_mid, h->stream);
     if (e == cudaSuccess && blocks > 0) {
         e = fp32 ? launch_trace_f32(a, G.kind, r.source, profile, blocks, threads, smem, h->stream)
                  : launch_trace_f64(a, G.kind, r.source, profile, blocks, threads, smem, h->stream);
-        h->launches = 1;
+        h->launches += 1;
     }
     if (e == cudaSuccess) e = cudaEventRecord(h->ev_stop, h->stream);
     if (e != cudaSuccess) {
@@ -423,9 +455,13 @@ le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out)
     if (s != LE_MC_OK) return s;
     memset(out, 0, sizeof(*out));
     normalize(&h->geo->desc, &h->desc, h->mat->sums, h->sums, h->counters, out);
-    float ms = 0.0f;
-    if (h->launches) cudaEventElapsedTime(&ms, h->ev_start, h->ev_stop);
+    float ms = 0.0f, pre = 0.0f;
+    if (h->launches) {
+        cudaEventElapsedTime(&ms, h->ev_mid, h->ev_stop);
+        cudaEventElapsedTime(&pre, h->ev_start, h->ev_mid);
+    }
     out->kernel_ms = ms;
+    out->prepass_ms = pre;
     out->kernel_launches = h->launches;
     out->device_flags = h->flags;
     return LE_MC_OK;
@@ -499,6 +535,7 @@ le_mc_status le_mc_destroy_run(le_mc_run_handle h)
         if (cudaFreeAsync(h->dev, h->stream) != cudaSuccess) cudaFree(h->dev);
     }
     if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->ev_mid) cudaEventDestroy(h->ev_mid);
     if (h->ev_stop) cudaEventDestroy(h->ev_stop);
     material_release(h->mat);
     geometry_release(h->geo);

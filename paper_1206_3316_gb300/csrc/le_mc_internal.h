@@ -65,6 +65,14 @@ struct TraceParams {
     unsigned long long* counters;  // [CNT_N]
     unsigned int* queue;           // [1]: next particle id
     unsigned int* flags;           // [1]
+    // long-first schedule: ids of particles whose emission mode has a mean
+    // free path above lam_cut, served before the natural order (which then
+    // skips the ids flagged in long_bits); long_list == nullptr disables it
+    uint32_t* long_list;           // [long_cap]
+    uint32_t* long_bits;           // [ceil(n_particles / 32)]
+    unsigned int* long_count;      // [1]
+    uint32_t long_cap;
+    double lam_cut;
 };
 
 // Host helpers (le_mc_host.cpp).

@@ -1,4 +1,4 @@
-// Instantiations and launcher of the float trace kernels (one translation
+// Instantiations and launchers of the float trace kernels (one translation
 // unit per trajectory precision so the two compile in parallel).
 #include <cuda_runtime.h>
 
@@ -25,6 +25,13 @@ cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
+}
+
+template <int G, int S, bool PR>
+cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t* bytes)
+{
+    *bytes = trace_smem_bytes<float, G, S>(n_modes, threads, prof_len, hj_len);
+    return cudaSuccess;
 }
 }  // namespace
 
@@ -56,9 +63,16 @@ cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, si
     LEMC_DISPATCH(occupancy_one, threads, smem, per_sm)
 }
 
-size_t smem_trace_f32(int n_modes, int threads, int prof_len, int hj_len)
+cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
+                            size_t* bytes)
 {
-    return trace_smem_bytes<float>(n_modes, threads, prof_len, hj_len);
+    LEMC_DISPATCH(smem_one, n_modes, threads, prof_len, hj_len, bytes)
+}
+
+cudaError_t launch_classify_f32(const KernelArgs& a, int blocks, cudaStream_t st)
+{
+    classify_kernel<float><<<blocks, 256, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace lemc

@@ -38,28 +38,43 @@ enum { HIT_NONE = 0, HIT_XLO = 1, HIT_XHI = 2, HIT_CYL = 3, HIT_YLO = 4, HIT_YHI
 
 constexpr int kBufSlots = 64;  // emission buffer entries per warp
 
-// Emission buffer of one warp, structure of arrays.
-template <typename R>
+// Fields of the emission buffer that a geometry or source may not need.
+template <typename T, int N>
+struct Slots {
+    T v[N];
+};
+template <typename T>
+struct Slots<T, 0> {};
+
+// Emission buffer of one warp, structure of arrays.  y, z and the unit cell
+// are kept only for POROUS geometries, the emission time only for PULSE.
+template <typename R, bool YZ, bool TIME>
 struct EmitBuffer {
-    R x[kBufSlots], y[kBufSlots], z[kBufSlots];
+    R x[kBufSlots];
     R ox[kBufSlots], oy[kBufSlots], oz[kBufSlots];
-    R t[kBufSlots];
     uint32_t pid[kBufSlots];
     uint32_t mode_sign[kBufSlots];  // mode | (sign < 0) << 31
-    uint32_t cell[kBufSlots];       // cy | cz << 16 (POROUS)
+    Slots<R, YZ ? kBufSlots : 0> y, z;
+    Slots<uint32_t, YZ ? kBufSlots : 0> cell;  // cy | cz << 16
+    Slots<R, TIME ? kBufSlots : 0> t;
 };
 
-// Compensated FP32 sum (Neumaier); plain sum for FP64.
+template <typename R, int GEOM, int SRC>
+using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE>;
+
+// Compensated FP32 sum (Kahan: c carries the part of each addend that the
+// running sum lost); plain sum for FP64.
 template <typename R>
 struct Acc {
     R s = 0, c = 0;
     __device__ __forceinline__ void add(R v)
     {
-        const R t = s + v;
-        c += (fabs(s) >= fabs(v)) ? ((s - t) + v) : ((v - t) + s);
+        const R y = v - c;
+        const R t = s + y;
+        c = (t - s) - y;
         s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 template <>
 struct Acc<double> {
@@ -186,6 +201,8 @@ template <typename R, int GEOM, int SRC, bool PROFILE>
 __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
 {
     using M = DMath<R>;
+    using Buf = BufferOf<R, GEOM, SRC>;
+    constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
     constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
     const TraceParams& P = args.p;
@@ -197,9 +214,10 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     uint2* s_scat = reinterpret_cast<uint2*>(smem + (size_t)n_modes * 2 * sizeof(R));
     size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
     off = (off + 15) & ~(size_t)15;
-    EmitBuffer<R>* s_buf = reinterpret_cast<EmitBuffer<R>*>(smem + off);
+    Buf* s_buf = reinterpret_cast<Buf*>(smem + off);
     const int n_warps = blockDim.x >> 5;
-    off += (size_t)n_warps * sizeof(EmitBuffer<R>);
+    off += (size_t)n_warps * sizeof(Buf);
+    off = (off + 7) & ~(size_t)7;
     double* s_prof = reinterpret_cast<double*>(smem + off);
     const int prof_len = PROFILE ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
     off += (size_t)prof_len * sizeof(double);
@@ -221,8 +239,11 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    EmitBuffer<R>& buf = s_buf[threadIdx.x >> 5];
+    Buf& buf = s_buf[threadIdx.x >> 5];
     const uint32_t N = P.n_particles;
+    // particles served first (long-first schedule), then ids 0..N-1 minus those
+    const uint32_t n_long = P.long_list ? min(*P.long_count, P.long_cap) : 0u;
+    const unsigned long long q_total = (unsigned long long)n_long + N;
     const R L = (R)P.L;
     const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, rad = (R)P.radius, rad2 = (R)(P.radius * P.radius);
     const R big = M::big();
@@ -245,7 +266,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     for (;;) {
         const unsigned dead = __ballot_sync(FULL, !alive);
         if (dead) {
-            if (pending) {  // flush the finished particle (step V totals)
+            if (pending) {  // totals of the finished particle (step V, Eq. 4)
                 const R sL = (R)sign * Lacc;
                 acc_sL.add(sL);
                 acc_sL2.add(sL * sL);
@@ -278,46 +299,66 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                 pending = false;
             }
             const int need = __popc(dead);
-            if (cnt < need && !qdone) {
-                // step I for a batch of 32 consecutive particle ids, whole warp
+            while (cnt < need && !qdone) {
+                // step I for the next 32 queue positions, whole warp
                 unsigned long long base = 0;
                 if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), 32ull);
                 base = __shfl_sync(FULL, base, 0);
-                int n_new = 0;
-                if (base < N) n_new = (int)min((unsigned long long)32, (unsigned long long)N - base);
-                if (base + 32ull >= N) qdone = true;
-                if (lane < n_new) {
-                    const uint32_t id = (uint32_t)base + (uint32_t)lane;
+                if (base + 32ull >= q_total) qdone = true;
+                const unsigned long long q = base + (unsigned long long)lane;
+                uint32_t id = 0;
+                bool valid = false;
+                if (q < n_long) {
+                    id = P.long_list[q];
+                    valid = true;
+                } else if (q < q_total) {
+                    id = (uint32_t)(q - n_long);
+                    valid = !(P.long_list && ((P.long_bits[id >> 5] >> (id & 31u)) & 1u));
+                }
+                const unsigned vmask = __ballot_sync(FULL, valid);
+                if (valid) {
                     R ex, ey, ez, eox, eoy, eoz, et;
                     uint32_t em, ecy, ecz;
                     int es;
                     if (!emit_particle<R, GEOM, SRC>(P, rk, P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es, ecy, ecz))
                         flags |= FLAG_REJECTION_EXHAUSTED;
-                    const int slot = cnt + lane;
-                    buf.x[slot] = ex; buf.y[slot] = ey; buf.z[slot] = ez;
-                    buf.ox[slot] = eox; buf.oy[slot] = eoy; buf.oz[slot] = eoz;
-                    buf.t[slot] = et;
+                    const int slot = cnt + __popc(vmask & lanemask_lt);
+                    buf.x[slot] = ex;
+                    buf.ox[slot] = eox;
+                    buf.oy[slot] = eoy;
+                    buf.oz[slot] = eoz;
                     buf.pid[slot] = id;
                     buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
-                    buf.cell[slot] = ecy | (ecz << 16);
+                    if constexpr (POROUS) {
+                        buf.y.v[slot] = ey;
+                        buf.z.v[slot] = ez;
+                        buf.cell.v[slot] = ecy | (ecz << 16);
+                    }
+                    if constexpr (TRANSIENT) buf.t.v[slot] = et;
                 }
-                cnt += n_new;
+                cnt += __popc(vmask);
                 __syncwarp();
             }
             if (!alive) {
                 const int rank = __popc(dead & lanemask_lt);
                 if (rank < cnt) {
                     const int slot = cnt - 1 - rank;
-                    x = buf.x[slot]; y = buf.y[slot]; z = buf.z[slot];
-                    ox = buf.ox[slot]; oy = buf.oy[slot]; oz = buf.oz[slot];
-                    t = buf.t[slot];
+                    x = buf.x[slot];
+                    ox = buf.ox[slot];
+                    oy = buf.oy[slot];
+                    oz = buf.oz[slot];
                     pid = buf.pid[slot];
                     const uint32_t ms = buf.mode_sign[slot];
+                    if constexpr (POROUS) {
+                        y = buf.y.v[slot];
+                        z = buf.z.v[slot];
+                        const uint32_t cell = buf.cell.v[slot];
+                        cy = (int)(cell & 0xFFFFu);
+                        cz = (int)(cell >> 16);
+                    }
+                    if constexpr (TRANSIENT) t = buf.t.v[slot];
                     mode0 = ms & 0x7FFFFFFFu;
                     sign = (ms >> 31) ? -1 : 1;
-                    const uint32_t cell = buf.cell[slot];
-                    cy = (int)(cell & 0xFFFFu);
-                    cz = (int)(cell >> 16);
                     lam = s_props[2 * mode0];
                     vg = s_props[2 * mode0 + 1];
                     x0 = x;
@@ -345,7 +386,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (ox > R(0)) { d_b = M::div(L - x, ox); kind = HIT_XHI; }
             else if (ox < R(0)) { d_b = M::div(x, -ox); kind = HIT_XLO; }
         }
-        if constexpr (GEOM == LE_MC_GEOM_POROUS) {
+        if constexpr (POROUS) {
             if (rad > R(0)) {
                 const R ry = y - half, rz = z - half;
                 const R a = oy * oy + oz * oz;
@@ -442,76 +483,81 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         Lacc += dL;
         hrun += dL;
 
-        // steps IVa / IVb: move, then wall response or relaxation event
+        // steps IVa / IVb.  Every lane evaluates the same straight-line code
+        // and keeps its own outcome through selects, so walls and relaxation
+        // events do not split the warp.
         x = x_new;
-        if constexpr (GEOM == LE_MC_GEOM_POROUS) {
+        if constexpr (POROUS) {
             y += oy * seg;
             z += oz * seg;
         }
         if constexpr (TRANSIENT) t += seg / vg;
         ++n_seg;
+        const bool scat = !hit;
+        int wall = -1;
+        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
+            if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
+            wall = hit ? wall : -1;
+        }
+        const bool on_wall = wall >= 0;
+        const bool absorbed = wall == LE_MC_WALL_BLACK;
+        const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
+        const bool periodic = hit && !on_wall;
+        // Eq. 2 redraw (kept only on a relaxation event)
+        const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+        const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
+        lam = scat ? lam_new : lam;
+        vg = scat ? vg_new : vg;
+        // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
         const R u2 = M::uniform(r.z);
         R sn, cs;
         M::sincos_2pi(M::uniform(r.w), &sn, &cs);
-        bool absorbed = false;
-        if (hit) {
-            int wall = -1;
-            if (kind == HIT_XLO) wall = P.wall_lo;
-            else if (kind == HIT_XHI) wall = P.wall_hi;
-            else if (kind == HIT_CYL) wall = P.pore_wall;
-            if (wall >= 0) {
-                ++n_wall;
-                if (wall == LE_MC_WALL_BLACK) {
-                    absorbed = true;
-                } else if (kind != HIT_CYL) {
-                    if (wall == LE_MC_WALL_SPECULAR) {
-                        ox = -ox;
-                    } else {  // Lambertian about the inward normal +-x
-                        const R mu = M::sqrt_(u2);
-                        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
-                        ox = (kind == HIT_XLO) ? mu : -mu;
-                        oy = st * cs;
-                        oz = st * sn;
-                    }
-                } else {
-                    const R ny = (y - half) / rad, nz = (z - half) / rad;
-                    if (wall == LE_MC_WALL_SPECULAR) {
-                        const R dn = oy * ny + oz * nz;
-                        oy -= R(2) * dn * ny;
-                        oz -= R(2) * dn * nz;
-                    } else {  // Lambertian about the normal pointing into the solid
-                        const R mu = M::sqrt_(u2);
-                        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
-                        ox = st * cs;
-                        oy = mu * ny - st * sn * nz;
-                        oz = mu * nz + st * sn * ny;
-                    }
-                }
-            } else {  // periodic face of the unit cell: re-insert opposite
-                ++n_per;
-                if (kind == HIT_YHI) { y = R(0); ++cy; }
-                else if (kind == HIT_YLO) { y = pitch; --cy; }
-                else if (kind == HIT_ZHI) { z = R(0); ++cz; }
-                else { z = pitch; --cz; }
+        const R mu = scat ? (R(2) * u2 - R(1)) : M::sqrt_(u2);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        const R a = st * cs, b = st * sn;
+        R nox = a, noy = b, noz = mu;
+        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            // x walls: Lambertian about +-x, or mirror
+            const R wox = diffuse ? ((kind == HIT_XLO) ? mu : -mu) : -ox;
+            const R woy = diffuse ? a : oy;
+            const R woz = diffuse ? b : oz;
+            if constexpr (POROUS) {
+                // pore wall: normal from the axis to the hit point
+                const R ny = (y - half) / rad, nz = (z - half) / rad;
+                const R dn = oy * ny + oz * nz;
+                const R cox = diffuse ? a : ox;
+                const R coy = diffuse ? (mu * ny - b * nz) : (oy - R(2) * dn * ny);
+                const R coz = diffuse ? (mu * nz + b * ny) : (oz - R(2) * dn * nz);
+                const bool cyl = kind == HIT_CYL;
+                nox = scat ? a : (periodic ? ox : (cyl ? cox : wox));
+                noy = scat ? b : (periodic ? oy : (cyl ? coy : woy));
+                noz = scat ? mu : (periodic ? oz : (cyl ? coz : woz));
+                // periodic unit-cell face: re-insert on the opposite face
+                const bool yhi = periodic && kind == HIT_YHI, ylo = periodic && kind == HIT_YLO;
+                const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
+                y = yhi ? R(0) : (ylo ? pitch : y);
+                z = zhi ? R(0) : (zlo ? pitch : z);
+                cy += (int)yhi - (int)ylo;
+                cz += (int)zhi - (int)zlo;
+            } else {
+                nox = scat ? a : wox;
+                noy = scat ? b : woy;
+                noz = scat ? mu : woz;
             }
-        } else {
-            // step IVb: (omega, p) from normalised Eq. 2, isotropic direction, sign kept
-            ++n_scat;
-            if (P.n_hj > 0) {
-                if (n_scat - 1u < (uint32_t)P.n_hj) {
-                    atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
-                    atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
-                }
-                hrun = R(0);
+        }
+        ox = nox;
+        oy = noy;
+        oz = noz;
+        n_scat += scat ? 1u : 0u;
+        n_wall += on_wall ? 1u : 0u;
+        n_per += periodic ? 1u : 0u;
+        if (P.n_hj > 0 && scat) {
+            if (n_scat - 1u < (uint32_t)P.n_hj) {
+                atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
+                atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
             }
-            const uint32_t mode = alias_draw(s_scat, (uint32_t)n_modes, r.y);
-            lam = s_props[2 * mode];
-            vg = s_props[2 * mode + 1];
-            const R mu = R(2) * u2 - R(1);
-            const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
-            ox = st * cs;
-            oy = st * sn;
-            oz = mu;
+            hrun = R(0);
         }
         // step VI and truncation
         if (absorbed) { fate = FATE_ABSORBED; alive = false; }
@@ -542,20 +588,65 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (red[i]) atomicAdd(&P.counters[i], red[i]);
         if (fl) atomicOr(P.flags, fl);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < prof_len; i += blockDim.x)
-        if (s_prof[i] != 0.0) atomicAdd(&P.prof[i], s_prof[i]);
-    for (int i = threadIdx.x; i < hj_len; i += blockDim.x)
-        if (s_hj[i] != 0.0) atomicAdd(&P.hj[i], s_hj[i]);
+    if (prof_len + hj_len > 0) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < prof_len; i += blockDim.x)
+            if (s_prof[i] != 0.0) atomicAdd(&P.prof[i], s_prof[i]);
+        for (int i = threadIdx.x; i < hj_len; i += blockDim.x)
+            if (s_hj[i] != 0.0) atomicAdd(&P.hj[i], s_hj[i]);
+    }
+}
+
+// Long-first schedule, pass 1: flag the particles whose emission mode has a
+// mean free path above lam_cut (they make the longest trajectories: many
+// wall segments before their first relaxation event) and list them so the
+// trace kernel can serve them first.  Same random words as step I.
+template <typename R>
+__global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ KernelArgs args)
+{
+    const TraceParams& P = args.p;
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lanemask_lt = (1u << lane) - 1u;
+    const R cut = (R)P.lam_cut;
+    const uint32_t N = P.n_particles;
+    const uint32_t stride = gridDim.x * blockDim.x;
+    // whole warps iterate together so the ballots below see full masks
+    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
+    for (uint32_t w0 = first; w0 < N; w0 += stride) {
+        const uint32_t pid = w0 + (uint32_t)lane;
+        bool is_long = false;
+        if (pid < N) {
+            const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, P.inst), args.rk);
+            const uint32_t mode = alias_draw(P.alias_emit, (uint32_t)P.n_modes, r.y);
+            R lam, vg;
+            load_props<R>(P.props, mode, lam, vg);
+            is_long = lam > cut;
+        }
+        const unsigned m = __ballot_sync(FULL, is_long);
+        if (m) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(P.long_count, (unsigned)__popc(m));
+            base = __shfl_sync(FULL, base, 0);
+            if (is_long) {
+                const unsigned slot = base + (unsigned)__popc(m & lanemask_lt);
+                if (slot < P.long_cap) {
+                    P.long_list[slot] = pid;
+                    atomicOr(&P.long_bits[pid >> 5], 1u << (pid & 31u));
+                }
+            }
+        }
+    }
 }
 
 // Dynamic shared memory of one block.
-template <typename R>
+template <typename R, int GEOM, int SRC>
 inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_len)
 {
     size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
     off = (off + 15) & ~(size_t)15;
-    off += (size_t)(threads / 32) * sizeof(EmitBuffer<R>);
+    off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC>);
+    off = (off + 7) & ~(size_t)7;
     off += (size_t)prof_len * sizeof(double);
     off += (size_t)hj_len * sizeof(double);
     return off;

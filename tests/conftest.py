@@ -25,3 +25,15 @@ def oracle():
 def analytic():
     from oracle import analytic as A
     return A
+
+
+@pytest.fixture(scope="session")
+def built_library():
+    """Builds libLeMC.so in tree (nvcc) and returns the imported package."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("le_mc_build", os.path.join(ROOT, "paper_1206_3316_gb300", "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    import paper_1206_3316_gb300 as pkg
+    return pkg

@@ -17,14 +17,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def P():
+def P(built_library):
     import torch
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
-    from paper_1206_3316_gb300 import build as B
-    B.build()
-    import paper_1206_3316_gb300 as pkg
-    return pkg
+    return built_library
 
 
 def _z(g, o, key):
@@ -32,6 +29,10 @@ def _z(g, o, key):
 
 
 def _same_particles(gr, orr, atol=1e-12):
+    # Discrete outcomes must agree exactly.  Path lengths agree to rounding:
+    # the device contracts a*b+c into FMAs and near-tangent pore hits subtract
+    # nearly equal squares, so the tolerance is a small fraction of a mean
+    # free path (any algorithmic difference moves L by O(mean free path)).
     for f in ("sign", "fate", "n_seg", "n_scat", "n_wall", "n_periodic", "mode0"):
         assert np.array_equal(gr[f], orr[f]), f
     np.testing.assert_allclose(gr["L_axis"], orr["L_axis"], rtol=0, atol=atol)
@@ -119,7 +120,7 @@ def test_gray_porous_per_particle(P, oracle):
                          max_events=300, max_scatter=20)
     g = P.simulate(prob, record_particles=True)
     o = oracle.run(prob, record_particles=True)
-    _same_particles(g["particles_rec"], o["particles_rec"], atol=1e-18)
+    _same_particles(g["particles_rec"], o["particles_rec"], atol=2e-8 * 1e-6)
     assert g["periodic"] == o["periodic"] > 0
     assert g["kappa"] == pytest.approx(o["kappa"], rel=1e-9)
 
@@ -129,7 +130,7 @@ def test_gray_pulse_grid_bit_exact(P, oracle):
                           sample_dt=25e-12, t_final=1e-9, material=dict(W.GRAY_UNIT, tau=1e-11, v=3000.0))
     g = P.simulate(prob, record_particles=True)
     o = oracle.run(prob, record_particles=True)
-    _same_particles(g["particles_rec"], o["particles_rec"], atol=1e-18)
+    _same_particles(g["particles_rec"], o["particles_rec"], atol=3e-8 * 1e-6)
     assert np.array_equal(g["grid"].astype(np.int64), o["grid"])
 
 
@@ -191,8 +192,8 @@ def test_pulse_fp32_energy_conservation_and_oracle(P, oracle):
 
 # ------------------------------------------- full size, launch invariance
 def test_film_full_size_bias_below_one_per_mille(P, analytic):
-    # 3 sigma < 1e-3 kappa needs ~5e8 particles of the 100 nm film
-    prob = W.silicon_film(n_particles=500_000_000, precision="fp32")
+    # 3 sigma < 1e-3 kappa needs ~5.2e8 particles of the 100 nm film
+    prob = W.silicon_film(n_particles=640_000_000, precision="fp32")
     g = P.simulate(prob)
     pin = analytic.kappa_film(W.SILICON_LIKE, 100e-9)
     assert 3.0 * g["kappa_se"] < 1e-3 * pin

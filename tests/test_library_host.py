@@ -14,11 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
-def P():
-    from paper_1206_3316_gb300 import build as B
-    B.build()
-    import paper_1206_3316_gb300 as pkg
-    return pkg
+def P(built_library):
+    return built_library
 
 
 def _declared_functions():
