@@ -41,7 +41,7 @@ import workloads as W  # noqa: E402
 N_PARTICLES = 10_000_000
 METRIC = "free-flight segments/s per GB300 (plain vs batched); p50/p99 latency at 1% std error"
 UNIT = "segments/s"
-WORKLOAD = ("silicon-like thin film 100 nm, diffuse walls, gradient along z, 3x1000 modes at 300 K, "
+WORKLOAD = ("silicon-like thin film 100 nm, diffuse walls, gradient along z, LA + doubly degenerate TA x 1000 bins (2000 modes) at 300 K, "
             "1e7 particles, K_s=40, K_e=4096, FP32 trajectories / FP64 tallies")
 
 # Algorithmic lane operations per free-flight segment of the film kernel
@@ -191,6 +191,100 @@ def cpu_baseline(problem, seconds=12.0):
             "sample": f"{n} particles of the same film workload, FP64, {dt:.1f} s on {cores} threads"}
 
 
+def batched_measurement(P, torch, dev, stream, steps, launch):
+    """Plain vs batched on the many-instance workload: 256 silicon-like films,
+    thickness log-uniform in [10 nm, 100 um], particle counts log-uniform in
+    [1e4, 1e7].  Plain = one le_mc_run per instance, back to back on one
+    stream; batched = one persistent launch over all instances (autotuned
+    shape, replayed CUDA graph)."""
+    probs = W.batched_films(256)
+    total = sum(p["run"]["n_particles"] for p in probs)
+    mat = P.le_mc_create_material(P.material_desc(probs[0]["material"]))
+    geos = [P.le_mc_create_geometry(P.geometry_desc(p["geometry"])) for p in probs]
+    rds = [P.run_desc(p["source"], p["run"], launch) for p in probs]
+
+    def plain_pass():
+        hs = [P.le_mc_run(mat, g, r, stream) for g, r in zip(geos, rds)]
+        return hs
+
+    for h in plain_pass():  # warm-up
+        P.le_mc_destroy_run(h)
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    hs = plain_pass()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = a.elapsed_time(b)
+    plain_segs = sum(P.le_mc_read_tallies(h)["segments"] for h in hs)
+    plain_launches = sum(P.le_mc_read_tallies(h)["kernel_launches"] for h in hs)
+    for h in hs:
+        P.le_mc_destroy_run(h)
+    for g in geos:
+        P.le_mc_destroy_geometry(g)
+    P.le_mc_destroy_material(mat)
+
+    with P.Batch(probs) as bt:
+        cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
+        os.makedirs(os.path.dirname(cache), exist_ok=True)
+        cfg = bt.autotune(stream, cache_path=cache)
+        bt.set_config(dict(cfg, use_graph=True))
+        bt.launch(stream)  # capture + warm-up
+        bt.wait()
+        ms, segs, launches = [], 0, 0
+        for _ in range(max(1, min(steps, 5))):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            bt.launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+            res = bt.results()
+            segs += sum(r["segments"] for r in res)
+            launches += res[0]["kernel_launches"]
+    batched = segs / (sum(ms) / 1e3)
+    plain = plain_segs / (plain_ms / 1e3)
+    return {"value": batched, "unit": UNIT, "plain_sequential": plain, "speedup": batched / plain,
+            "instances": len(probs), "particles_per_launch": total, "ms_per_launch": statistics.mean(ms),
+            "plain_ms_per_pass": plain_ms, "launch": cfg, "graph": True,
+            "workload": "256 silicon-like films, L log-uniform [10 nm, 100 um], N log-uniform [1e4, 1e7]",
+            "gpu_launches": launches + plain_launches}
+
+
+def served_measurement(P, seconds, max_slots=16):
+    """Served form: Poisson request arrivals (mean 50/s) mixing gray slabs,
+    silicon-like films and porous films of random size, T_eq in [100, 400] K,
+    target relative std errors 1 % and 0.3 %, particle budgets log-uniform in
+    [1e5, 1e8]; requests are admitted by the native server as slots and
+    device memory free up.  Latency = completion - submission."""
+    reqs = W.served_stream(duration_s=seconds)
+    with P.Server(max_slots=max_slots) as srv:
+        ids = []
+        t0 = time.perf_counter()
+        for r in reqs:
+            delay = r["arrival_s"] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(srv.submit(r["problem"], r["target_rel_err"]))
+        srv.wait_all(1800)
+        stats = srv.stats()
+        res = [srv.poll(i) for i in ids]
+    done = [(q, r) for q, r in zip(reqs, res) if r["state"] == "done"]
+    first = min(r["submit_s"] for r in res)
+    last = max(r["done_s"] for _, r in done)
+    out = {"requests": len(reqs), "completed": len(done), "failed": stats["failed"],
+           "aggregate_segments_per_s": stats["segments"] / (last - first), "unit": UNIT,
+           "arrival_rate_hz": 50.0, "seconds": seconds, "max_slots": max_slots}
+    for target in (0.01, 0.003):
+        lat = sorted(r["done_s"] - r["submit_s"] for q, r in done if q["target_rel_err"] == target)
+        met = sum(1 for q, r in done if q["target_rel_err"] == target and r["rel_err"] <= target)
+        if lat:
+            key = f"target_{target:g}"
+            out[key] = {"n": len(lat), "p50_s": lat[len(lat) // 2],
+                        "p99_s": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "met_target": met}
+    return out
+
+
 def run_reference(args, problem, rank, world):
     """Reference arm: the FP64 CPU oracle, one bounded sample per step."""
     if rank != 0:
@@ -233,9 +327,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n-particles", type=int, default=N_PARTICLES)
-    ap.add_argument("--threads-per-block", type=int, default=0)
+    ap.add_argument("--threads-per-block", type=int, default=256)
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--served-seconds", type=float, default=10.0,
+                    help="length of the request stream of the served form (0 = skip)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -375,6 +472,12 @@ def main():
         "clocks": clocks,
         "device_flags": flags,
     }
+    if not args.no_batched:
+        bm = batched_measurement(P, torch, dev, stream, args.steps, launch)
+        line["gpu_launches"] += bm.pop("gpu_launches")
+        line["batched"] = bm
+    if args.served_seconds > 0:
+        line["served"] = served_measurement(P, args.served_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(problem)
     print(json.dumps(line), flush=True)

@@ -182,8 +182,14 @@ typedef struct {
                                      * the bulk instead of trailing it.  Results
                                      * do not depend on the order (up to FP64
                                      * summation order).                       */
-    int32_t pad_schedule;
+    int32_t refill_min;             /* a warp refills idle lanes once this many
+                                     * are idle (0 = 1: at once)                 */
     double long_mfp_cut;            /* [m]; 0 = 32 L (PLANES, POROUS)            */
+    int32_t chunk;                  /* queue positions a warp claims per atomic,
+                                     * multiple of 32 (0 = 32)                   */
+    uint32_t first_particle;        /* particle ids traced are first_particle ..
+                                     * first_particle + n_particles - 1 (< 2^32),
+                                     * so a problem can be traced in pieces      */
 } le_mc_run_desc;
 
 typedef struct le_mc_run_s* le_mc_run_handle;
@@ -254,6 +260,108 @@ typedef struct {
 
 LE_MC_API le_mc_status le_mc_destroy_run(le_mc_run_handle h);
 
+/* ---- batches: many instances of one problem family in one launch ---------
+ * Not in the paper: the instances are independent simulations of the method
+ * (same steps I-VI), packed into one persistent launch so that small
+ * instances do not leave the GPU idle.  The particle stream of an instance is
+ * fixed by (seed, instance_id, particle id), so each instance's result is the
+ * one le_mc_run gives for it alone, up to FP64 summation order. */
+typedef struct le_mc_batch_s* le_mc_batch;
+
+typedef struct {
+    int32_t threads_per_block; /* 0 = 512                                   */
+    int32_t blocks_per_sm;     /* 0 = as many as fit                        */
+    int32_t refill_min;        /* 0 = 1                                     */
+    int32_t chunk;             /* queue positions per claim, 0 = 32         */
+    int32_t use_graph;         /* 1: capture zero + classify + trace once as
+                                * a CUDA graph and replay it per launch     */
+    float ms;                  /* autotune: time of one launch with this shape */
+} le_mc_launch_config;
+
+/* n >= 1 instances sharing material m.  All geoms[i] are PLANES with the same
+ * wall types; all runs[i] share source kind, precision, seed, max_scatter and
+ * max_events; each has its own thickness geoms[i].L, drive (dT_lo, dT_hi or
+ * dTdz), n_particles and instance_id.  Profiles, H_j, grids and records are
+ * not available in batches.  The sum of n_particles must be < 2^32.  Device
+ * memory for every instance's tallies is allocated here, once.
+ * Errors: LE_MC_ERR_INVALID, LE_MC_ERR_NOMEM, LE_MC_ERR_CUDA. */
+LE_MC_API le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometry_desc* geoms,
+                                          const le_mc_run_desc* runs, le_mc_batch* out);
+/* Launch shape of later launches (drops a captured graph).  INVALID if out of range. */
+LE_MC_API le_mc_status le_mc_batch_set_config(le_mc_batch b, const le_mc_launch_config* cfg);
+/* Enqueues one pass over every instance on `stream`: zero the tallies,
+ * classify (long-first), trace.  Asynchronous; a launch may overlap nothing
+ * else that uses the same batch. */
+LE_MC_API le_mc_status le_mc_batch_launch(le_mc_batch b, void* stream);
+LE_MC_API le_mc_status le_mc_batch_wait(le_mc_batch b);
+/* Tallies of instance i from the last launch (waits for it); kernel_ms is the
+ * device time of the whole launch. */
+LE_MC_API le_mc_status le_mc_batch_read(le_mc_batch b, int32_t i, le_mc_tallies* out);
+/* Picks threads_per_block, blocks_per_sm, refill_min and chunk by timing
+ * launches of this batch (each candidate once after one warm-up), sets the
+ * best and returns it.  If cache_path is not NULL, a previous result for the
+ * same (geometry kind, source, precision, mode count, GPU name) is reused and
+ * a new one appended.  Synchronous on `stream`. */
+LE_MC_API le_mc_status le_mc_batch_autotune(le_mc_batch b, void* stream, const char* cache_path,
+                                            le_mc_launch_config* best);
+LE_MC_API le_mc_status le_mc_batch_destroy(le_mc_batch b);
+
+/* ---- serving: continuous batching of simulation requests -------------------
+ * Not in the paper.  A worker thread owned by the server admits submitted
+ * requests into slots while a slot and device memory are free, traces each
+ * request in epochs (le_mc_run over consecutive particle-id ranges) on the
+ * slot's own stream so that requests overlap on the GPU, and retires a
+ * request once the relative standard error of its primary estimate (kappa
+ * for GRADIENT, Psi for WALLS) is at or below its target, or its particle
+ * budget is spent.  A request's epoch sizes depend only on its own
+ * statistics, so its particle set, and therefore its result, is the same
+ * whether it runs alone or among others (up to FP64 summation order). */
+typedef struct le_mc_server_s* le_mc_server;
+
+typedef struct {
+    int32_t max_slots;             /* requests traced at once, 1..64 (0 = 8)        */
+    int32_t pad;
+    uint64_t hbm_budget_bytes;     /* device memory active requests may hold
+                                    * (0 = half of the free memory at creation)    */
+    uint64_t pilot_particles;      /* first epoch of every request (0 = 65536)      */
+    uint64_t max_epoch_particles;  /* largest epoch of one request (0 = 2^24)       */
+} le_mc_server_config;
+
+enum { LE_MC_REQ_QUEUED = 0, LE_MC_REQ_RUNNING = 1, LE_MC_REQ_DONE = 2, LE_MC_REQ_FAILED = 3 };
+
+typedef struct {
+    int32_t state;                 /* LE_MC_REQ_*                                   */
+    int32_t epochs;                /* le_mc_run calls made for the request          */
+    double submit_s, start_s, done_s; /* server clock, seconds since creation        */
+    double rel_err;                /* achieved relative std error of the estimate   */
+    le_mc_tallies tallies;         /* over every particle traced for the request    */
+} le_mc_request_status;
+
+typedef struct {
+    uint64_t submitted, completed, failed, active, queued;
+    uint64_t segments, particles;  /* traced by completed epochs                    */
+    uint64_t hbm_in_use;           /* bytes held by admitted requests (estimate)    */
+    double uptime_s;
+} le_mc_server_counters;
+
+/* Starts the worker thread on the current device.  Errors: INVALID, NOMEM, CUDA. */
+LE_MC_API le_mc_status le_mc_server_create(const le_mc_server_config* cfg, le_mc_server* out);
+/* Queues a request; r->n_particles is its particle budget, target_rel_err > 0
+ * its goal.  Descriptors are copied.  WALLS or GRADIENT sources only.
+ * Errors: INVALID (descriptor or target), STATE (server stopping). */
+LE_MC_API le_mc_status le_mc_server_submit(le_mc_server s, const le_mc_material_desc* m,
+                                           const le_mc_geometry_desc* g, const le_mc_run_desc* r,
+                                           double target_rel_err, uint64_t* request_id);
+/* Non-blocking status of a request.  Errors: INVALID (unknown id). */
+LE_MC_API le_mc_status le_mc_server_poll(le_mc_server s, uint64_t request_id, le_mc_request_status* out);
+/* A queued request fails at once; a running one after its epoch in flight. */
+LE_MC_API le_mc_status le_mc_server_cancel(le_mc_server s, uint64_t request_id);
+/* Blocks until no request is queued or running; TIMEOUT after timeout_s. */
+LE_MC_API le_mc_status le_mc_server_wait_all(le_mc_server s, double timeout_s);
+LE_MC_API le_mc_status le_mc_server_stats(le_mc_server s, le_mc_server_counters* out);
+/* Cancels what is queued, lets epochs in flight finish, joins the worker. */
+LE_MC_API le_mc_status le_mc_server_destroy(le_mc_server s);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 /* Philox4x32-10 of n counters (4 words each) under one key, computed by a GPU
  * kernel; host arrays in and out.  Synchronous. */
@@ -270,7 +378,8 @@ LE_MC_API le_mc_status le_mc_device_info(int32_t* sm_count, char* name, size_t n
 
 /* Thread-local description of the last failure on this thread ("" if none). */
 /* sizeof of the ABI structs, for binding checks: which = 0 material_desc,
- * 1 geometry_desc, 2 run_desc, 3 tallies, 4 particle; -1 if unknown. */
+ * 1 geometry_desc, 2 run_desc, 3 tallies, 4 particle, 5 launch_config;
+ * -1 if unknown. */
 LE_MC_API int32_t le_mc_struct_size(int32_t which);
 
 LE_MC_API const char* le_mc_last_error(void);

@@ -9,11 +9,13 @@ material, geometry, source and run parameters.
 from __future__ import annotations
 
 from ._binding import (  # noqa: F401
-    ARRAY, LeMcError, PARTICLE_DTYPE, geometry_desc, le_mc_abi_version, le_mc_alias_table,
-    le_mc_create_geometry, le_mc_create_material, le_mc_destroy_geometry, le_mc_destroy_material,
-    le_mc_destroy_run, le_mc_device_info, le_mc_last_error, le_mc_material_table, le_mc_philox,
-    le_mc_read_array, le_mc_read_tallies, le_mc_run, le_mc_sample_modes, le_mc_wait, lib, material_desc,
-    run_desc, LIB_PATH,
+    ARRAY, LeMcError, PARTICLE_DTYPE, config_dict, geometry_desc, launch_config, le_mc_abi_version,
+    le_mc_alias_table, le_mc_batch_autotune, le_mc_batch_create, le_mc_batch_destroy, le_mc_batch_launch,
+    le_mc_batch_read, le_mc_batch_set_config, le_mc_batch_wait, le_mc_create_geometry, le_mc_create_material,
+    le_mc_destroy_geometry, le_mc_destroy_material, le_mc_destroy_run, le_mc_device_info, le_mc_last_error,
+    le_mc_material_table, le_mc_philox, le_mc_read_array, le_mc_read_tallies, le_mc_run, le_mc_sample_modes,
+    le_mc_wait, lib, material_desc, run_desc, LIB_PATH, le_mc_server_cancel, le_mc_server_create,
+    le_mc_server_destroy, le_mc_server_poll, le_mc_server_stats, le_mc_server_submit, le_mc_server_wait_all,
 )
 
 
@@ -52,3 +54,91 @@ def simulate(problem, stream=None, arrays=True, record_particles=False, launch=N
             le_mc_destroy_geometry(geo)
     finally:
         le_mc_destroy_material(mat)
+
+
+class Batch:
+    """Many film or slab instances sharing one material, traced by one launch.
+
+    ``problems`` are workload dicts that differ only in thickness, drive,
+    particle count and instance id (see ``le_mc_batch_create``)."""
+
+    def __init__(self, problems, config=None):
+        if any(p["material"] != problems[0]["material"] for p in problems):
+            raise ValueError("all instances of a batch share one material")
+        self.problems = problems
+        self.mat = le_mc_create_material(material_desc(problems[0]["material"]))
+        try:
+            self.h = le_mc_batch_create(self.mat, [geometry_desc(p["geometry"]) for p in problems],
+                                        [run_desc(p["source"], p["run"]) for p in problems])
+        except Exception:
+            le_mc_destroy_material(self.mat)
+            raise
+        if config:
+            le_mc_batch_set_config(self.h, config)
+
+    def launch(self, stream=None):
+        le_mc_batch_launch(self.h, stream)
+
+    def wait(self):
+        le_mc_batch_wait(self.h)
+
+    def results(self):
+        return [le_mc_batch_read(self.h, i) for i in range(len(self.problems))]
+
+    def autotune(self, stream=None, cache_path=None):
+        return le_mc_batch_autotune(self.h, stream, cache_path)
+
+    def set_config(self, config):
+        le_mc_batch_set_config(self.h, config)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            le_mc_batch_destroy(self.h)
+            self.h = None
+        if getattr(self, "mat", None) is not None:
+            le_mc_destroy_material(self.mat)
+            self.mat = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Server:
+    """Continuous-batching request server (native worker thread).
+
+    ``submit(problem, target_rel_err)`` queues a workload dict whose
+    ``n_particles`` is the particle budget; ``poll`` returns its state and,
+    once done, its normalised tallies over every particle traced."""
+
+    def __init__(self, max_slots=8, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0):
+        self.h = le_mc_server_create(max_slots, hbm_budget_bytes, pilot_particles, max_epoch_particles)
+
+    def submit(self, problem, target_rel_err):
+        return le_mc_server_submit(self.h, material_desc(problem["material"]), geometry_desc(problem["geometry"]),
+                                   run_desc(problem["source"], problem["run"]), target_rel_err)
+
+    def poll(self, rid):
+        return le_mc_server_poll(self.h, rid)
+
+    def cancel(self, rid):
+        le_mc_server_cancel(self.h, rid)
+
+    def wait_all(self, timeout_s=600.0):
+        le_mc_server_wait_all(self.h, timeout_s)
+
+    def stats(self):
+        return le_mc_server_stats(self.h)
+
+    def close(self):
+        if getattr(self, "h", None) is not None:
+            le_mc_server_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

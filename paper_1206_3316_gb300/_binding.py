@@ -63,7 +63,8 @@ class RunDesc(C.Structure):
                 ("t_final", C.c_double), ("sample_dt", C.c_double),
                 ("n_hj", C.c_int32), ("record_particles", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32),
-                ("schedule", C.c_int32), ("pad_schedule", C.c_int32), ("long_mfp_cut", C.c_double)]
+                ("schedule", C.c_int32), ("refill_min", C.c_int32), ("long_mfp_cut", C.c_double),
+                ("chunk", C.c_int32), ("first_particle", C.c_uint32)]
 
 
 class Tallies(C.Structure):
@@ -82,6 +83,28 @@ class Particle(C.Structure):
                 ("n_periodic", C.c_uint32), ("mode0", C.c_uint32),
                 ("L_axis", C.c_double), ("x0", C.c_double), ("t0", C.c_double)]
 
+
+class LaunchConfig(C.Structure):
+    _fields_ = [("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32), ("refill_min", C.c_int32),
+                ("chunk", C.c_int32), ("use_graph", C.c_int32), ("ms", C.c_float)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("max_slots", C.c_int32), ("pad", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
+                ("pilot_particles", C.c_uint64), ("max_epoch_particles", C.c_uint64)]
+
+
+class RequestStatus(C.Structure):
+    _fields_ = [("state", C.c_int32), ("epochs", C.c_int32), ("submit_s", C.c_double), ("start_s", C.c_double),
+                ("done_s", C.c_double), ("rel_err", C.c_double), ("tallies", Tallies)]
+
+
+class ServerCounters(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "active", "queued", "segments",
+                                          "particles", "hbm_in_use")] + [("uptime_s", C.c_double)]
+
+
+REQUEST_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 PARTICLE_DTYPE = np.dtype([("sign", np.int8), ("fate", np.int8), ("pad", np.int16),
                            ("n_seg", np.uint32), ("n_scat", np.uint32), ("n_wall", np.uint32),
@@ -108,6 +131,21 @@ SIGNATURES = {
     "le_mc_philox": (_STATUS, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p, C.c_size_t]),
     "le_mc_sample_modes": (_STATUS, [_H, C.c_int32, C.c_void_p, C.c_void_p, C.c_size_t]),
     "le_mc_device_info": (_STATUS, [C.POINTER(C.c_int32), C.c_char_p, C.c_size_t]),
+    "le_mc_batch_create": (_STATUS, [_H, C.c_int32, C.c_void_p, C.c_void_p, C.POINTER(_H)]),
+    "le_mc_batch_set_config": (_STATUS, [_H, C.POINTER(LaunchConfig)]),
+    "le_mc_batch_launch": (_STATUS, [_H, C.c_void_p]),
+    "le_mc_batch_wait": (_STATUS, [_H]),
+    "le_mc_batch_read": (_STATUS, [_H, C.c_int32, C.POINTER(Tallies)]),
+    "le_mc_batch_autotune": (_STATUS, [_H, C.c_void_p, C.c_char_p, C.POINTER(LaunchConfig)]),
+    "le_mc_batch_destroy": (_STATUS, [_H]),
+    "le_mc_server_create": (_STATUS, [C.POINTER(ServerConfig), C.POINTER(_H)]),
+    "le_mc_server_submit": (_STATUS, [_H, C.POINTER(MaterialDesc), C.POINTER(GeometryDesc), C.POINTER(RunDesc),
+                                      C.c_double, C.POINTER(C.c_uint64)]),
+    "le_mc_server_poll": (_STATUS, [_H, C.c_uint64, C.POINTER(RequestStatus)]),
+    "le_mc_server_cancel": (_STATUS, [_H, C.c_uint64]),
+    "le_mc_server_wait_all": (_STATUS, [_H, C.c_double]),
+    "le_mc_server_stats": (_STATUS, [_H, C.POINTER(ServerCounters)]),
+    "le_mc_server_destroy": (_STATUS, [_H]),
     "le_mc_struct_size": (C.c_int32, [C.c_int32]),
     "le_mc_last_error": (C.c_char_p, []),
     "le_mc_abi_version": (C.c_int32, []),
@@ -122,7 +160,7 @@ for _name, (_res, _args) in SIGNATURES.items():
     _f.restype = _res
     _f.argtypes = _args
 
-for _i, _cls in enumerate((MaterialDesc, GeometryDesc, RunDesc, Tallies, Particle)):
+for _i, _cls in enumerate((MaterialDesc, GeometryDesc, RunDesc, Tallies, Particle, LaunchConfig)):
     if lib.le_mc_struct_size(_i) != C.sizeof(_cls):
         raise ImportError(f"ABI mismatch: {_cls.__name__} is {C.sizeof(_cls)} bytes in Python, "
                           f"{lib.le_mc_struct_size(_i)} in libLeMC.so")
@@ -202,6 +240,9 @@ def run_desc(src, run, launch=None):
     r.threads_per_block = int(launch.get("threads_per_block", run.get("threads_per_block", 0)))
     r.schedule = {"auto": 0, "long_first": 1, "natural": 2}[launch.get("schedule", run.get("schedule", "auto"))]
     r.long_mfp_cut = float(launch.get("long_mfp_cut", run.get("long_mfp_cut", 0.0)))
+    r.refill_min = int(launch.get("refill_min", run.get("refill_min", 0)))
+    r.chunk = int(launch.get("chunk", run.get("chunk", 0)))
+    r.first_particle = int(run.get("first_particle", 0))
     return r
 
 
@@ -310,3 +351,102 @@ def le_mc_last_error():
 
 def le_mc_abi_version():
     return lib.le_mc_abi_version()
+
+
+def launch_config(cfg=None):
+    c = LaunchConfig()
+    cfg = cfg or {}
+    c.threads_per_block = int(cfg.get("threads_per_block", 0))
+    c.blocks_per_sm = int(cfg.get("blocks_per_sm", 0))
+    c.refill_min = int(cfg.get("refill_min", 0))
+    c.chunk = int(cfg.get("chunk", 0))
+    c.use_graph = 1 if cfg.get("use_graph", False) else 0
+    return c
+
+
+def config_dict(c):
+    return {"threads_per_block": c.threads_per_block, "blocks_per_sm": c.blocks_per_sm,
+            "refill_min": c.refill_min, "chunk": c.chunk, "use_graph": bool(c.use_graph), "ms": c.ms}
+
+
+def le_mc_batch_create(mat, geoms, runs):
+    n = len(geoms)
+    g = (GeometryDesc * n)(*geoms)
+    r = (RunDesc * n)(*runs)
+    h = _H()
+    _check(lib.le_mc_batch_create(mat, n, C.cast(g, C.c_void_p), C.cast(r, C.c_void_p), C.byref(h)),
+           "le_mc_batch_create")
+    return h
+
+
+def le_mc_batch_set_config(b, cfg):
+    _check(lib.le_mc_batch_set_config(b, C.byref(launch_config(cfg) if isinstance(cfg, dict) else cfg)),
+           "le_mc_batch_set_config")
+
+
+def le_mc_batch_launch(b, stream=None):
+    _check(lib.le_mc_batch_launch(b, _stream_ptr(stream)), "le_mc_batch_launch")
+
+
+def le_mc_batch_wait(b):
+    _check(lib.le_mc_batch_wait(b), "le_mc_batch_wait")
+
+
+def le_mc_batch_read(b, i):
+    t = Tallies()
+    _check(lib.le_mc_batch_read(b, i, C.byref(t)), "le_mc_batch_read")
+    return {f[0]: getattr(t, f[0]) for f in Tallies._fields_}
+
+
+def le_mc_batch_autotune(b, stream=None, cache_path=None):
+    c = LaunchConfig()
+    path = cache_path.encode() if cache_path else None
+    _check(lib.le_mc_batch_autotune(b, _stream_ptr(stream), path, C.byref(c)), "le_mc_batch_autotune")
+    return config_dict(c)
+
+
+def le_mc_batch_destroy(b):
+    _check(lib.le_mc_batch_destroy(b), "le_mc_batch_destroy")
+
+
+def le_mc_server_create(max_slots=0, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0):
+    c = ServerConfig()
+    c.max_slots, c.hbm_budget_bytes = int(max_slots), int(hbm_budget_bytes)
+    c.pilot_particles, c.max_epoch_particles = int(pilot_particles), int(max_epoch_particles)
+    h = _H()
+    _check(lib.le_mc_server_create(C.byref(c), C.byref(h)), "le_mc_server_create")
+    return h
+
+
+def le_mc_server_submit(s, mdesc, gdesc, rdesc, target_rel_err):
+    rid = C.c_uint64()
+    _check(lib.le_mc_server_submit(s, C.byref(mdesc), C.byref(gdesc), C.byref(rdesc), float(target_rel_err),
+                                   C.byref(rid)), "le_mc_server_submit")
+    return rid.value
+
+
+def le_mc_server_poll(s, rid):
+    st = RequestStatus()
+    _check(lib.le_mc_server_poll(s, int(rid), C.byref(st)), "le_mc_server_poll")
+    out = {"state": REQUEST_STATES[st.state], "epochs": st.epochs, "submit_s": st.submit_s,
+           "start_s": st.start_s, "done_s": st.done_s, "rel_err": st.rel_err}
+    out.update({f[0]: getattr(st.tallies, f[0]) for f in Tallies._fields_})
+    return out
+
+
+def le_mc_server_cancel(s, rid):
+    _check(lib.le_mc_server_cancel(s, int(rid)), "le_mc_server_cancel")
+
+
+def le_mc_server_wait_all(s, timeout_s):
+    _check(lib.le_mc_server_wait_all(s, float(timeout_s)), "le_mc_server_wait_all")
+
+
+def le_mc_server_stats(s):
+    c = ServerCounters()
+    _check(lib.le_mc_server_stats(s, C.byref(c)), "le_mc_server_stats")
+    return {f[0]: getattr(c, f[0]) for f in ServerCounters._fields_}
+
+
+def le_mc_server_destroy(s):
+    _check(lib.le_mc_server_destroy(s), "le_mc_server_destroy")

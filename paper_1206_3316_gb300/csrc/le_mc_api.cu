@@ -105,13 +105,16 @@ void material_release(le_mc_material m)
 {
     if (!m) return;
     if (m->refs.fetch_sub(1) != 1) return;
+    // Every run and batch that used the tables has finished (they hold a
+    // reference until destroyed, and destroying them waits for their device
+    // work), so the stream-ordered frees need no device-wide synchronisation.
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(m->device);
-    cudaFree(m->d_props32);
-    cudaFree(m->d_props64);
-    cudaFree(m->d_alias_scat);
-    cudaFree(m->d_alias_emit);
+    if (m->d_props32) cudaFreeAsync(m->d_props32, 0);
+    if (m->d_props64) cudaFreeAsync(m->d_props64, 0);
+    if (m->d_alias_scat) cudaFreeAsync(m->d_alias_scat, 0);
+    if (m->d_alias_emit) cudaFreeAsync(m->d_alias_emit, 0);
     cudaSetDevice(cur);
     delete m;
 }
@@ -127,6 +130,46 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
 
+namespace lemc {
+// Internal access for the batch and static-scratch translation units.
+
+bool material_view(le_mc_material m, MaterialView* out)
+{
+    if (!m) return false;
+    out->props32 = m->d_props32;
+    out->props64 = m->d_props64;
+    out->alias_scat = m->d_alias_scat;
+    out->alias_emit = m->d_alias_emit;
+    out->n_modes = m->n_modes;
+    out->device = m->device;
+    out->sums = m->sums;
+    return true;
+}
+
+void material_retain(le_mc_material m)
+{
+    if (m) m->refs.fetch_add(1);
+}
+
+void material_drop(le_mc_material m) { material_release(m); }
+
+le_mc_status set_error(le_mc_status s, const char* what, const char* detail) { return fail(s, what, detail); }
+
+le_mc_status set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+
+// 1 when the run's device work is complete, 0 while it runs, -1 on error.
+int run_ready(le_mc_run_handle h)
+{
+    if (!h || h->failed) return -1;
+    if (!h->launches) return 1;
+    const cudaError_t e = cudaEventQuery(h->ev_stop);
+    if (e == cudaSuccess) return 1;
+    if (e == cudaErrorNotReady) return 0;
+    h->failed = true;
+    return -1;
+}
+}  // namespace lemc
+
 extern "C" {
 
 const char* le_mc_last_error(void) { return g_err; }
@@ -140,6 +183,7 @@ int32_t le_mc_struct_size(int32_t which)
     case 2: return (int32_t)sizeof(le_mc_run_desc);
     case 3: return (int32_t)sizeof(le_mc_tallies);
     case 4: return (int32_t)sizeof(le_mc_particle);
+    case 5: return (int32_t)sizeof(le_mc_launch_config);
     default: return -1;
     }
 }
@@ -209,15 +253,17 @@ le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_materi
         ae[i] = make_uint2(thr_e[i], al_e[i]);
         as[i] = make_uint2(thr_s[i], al_s[i]);
     }
+    // stream-ordered pool on the legacy stream, complete before returning
     cudaError_t e = cudaGetDevice(&m->device);
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_props32, props32.size() * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&m->d_props64, props64.size() * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_alias_scat, n * sizeof(uint2));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&m->d_alias_emit, n * sizeof(uint2));
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_props32, props32.data(), props32.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_props64, props64.data(), props64.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_alias_scat, as.data(), n * sizeof(uint2), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(m->d_alias_emit, ae.data(), n * sizeof(uint2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMallocAsync(&m->d_props32, props32.size() * sizeof(float), 0);
+    if (e == cudaSuccess) e = cudaMallocAsync(&m->d_props64, props64.size() * sizeof(double), 0);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_scat, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_emit, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props32, props32.data(), props32.size() * sizeof(float), cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props64, props64.data(), props64.size() * sizeof(double), cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_scat, as.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_emit, ae.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         material_release(m);
         return cuda_fail(e, "le_mc_create_material");
@@ -367,6 +413,9 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.counters = reinterpret_cast<unsigned long long*>(h->dev + h->off_counters);
     P.queue = reinterpret_cast<unsigned int*>(h->dev + h->off_queue);
     P.flags = reinterpret_cast<unsigned int*>(h->dev + h->off_flags);
+    P.refill_min = r.refill_min > 0 ? r.refill_min : 1;
+    P.chunk = r.chunk > 0 ? r.chunk : 32;
+    P.first = r.first_particle;
     for (int i = 0; i < 10; ++i) {
         a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
         a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
@@ -530,6 +579,8 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
 le_mc_status le_mc_destroy_run(le_mc_run_handle h)
 {
     if (!h) return LE_MC_OK;
+    // the run's kernels read the material tables: let them finish first
+    if (h->ev_stop && h->launches && !h->failed) cudaEventSynchronize(h->ev_stop);
     if (h->dev) {
         // stream-ordered free after the run's work
         if (cudaFreeAsync(h->dev, h->stream) != cudaSuccess) cudaFree(h->dev);

@@ -167,7 +167,10 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
 {
     if (!r) { *why = "null run descriptor"; return LE_MC_ERR_INVALID; }
     if (r->precision != LE_MC_PREC_FP64 && r->precision != LE_MC_PREC_FP32) { *why = "unknown precision"; return LE_MC_ERR_INVALID; }
-    if (r->n_particles > 0xFFFFFFFFull) { *why = "n_particles must be < 2^32"; return LE_MC_ERR_INVALID; }
+    if (r->n_particles + r->first_particle > 0xFFFFFFFFull) {
+        *why = "first_particle + n_particles must be < 2^32";
+        return LE_MC_ERR_INVALID;
+    }
     if (r->max_events < 1) { *why = "max_events must be >= 1"; return LE_MC_ERR_INVALID; }
     if (n_modes < 1 || n_modes > LE_MC_MAX_MODES) { *why = "bad material"; return LE_MC_ERR_INVALID; }
     switch (r->source) {
@@ -215,6 +218,12 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
         return LE_MC_ERR_INVALID;
     }
     if (r->blocks_per_sm < 0 || r->blocks_per_sm > 32) { *why = "blocks_per_sm out of range"; return LE_MC_ERR_INVALID; }
+    if (r->refill_min < 0 || r->refill_min > 32) { *why = "refill_min out of 0..32"; return LE_MC_ERR_INVALID; }
+    if (r->chunk < 0 || r->chunk % 32 != 0 || r->chunk > (1 << 20)) {
+        *why = "chunk must be a multiple of 32 up to 2^20";
+        return LE_MC_ERR_INVALID;
+    }
+    if (r->schedule < 0 || r->schedule > 2) { *why = "schedule out of 0..2"; return LE_MC_ERR_INVALID; }
     return LE_MC_OK;
 }
 

@@ -31,6 +31,17 @@ enum { FATE_ABSORBED = 0, FATE_MAX_SCATTER = 1, FATE_MAX_EVENTS = 2, FATE_T_FINA
 constexpr uint32_t kMaxTries = 64;
 constexpr uint32_t kTimeBlock0 = 65;
 
+// One instance of a batch (same material, geometry kind, source kind and
+// caps as the rest of the batch; its own thickness, drive, size and stream).
+struct BatchInstance {
+    double L, dT_lo, dT_hi, dTdz;
+    double lam_cut;        // long-first threshold for this instance
+    uint32_t inst_id;      // 4th Philox counter word
+    uint32_t n_particles;
+};
+
+constexpr int kBatchSmemMax = 512;  // batches up to this size accumulate per block in shared memory
+
 struct TraceParams {
     // material tables (device pointers)
     const void* props;        // float2 or double2 [n_modes]: (Lambda_b, v_b)
@@ -73,6 +84,16 @@ struct TraceParams {
     unsigned int* long_count;      // [1]
     uint32_t long_cap;
     double lam_cut;
+    // batch mode: queue positions 0 .. offsets[n_instances] - 1 run over the
+    // concatenated instances; per-instance sums and counters
+    const BatchInstance* instances;
+    const unsigned long long* offsets;  // [n_instances + 1]
+    int32_t n_instances;
+    int32_t refill_min;                 // dead lanes a warp tolerates before refilling (>= 1)
+    int32_t chunk;                      // queue positions a warp claims at a time (multiple of 32)
+    uint32_t first;                     // particle id of queue position 0 (run mode)
+    double* inst_sums;                  // [n_instances][2]
+    unsigned long long* inst_counters;  // [n_instances][CNT_N]
 };
 
 // Host helpers (le_mc_host.cpp).
@@ -85,6 +106,22 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
 struct MaterialSums {
     double C_tot, Cv_sum;
 };
+
+// Device tables of a material, for translation units other than the one
+// that owns le_mc_material_s.
+struct MaterialView {
+    const void* props32;
+    const void* props64;
+    const uint2* alias_scat;
+    const uint2* alias_emit;
+    int n_modes;
+    int device;
+    MaterialSums sums;
+};
+bool material_view(le_mc_material m, MaterialView* out);
+void material_retain(le_mc_material m);
+void material_drop(le_mc_material m);
+le_mc_status set_error(le_mc_status s, const char* what, const char* detail);
 
 // Normalisation of the raw device sums into le_mc_tallies (after the
 // algorithm: N = energy / E_eff; Eq. 4: E_eff_dot = P / N).

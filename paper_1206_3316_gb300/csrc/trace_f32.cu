@@ -30,7 +30,7 @@ cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
 template <int G, int S, bool PR>
 cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t* bytes)
 {
-    *bytes = trace_smem_bytes<float, G, S>(n_modes, threads, prof_len, hj_len);
+    *bytes = trace_smem_bytes<float, G, S, PR>(n_modes, threads, prof_len, hj_len);
     return cudaSuccess;
 }
 }  // namespace
@@ -67,6 +67,35 @@ cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int thr
                             size_t* bytes)
 {
     LEMC_DISPATCH(smem_one, n_modes, threads, prof_len, hj_len, bytes)
+}
+
+// Batch mode: PLANES geometry with the WALLS or GRADIENT source.
+cudaError_t batch_attr_f32(int src, int threads, size_t smem, int* per_sm)
+{
+    auto k = src == LE_MC_SRC_WALLS ? trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>
+                                    : trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
+}
+
+// Launch only (no attribute calls), so it can be captured into a graph.
+cudaError_t batch_launch_f32(const KernelArgs& a, int src, int blocks, int threads, size_t smem, cudaStream_t st)
+{
+    if (blocks <= 0) return cudaSuccess;
+    if (src == LE_MC_SRC_WALLS)
+        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true><<<blocks, threads, smem, st>>>(a);
+    else
+        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true><<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+size_t batch_smem_f32(int src, int n_modes, int threads, int n_instances)
+{
+    return src == LE_MC_SRC_WALLS
+               ? trace_smem_bytes<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>(n_modes, threads, 0, 0, n_instances)
+               : trace_smem_bytes<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(n_modes, threads, 0, 0,
+                                                                                            n_instances);
 }
 
 cudaError_t launch_classify_f32(const KernelArgs& a, int blocks, cudaStream_t st)

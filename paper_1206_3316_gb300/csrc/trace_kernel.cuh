@@ -47,8 +47,9 @@ template <typename T>
 struct Slots<T, 0> {};
 
 // Emission buffer of one warp, structure of arrays.  y, z and the unit cell
-// are kept only for POROUS geometries, the emission time only for PULSE.
-template <typename R, bool YZ, bool TIME>
+// are kept only for POROUS geometries, the emission time only for PULSE, the
+// batch instance only in batch mode.
+template <typename R, bool YZ, bool TIME, bool INST>
 struct EmitBuffer {
     R x[kBufSlots];
     R ox[kBufSlots], oy[kBufSlots], oz[kBufSlots];
@@ -57,10 +58,11 @@ struct EmitBuffer {
     Slots<R, YZ ? kBufSlots : 0> y, z;
     Slots<uint32_t, YZ ? kBufSlots : 0> cell;  // cy | cz << 16
     Slots<R, TIME ? kBufSlots : 0> t;
+    Slots<uint32_t, INST ? kBufSlots : 0> inst;
 };
 
-template <typename R, int GEOM, int SRC>
-using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE>;
+template <typename R, int GEOM, int SRC, bool BATCH = false>
+using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE, BATCH>;
 
 // Compensated FP32 sum (Kahan: c carries the part of each addend that the
 // running sum lost); plain sum for FP64.
@@ -97,16 +99,57 @@ __device__ __forceinline__ void load_props(const void* props, uint32_t mode, R& 
     }
 }
 
+// What step I needs to know about the problem a particle belongs to: the
+// run itself, or one instance of a batch.
+struct EmitCtx {
+    double L, dT_lo, dT_hi, dTdz;
+    uint32_t inst;
+};
+
+__device__ __forceinline__ EmitCtx run_ctx(const TraceParams& P)
+{
+    EmitCtx c;
+    c.L = P.L;
+    c.dT_lo = P.dT_lo;
+    c.dT_hi = P.dT_hi;
+    c.dTdz = P.dTdz;
+    c.inst = P.inst;
+    return c;
+}
+
+__device__ __forceinline__ EmitCtx batch_ctx(const BatchInstance& b)
+{
+    EmitCtx c;
+    c.L = b.L;
+    c.dT_lo = b.dT_lo;
+    c.dT_hi = b.dT_hi;
+    c.dTdz = b.dTdz;
+    c.inst = b.inst_id;
+    return c;
+}
+
+// Batch instance holding global queue position p (offsets has n + 1 entries).
+__device__ __forceinline__ uint32_t batch_find(const unsigned long long* offsets, uint32_t n, unsigned long long p)
+{
+    uint32_t lo = 0, hi = n;  // offsets[lo] <= p < offsets[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (offsets[mid] <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
 // Step I for one particle; returns false if a rejection loop ran out.  The
 // emission alias table is read from global memory (once per particle, cached
 // in L1), which leaves shared memory to the per-flight tables.
 template <typename R, int GEOM, int SRC>
-__device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundKeys& rk, const uint2* alias_emit,
-                                              uint32_t pid, R& x, R& y, R& z, R& ox, R& oy, R& oz, R& t,
-                                              uint32_t& mode, int& sign, uint32_t& cy, uint32_t& cz)
+__device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCtx& E, const RoundKeys& rk,
+                                              const uint2* alias_emit, uint32_t pid, R& x, R& y, R& z, R& ox,
+                                              R& oy, R& oz, R& t, uint32_t& mode, int& sign, uint32_t& cy,
+                                              uint32_t& cz)
 {
     using M = DMath<R>;
-    const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, P.inst), rk);
+    const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, E.inst), rk);
     mode = alias_draw(alias_emit, (uint32_t)P.n_modes, r.y);
     const R u0 = M::uniform(r.x), u2 = M::uniform(r.z), u3 = M::uniform(r.w);
     R sn, cs;
@@ -116,30 +159,30 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundK
     bool ok = true;
     if constexpr (SRC == LE_MC_SRC_WALLS) {
         // isothermal walls: wall picked by |T_b - T_eq|, cosine law into the domain
-        const R wlo = (R)fabs(P.dT_lo), whi = (R)fabs(P.dT_hi);
+        const R wlo = (R)fabs(E.dT_lo), whi = (R)fabs(E.dT_hi);
         const bool lo = u0 * (wlo + whi) < wlo;
         const R mu = M::sqrt_(u2);
         const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
         ox = lo ? mu : -mu;
         oy = st * cs;
         oz = st * sn;
-        x = lo ? R(0) : (R)P.L;
-        sign = lo ? (P.dT_lo >= 0.0 ? 1 : -1) : (P.dT_hi >= 0.0 ? 1 : -1);
+        x = lo ? R(0) : (R)E.L;
+        sign = lo ? (E.dT_lo >= 0.0 ? 1 : -1) : (E.dT_hi >= 0.0 ? 1 : -1);
     } else if constexpr (SRC == LE_MC_SRC_GRADIENT) {
         // Eq. 6: |cos| law about z, sign sgn(-cos dT/dz), even ids positive
         sign = (pid & 1u) ? -1 : 1;
-        const R dir = (R)sign * (P.dTdz > 0.0 ? R(-1) : R(1));
+        const R dir = (R)sign * (E.dTdz > 0.0 ? R(-1) : R(1));
         const R mu = dir * M::sqrt_(u2);
         const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
         ox = st * cs;
         oy = st * sn;
         oz = mu;
-        x = (GEOM == LE_MC_GEOM_BULK) ? R(0) : u0 * (R)P.L;
+        x = (GEOM == LE_MC_GEOM_BULK) ? R(0) : u0 * (R)E.L;
         if constexpr (GEOM == LE_MC_GEOM_POROUS) {
             const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
             ok = false;
             for (uint32_t b = 1; b <= kMaxTries; ++b) {
-                const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+                const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
                 const R Y = M::uniform(q.x) * pitch * (R)P.cells_y;
                 const R Z = M::uniform(q.y) * pitch * (R)P.cells_z;
                 int iy = (int)M::floor_(Y / pitch), iz = (int)M::floor_(Z / pitch);
@@ -160,12 +203,12 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundK
         ox = -mu;
         oy = st * cs;
         oz = st * sn;
-        x = (R)P.L;
+        x = (R)E.L;
         const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
         const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
         ok = false;
         for (uint32_t b = 1; b <= kMaxTries; ++b) {
-            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
             const R rad = (R)P.p_sx * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x)));
             R s2, c2;
             M::sincos_2pi(M::uniform(q.y), &s2, &c2);
@@ -186,7 +229,7 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundK
         t = (R)P.p_tc;
         bool tok = false;
         for (uint32_t b = kTimeBlock0; b < kTimeBlock0 + kMaxTries; ++b) {
-            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, P.inst), rk);
+            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
             R s2, c2;
             M::sincos_2pi(M::uniform(q.y), &s2, &c2);
             const R t0 = (R)P.p_tc + (R)P.p_st * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x))) * c2;
@@ -197,14 +240,31 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const RoundK
     return ok;
 }
 
-template <typename R, int GEOM, int SRC, bool PROFILE>
+template <typename R, int SRC, bool PROFILE>
+struct FusedTable {
+    static constexpr bool value = sizeof(R) == 4 && SRC != LE_MC_SRC_PULSE && !PROFILE;
+};
+
+// Bytes of the per-mode tables at the start of shared memory (16-aligned).
+template <typename R, int SRC, bool PROFILE>
+__host__ __device__ inline size_t table_bytes(int n_modes)
+{
+    const size_t per_mode = FusedTable<R, SRC, PROFILE>::value ? 16 : (2 * sizeof(R) + 8);
+    return ((size_t)n_modes * per_mode + 15) & ~(size_t)15;
+}
+
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false>
 __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
 {
     using M = DMath<R>;
-    using Buf = BufferOf<R, GEOM, SRC>;
+    using Buf = BufferOf<R, GEOM, SRC, BATCH>;
     constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
     constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
+    // Kernels whose estimators never need the group velocity (steady path
+    // integrals) keep one 16-byte word per mode: (threshold, alias,
+    // Lambda_j, Lambda_alias), so an Eq. 2 redraw is a single shared load.
+    constexpr bool FUSED = FusedTable<R, SRC, PROFILE>::value;
     const TraceParams& P = args.p;
     const RoundKeys& rk = args.rk;
 
@@ -212,8 +272,8 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     const int n_modes = P.n_modes;
     R* s_props = reinterpret_cast<R*>(smem);
     uint2* s_scat = reinterpret_cast<uint2*>(smem + (size_t)n_modes * 2 * sizeof(R));
-    size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
-    off = (off + 15) & ~(size_t)15;
+    uint4* s_fused = reinterpret_cast<uint4*>(smem);
+    size_t off = table_bytes<R, SRC, PROFILE>(n_modes);
     Buf* s_buf = reinterpret_cast<Buf*>(smem + off);
     const int n_warps = blockDim.x >> 5;
     off += (size_t)n_warps * sizeof(Buf);
@@ -223,27 +283,45 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     off += (size_t)prof_len * sizeof(double);
     double* s_hj = reinterpret_cast<double*>(smem + off);
     const int hj_len = 2 * P.n_hj;
+    off += (size_t)hj_len * sizeof(double);
+    // batch mode: per-instance sums [n][2] and counters [n][CNT_N] of this block
+    const bool inst_in_smem = BATCH && P.n_instances <= kBatchSmemMax;
+    const int inst_len = inst_in_smem ? P.n_instances : 0;
+    double* s_isum = reinterpret_cast<double*>(smem + off);
+    unsigned long long* s_icnt = reinterpret_cast<unsigned long long*>(smem + off + (size_t)inst_len * 2 * sizeof(double));
 
     // mode tables and block tallies
     for (int i = threadIdx.x; i < n_modes; i += blockDim.x) {
         R lam, vg;
         load_props<R>(P.props, (uint32_t)i, lam, vg);
-        s_props[2 * i] = lam;
-        s_props[2 * i + 1] = vg;
-        s_scat[i] = P.alias_scat[i];
+        const uint2 e = P.alias_scat[i];
+        if constexpr (FUSED) {
+            R lam_a, vg_a;
+            load_props<R>(P.props, e.y, lam_a, vg_a);
+            s_fused[i] = make_uint4(e.x, e.y, __float_as_uint((float)lam), __float_as_uint((float)lam_a));
+        } else {
+            s_props[2 * i] = lam;
+            s_props[2 * i + 1] = vg;
+            s_scat[i] = e;
+        }
     }
     for (int i = threadIdx.x; i < prof_len; i += blockDim.x) s_prof[i] = 0.0;
     for (int i = threadIdx.x; i < hj_len; i += blockDim.x) s_hj[i] = 0.0;
+    for (int i = threadIdx.x; i < 2 * inst_len; i += blockDim.x) s_isum[i] = 0.0;
+    for (int i = threadIdx.x; i < CNT_N * inst_len; i += blockDim.x) s_icnt[i] = 0ull;
     __syncthreads();
 
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     Buf& buf = s_buf[threadIdx.x >> 5];
-    const uint32_t N = P.n_particles;
-    // particles served first (long-first schedule), then ids 0..N-1 minus those
+    // queue positions: the long-first list, then positions 0 .. n_pos - 1
+    // (particle ids of the run, or the concatenated instances of a batch)
+    // minus those already listed
+    const unsigned long long n_pos = BATCH ? P.offsets[P.n_instances] : (unsigned long long)P.n_particles;
     const uint32_t n_long = P.long_list ? min(*P.long_count, P.long_cap) : 0u;
-    const unsigned long long q_total = (unsigned long long)n_long + N;
+    const unsigned long long q_total = (unsigned long long)n_long + n_pos;
+    const int refill_min = P.refill_min > 1 ? P.refill_min : 1;
     const R L = (R)P.L;
     const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, rad = (R)P.radius, rad2 = (R)(P.radius * P.radius);
     const R big = M::big();
@@ -254,6 +332,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     uint32_t pid = 0, n_seg = 0, n_scat = 0, n_wall = 0, n_per = 0, mode0 = 0;
     int cy = 0, cz = 0, sign = 1, fate = FATE_MAX_EVENTS;
     bool alive = false, pending = false;
+    // problem of the current particle (batch mode: its instance)
+    uint32_t bidx = 0, instw = P.inst;
+    R Lp = L;
 
     // lane accumulators
     Acc<R> acc_sL, acc_sL2;
@@ -262,11 +343,44 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
 
     int cnt = 0;         // emission buffer fill (warp-uniform)
     bool qdone = false;  // particle queue exhausted (warp-uniform)
+    // queue positions this warp has claimed but not yet emitted (warp-uniform);
+    // claims are `chunk` positions at a time
+    const unsigned long long chunk = P.chunk >= 32 ? (unsigned long long)P.chunk : 32ull;
+    unsigned long long w_next = 0, w_end = 0;
+    uint32_t cur_b = 0xFFFFFFFFu;  // batch instance the lane accumulators belong to
+
+    // batch mode: move the lane accumulators to instance b's totals
+    auto flush_lane = [&](uint32_t b) {
+        if (b == 0xFFFFFFFFu) return;
+        const double v[2] = {acc_sL.value(), acc_sL2.value()};
+        const uint32_t c[CNT_N] = {c_part, c_seg, c_scat, c_wall, c_per, c_trunc, c_abs};
+        if (inst_in_smem) {
+            atomicAdd(&s_isum[2 * b], v[0]);
+            atomicAdd(&s_isum[2 * b + 1], v[1]);
+            for (int i = 0; i < CNT_N; ++i)
+                if (c[i]) atomicAdd(&s_icnt[CNT_N * b + i], (unsigned long long)c[i]);
+        } else {
+            atomicAdd(&P.inst_sums[2 * b], v[0]);
+            atomicAdd(&P.inst_sums[2 * b + 1], v[1]);
+            for (int i = 0; i < CNT_N; ++i)
+                if (c[i]) atomicAdd(&P.inst_counters[(size_t)CNT_N * b + i], (unsigned long long)c[i]);
+        }
+        acc_sL = Acc<R>();
+        acc_sL2 = Acc<R>();
+        c_part = c_seg = c_scat = c_wall = c_per = c_trunc = c_abs = 0;
+    };
 
     for (;;) {
         const unsigned dead = __ballot_sync(FULL, !alive);
-        if (dead) {
+        // refill once refill_min lanes are idle (or at once near the end)
+        if (dead && (dead == FULL || qdone || __popc(dead) >= refill_min)) {
             if (pending) {  // totals of the finished particle (step V, Eq. 4)
+                if constexpr (BATCH) {
+                    if (bidx != cur_b) {
+                        flush_lane(cur_b);
+                        cur_b = bidx;
+                    }
+                }
                 const R sL = (R)sign * Lacc;
                 acc_sL.add(sL);
                 acc_sL2.add(sL * sL);
@@ -294,33 +408,56 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                     rec.L_axis = (double)Lacc;
                     rec.x0 = (double)x0;
                     rec.t0 = (double)t0;
-                    P.records[pid] = rec;
+                    P.records[pid - P.first] = rec;
                 }
                 pending = false;
             }
             const int need = __popc(dead);
             while (cnt < need && !qdone) {
-                // step I for the next 32 queue positions, whole warp
-                unsigned long long base = 0;
-                if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), 32ull);
-                base = __shfl_sync(FULL, base, 0);
-                if (base + 32ull >= q_total) qdone = true;
-                const unsigned long long q = base + (unsigned long long)lane;
-                uint32_t id = 0;
+                // step I for the next 32 claimed queue positions, whole warp
+                if (w_next >= w_end) {
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), chunk);
+                    base = __shfl_sync(FULL, base, 0);
+                    w_next = base;
+                    w_end = min(base + chunk, q_total);
+                    if (base >= q_total) {
+                        qdone = true;
+                        break;
+                    }
+                }
+                const unsigned long long q = w_next + (unsigned long long)lane;
+                const unsigned long long q_end = w_end;
+                w_next = min(w_next + 32ull, w_end);
+                if (w_next >= w_end && w_end >= q_total) qdone = true;
+                uint32_t pos = 0;
                 bool valid = false;
-                if (q < n_long) {
-                    id = P.long_list[q];
+                if (q >= q_end) {
+                    valid = false;
+                } else if (q < n_long) {
+                    pos = P.long_list[q];
                     valid = true;
-                } else if (q < q_total) {
-                    id = (uint32_t)(q - n_long);
-                    valid = !(P.long_list && ((P.long_bits[id >> 5] >> (id & 31u)) & 1u));
+                } else {
+                    pos = (uint32_t)(q - n_long);
+                    valid = !(P.long_list && ((P.long_bits[pos >> 5] >> (pos & 31u)) & 1u));
                 }
                 const unsigned vmask = __ballot_sync(FULL, valid);
                 if (valid) {
+                    uint32_t id = pos, eb = 0;
+                    EmitCtx ctx;
+                    if constexpr (BATCH) {
+                        eb = batch_find(P.offsets, (uint32_t)P.n_instances, pos);
+                        id = (uint32_t)(pos - P.offsets[eb]);
+                        ctx = batch_ctx(P.instances[eb]);
+                    } else {
+                        id = P.first + pos;
+                        ctx = run_ctx(P);
+                    }
                     R ex, ey, ez, eox, eoy, eoz, et;
                     uint32_t em, ecy, ecz;
                     int es;
-                    if (!emit_particle<R, GEOM, SRC>(P, rk, P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es, ecy, ecz))
+                    if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es,
+                                                     ecy, ecz))
                         flags |= FLAG_REJECTION_EXHAUSTED;
                     const int slot = cnt + __popc(vmask & lanemask_lt);
                     buf.x[slot] = ex;
@@ -335,6 +472,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                         buf.cell.v[slot] = ecy | (ecz << 16);
                     }
                     if constexpr (TRANSIENT) buf.t.v[slot] = et;
+                    if constexpr (BATCH) buf.inst.v[slot] = eb;
                 }
                 cnt += __popc(vmask);
                 __syncwarp();
@@ -357,10 +495,20 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                         cz = (int)(cell >> 16);
                     }
                     if constexpr (TRANSIENT) t = buf.t.v[slot];
+                    if constexpr (BATCH) {
+                        bidx = buf.inst.v[slot];
+                        const BatchInstance& bi = P.instances[bidx];
+                        Lp = (R)bi.L;
+                        instw = bi.inst_id;
+                    }
                     mode0 = ms & 0x7FFFFFFFu;
                     sign = (ms >> 31) ? -1 : 1;
-                    lam = s_props[2 * mode0];
-                    vg = s_props[2 * mode0 + 1];
+                    if constexpr (FUSED) {
+                        lam = __uint_as_float(s_fused[mode0].z);
+                    } else {
+                        lam = s_props[2 * mode0];
+                        vg = s_props[2 * mode0 + 1];
+                    }
                     x0 = x;
                     t0 = t;
                     Lacc = 0;
@@ -376,15 +524,18 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         if (!alive) continue;
 
         // ---- one segment: steps II-VI ------------------------------------
-        const uint4 r = philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, P.inst), rk);
+        const uint4 r = philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk);
         // step II: flight to the next relaxation event (as a length)
         const R ell = lam * M::neg_log(M::uniform(r.x));
         // step III: first boundary along the ray
         R d_b = big;
         int kind = HIT_NONE;
         if constexpr (GEOM != LE_MC_GEOM_BULK) {
-            if (ox > R(0)) { d_b = M::div(L - x, ox); kind = HIT_XHI; }
-            else if (ox < R(0)) { d_b = M::div(x, -ox); kind = HIT_XLO; }
+            // distance to the wall ahead; a flight parallel to the walls gets
+            // an infinite (or NaN, never <= ell) distance and no hit
+            const bool up = ox > R(0);
+            d_b = M::div(up ? (Lp - x) : x, fabs(ox));
+            kind = up ? HIT_XHI : HIT_XLO;
         }
         if constexpr (POROUS) {
             if (rad > R(0)) {
@@ -410,7 +561,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         const R seg = hit ? d_b : ell;
         R x_new = x + ox * seg;
         if (hit && kind == HIT_XLO) x_new = R(0);
-        if (hit && kind == HIT_XHI) x_new = L;
+        if (hit && kind == HIT_XHI) x_new = Lp;
 
         // step V: contribution of the segment
         if constexpr (TRANSIENT) {
@@ -443,7 +594,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             // time and x-displacement spent in each bin along x (slab)
             const int nb = P.n_bins_x;
             const R dx = L / (R)nb;
-            const int g = (int)(pid % (uint32_t)P.n_batch);
+            const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
             const size_t stride = (size_t)nb + 1;
             double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
             double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
@@ -505,10 +656,17 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
         const bool periodic = hit && !on_wall;
         // Eq. 2 redraw (kept only on a relaxation event)
-        const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
-        const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
-        lam = scat ? lam_new : lam;
-        vg = scat ? vg_new : vg;
+        if constexpr (FUSED) {
+            const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
+            const uint4 e = s_fused[(uint32_t)(mm >> 32)];
+            const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
+            lam = scat ? lam_new : lam;
+        } else {
+            const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+            const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
+            lam = scat ? lam_new : lam;
+            vg = scat ? vg_new : vg;
+        }
         // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
         const R u2 = M::uniform(r.z);
         R sn, cs;
@@ -568,6 +726,19 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     }
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
+    if constexpr (BATCH) {
+        flush_lane(cur_b);
+        const uint32_t fl = __reduce_or_sync(FULL, flags);
+        if (lane == 0 && fl) atomicOr(P.flags, fl);
+        if (inst_len > 0) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < 2 * inst_len; i += blockDim.x)
+                if (s_isum[i] != 0.0) atomicAdd(&P.inst_sums[i], s_isum[i]);
+            for (int i = threadIdx.x; i < CNT_N * inst_len; i += blockDim.x)
+                if (s_icnt[i]) atomicAdd(&P.inst_counters[i], s_icnt[i]);
+        }
+        return;
+    }
     double v0 = acc_sL.value(), v1 = acc_sL2.value();
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -608,8 +779,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
-    const R cut = (R)P.lam_cut;
-    const uint32_t N = P.n_particles;
+    const bool batch = P.instances != nullptr;
+    const uint32_t N = batch ? (uint32_t)P.offsets[P.n_instances] : P.n_particles;
     const uint32_t stride = gridDim.x * blockDim.x;
     // whole warps iterate together so the ballots below see full masks
     const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
@@ -617,7 +788,15 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
         const uint32_t pid = w0 + (uint32_t)lane;
         bool is_long = false;
         if (pid < N) {
-            const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, P.inst), args.rk);
+            uint32_t id = batch ? pid : P.first + pid, inst = P.inst;
+            R cut = (R)P.lam_cut;
+            if (batch) {
+                const uint32_t b = batch_find(P.offsets, (uint32_t)P.n_instances, pid);
+                id = (uint32_t)(pid - P.offsets[b]);
+                inst = P.instances[b].inst_id;
+                cut = (R)P.instances[b].lam_cut;
+            }
+            const uint4 r = philox4x32_10(make_uint4(0u, 0u, id, inst), args.rk);
             const uint32_t mode = alias_draw(P.alias_emit, (uint32_t)P.n_modes, r.y);
             R lam, vg;
             load_props<R>(P.props, mode, lam, vg);
@@ -640,15 +819,16 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
 }
 
 // Dynamic shared memory of one block.
-template <typename R, int GEOM, int SRC>
-inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_len)
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false>
+inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_len, int n_instances = 0)
 {
-    size_t off = (size_t)n_modes * (2 * sizeof(R) + 8);
-    off = (off + 15) & ~(size_t)15;
-    off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC>);
+    size_t off = table_bytes<R, SRC, PROFILE>(n_modes);
+    off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC, BATCH>);
     off = (off + 7) & ~(size_t)7;
     off += (size_t)prof_len * sizeof(double);
     off += (size_t)hj_len * sizeof(double);
+    if (BATCH && n_instances <= kBatchSmemMax)
+        off += (size_t)n_instances * (2 * sizeof(double) + CNT_N * sizeof(unsigned long long));
     return off;
 }
 

@@ -248,3 +248,15 @@ def test_invalid_run_rejected(P):
     finally:
         P.le_mc_destroy_geometry(geo)
         P.le_mc_destroy_material(mat)
+
+
+def test_pieces_add_up(P):
+    # tracing ids [0, N) in two pieces (first_particle) gives the same particles
+    prob = W.silicon_film(n_particles=120_001, precision="fp32")
+    whole = P.simulate(prob, arrays=False)
+    a = P.simulate(W.with_run(prob, n_particles=50_000), arrays=False)
+    b = P.simulate(W.with_run(prob, n_particles=70_001, first_particle=50_000), arrays=False)
+    for k in ("particles", "segments", "scatters", "wall_hits", "truncated"):
+        assert a[k] + b[k] == whole[k]
+    assert a["sum_sL"] + b["sum_sL"] == pytest.approx(whole["sum_sL"], rel=1e-9, abs=1e-20)
+    assert a["sum_sL2"] + b["sum_sL2"] == pytest.approx(whole["sum_sL2"], rel=1e-9)

@@ -1,0 +1,100 @@
+"""GPU tests of the request server (continuous batching).
+
+A request's epochs depend only on its own statistics, so the particles it
+traces, and its result, are the same whether it runs alone or among other
+requests: integer counters exactly, FP64 sums up to summation order.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P(built_library):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    return built_library
+
+
+def _mix():
+    reqs = []
+    f = W.silicon_film(n_particles=20_000_000, thickness=100e-9)
+    reqs.append((f, 0.01))
+    f2 = W.silicon_film(n_particles=20_000_000, thickness=1e-6)
+    f2["material"]["T_eq"] = 150.0
+    f2["run"]["instance_id"] = 1
+    reqs.append((f2, 0.01))
+    s = W.gray_slab(n_particles=5_000_000, kn=2.0, n_bins=0, precision="fp32")
+    s["run"]["instance_id"] = 2
+    reqs.append((s, 0.003))
+    p = W.porous_film(n_particles=20_000_000, pitch=150e-9, radius=40e-9)
+    p["material"]["T_eq"] = 250.0
+    p["run"]["instance_id"] = 3
+    reqs.append((p, 0.01))
+    small = W.silicon_film(n_particles=70_000, thickness=30e-9)
+    small["run"]["instance_id"] = 4
+    reqs.append((small, 1e-4))  # budget-limited
+    return reqs
+
+
+INTS = ("particles", "segments", "scatters", "wall_hits", "periodic", "truncated", "absorbed")
+
+
+def test_results_same_alone_and_in_mix(P):
+    reqs = _mix()
+    alone = []
+    with P.Server(max_slots=4) as srv:
+        for prob, target in reqs:
+            rid = srv.submit(prob, target)
+            srv.wait_all(300)
+            alone.append(srv.poll(rid))
+    with P.Server(max_slots=4) as srv:
+        ids = [srv.submit(prob, target) for prob, target in reqs]
+        srv.wait_all(300)
+        mixed = [srv.poll(i) for i in ids]
+        stats = srv.stats()
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    for (prob, target), a, m in zip(reqs, alone, mixed):
+        assert a["state"] == m["state"] == "done"
+        for k in INTS:
+            assert a[k] == m[k], k
+        assert a["epochs"] == m["epochs"]
+        key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
+        assert m[key] == pytest.approx(a[key], rel=1e-9)
+        assert m["rel_err"] <= target or m["particles"] == prob["run"]["n_particles"]
+
+
+def test_served_film_matches_pin(P, analytic):
+    prob = W.silicon_film(n_particles=50_000_000, thickness=100e-9)
+    with P.Server() as srv:
+        rid = srv.submit(prob, 0.003)
+        srv.wait_all(300)
+        r = srv.poll(rid)
+    pin = analytic.kappa_film(W.SILICON_LIKE, 100e-9)
+    assert r["state"] == "done" and r["rel_err"] <= 0.003
+    assert abs(r["kappa"] - pin) < 3.0 * r["kappa_se"]
+
+
+def test_cancel_and_invalid(P):
+    with P.Server(max_slots=2, max_epoch_particles=1 << 16) as srv:
+        big = srv.submit(W.silicon_film(n_particles=4_000_000_000 - 1), 1e-9)
+        queued = [srv.submit(W.silicon_film(n_particles=3_000_000, thickness=1e-6 * (i + 1)), 1e-9) for i in range(3)]
+        srv.cancel(big)
+        for q in queued:
+            srv.cancel(q)
+        srv.wait_all(120)
+        assert srv.poll(big)["state"] == "failed"
+        assert all(srv.poll(q)["state"] == "failed" for q in queued)
+        ok = srv.submit(W.gray_slab(n_particles=100_000, n_bins=0), 0.05)
+        srv.wait_all(120)
+        assert srv.poll(ok)["state"] == "done"
+        with pytest.raises(P.LeMcError):
+            srv.submit(W.gray_slab(n_particles=100, n_bins=10), 0.01)  # arrays are not served
+        with pytest.raises(P.LeMcError):
+            srv.submit(W.gray_slab(n_particles=100, n_bins=0), 0.0)
+        with pytest.raises(P.LeMcError):
+            srv.poll(10 ** 9)
