@@ -362,6 +362,37 @@ LE_MC_API le_mc_status le_mc_server_stats(le_mc_server s, le_mc_server_counters*
 /* Cancels what is queued, lets epochs in flight finish, joins the worker. */
 LE_MC_API le_mc_status le_mc_server_destroy(le_mc_server s);
 
+/* ---- tracing without allocation -------------------------------------------
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate GPU memory while they trace, e.g. code running inside a host
+ * callback or in a region whose device memory belongs to a framework's own
+ * allocator (a cudaMalloc there fails, blocks, or corrupts the allocator's
+ * accounting), or a loop that cannot pay for an allocator call.  They create
+ * the material and geometry beforehand and pass their own result buffers.
+ *
+ * le_mc_run_noalloc traces particles first_particle .. first_particle +
+ * n_particles - 1 exactly like le_mc_run and writes the raw results to the
+ * caller's DEVICE buffers: d_sums[2] = (sum s L, sum (s L)^2) over particles
+ * (doubles) and d_counters[7] = (particles, segments, scatterings, wall
+ * hits, periodic crossings, truncated, absorbed) (unsigned 64-bit); both are
+ * cleared first.  It calls no cudaMalloc, cudaMallocAsync, cudaFree or
+ * allocating library routine and creates no stream or event.  Its kernel
+ * scratch (queue head, flags, long-first list and bitmap) is one fixed
+ * device array inside the library, about 0.6 MB, held by every GPU that
+ * loads the library until the process exits; that is why n_particles is
+ * limited to LE_MC_NOALLOC_MAX_PARTICLES per call (larger problems are
+ * traced in pieces with first_particle and the caller adds the pieces).
+ * The array's device address is looked up during the first call on each
+ * device, so make that first call before any stream capture.  Every call
+ * shares the array: calls whose device work overlaps in time race on it, so
+ * the caller must serialise them.  Steady WALLS / GRADIENT runs only (no
+ * profiles, H_j, grid or records).  Asynchronous on `stream`.
+ * Errors: LE_MC_ERR_INVALID (null pointer, bad descriptor, n_particles above
+ * the limit, arrays requested), LE_MC_ERR_CUDA. */
+#define LE_MC_NOALLOC_MAX_PARTICLES (1u << 22)
+LE_MC_API le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_run_desc* desc,
+                                         double* d_sums, unsigned long long* d_counters, void* stream);
+
 /* ---- diagnostics ---------------------------------------------------------- */
 /* Philox4x32-10 of n counters (4 words each) under one key, computed by a GPU
  * kernel; host arrays in and out.  Synchronous. */

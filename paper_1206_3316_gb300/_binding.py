@@ -146,6 +146,7 @@ SIGNATURES = {
     "le_mc_server_wait_all": (_STATUS, [_H, C.c_double]),
     "le_mc_server_stats": (_STATUS, [_H, C.POINTER(ServerCounters)]),
     "le_mc_server_destroy": (_STATUS, [_H]),
+    "le_mc_run_noalloc": (_STATUS, [_H, _H, C.POINTER(RunDesc), C.c_void_p, C.c_void_p, C.c_void_p]),
     "le_mc_struct_size": (C.c_int32, [C.c_int32]),
     "le_mc_last_error": (C.c_char_p, []),
     "le_mc_abi_version": (C.c_int32, []),
@@ -450,3 +451,13 @@ def le_mc_server_stats(s):
 
 def le_mc_server_destroy(s):
     _check(lib.le_mc_server_destroy(s), "le_mc_server_destroy")
+
+
+NOALLOC_MAX_PARTICLES = 1 << 22
+
+
+def le_mc_run_noalloc(mat, geo, desc, d_sums, d_counters, stream=None):
+    """Trace without allocating: d_sums (2 doubles) and d_counters (7 uint64)
+    are device addresses owned by the caller (ints, e.g. tensor.data_ptr())."""
+    _check(lib.le_mc_run_noalloc(mat, geo, C.byref(desc), int(d_sums), int(d_counters), _stream_ptr(stream)),
+           "le_mc_run_noalloc")

@@ -23,7 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP64 arithmetic is unaffected by these flags.
 CUFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + INC,
                   "-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-SOURCES = ["trace_f32.cu", "trace_f64.cu", "le_mc_api.cu", "le_mc_batch.cu", "le_mc_server.cu", "le_mc_diag.cu", "le_mc_host.cpp"]
+SOURCES = ["trace_f32.cu", "trace_f64.cu", "le_mc_api.cu", "le_mc_batch.cu", "le_mc_server.cu", "le_mc_noalloc.cu", "le_mc_diag.cu", "le_mc_host.cpp"]
 
 
 def nvcc():

@@ -146,6 +146,13 @@ bool material_view(le_mc_material m, MaterialView* out)
     return true;
 }
 
+bool geometry_view(le_mc_geometry g, le_mc_geometry_desc* out)
+{
+    if (!g) return false;
+    *out = g->desc;
+    return true;
+}
+
 void material_retain(le_mc_material m)
 {
     if (m) m->refs.fetch_add(1);
