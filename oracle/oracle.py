@@ -105,6 +105,32 @@ def build(force=False):
 _lib = None
 
 
+def _bind(handle):
+    handle.orc_run.restype = C.c_int
+    handle.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 8
+    return handle
+
+
+def load_variant(path):
+    """A separately compiled copy of the oracle (used by the tests that plant
+    mistakes in a copy of the source to show that the pins catch them)."""
+    return _bind(C.CDLL(path))
+
+
+def compile_variant(source_text, out_path):
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                    "-o", out_path, src, "-lm", "-lpthread"], check=True)
+    return load_variant(out_path)
+
+
+def source_text():
+    with open(_SRC) as fh:
+        return fh.read()
+
+
 def lib():
     global _lib
     if _lib is None:
@@ -166,11 +192,11 @@ def to_problem(prob, n_threads=None, record_particles=False):
     return p
 
 
-def run(prob, n_threads=None, record_particles=False):
+def run(prob, n_threads=None, record_particles=False, library=None):
     """Trace ``prob["run"]["n_particles"]`` particles; returns a dict of
     scalars, counters and (when requested by the problem) profile, H_j and
     transient-grid arrays, plus per-particle records when asked."""
-    L = lib()
+    L = library if library is not None else lib()
     p = to_problem(prob, n_threads, record_particles)
     res = Result()
     nb, nh = max(p.n_bins_x, 0), max(p.n_hj, 0)

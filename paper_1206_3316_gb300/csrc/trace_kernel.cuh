@@ -557,8 +557,25 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
             else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
         }
-        const bool hit = (kind != HIT_NONE) && (d_b <= ell);
-        const R seg = hit ? d_b : ell;
+        bool hit = (kind != HIT_NONE) && (d_b <= ell);
+        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+            // Absorbing walls decide a particle's fate: when the FP32 flight
+            // and wall distances are within a few ulp of each other (grazing
+            // flights make the wall distance large and its rounding
+            // relatively coarse), redo the comparison in FP64 from the same
+            // inputs.
+            const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
+            if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
+                const double u = (double)M::uniform(r.x);
+                const double ell64 = (double)lam * -log(u);
+                const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
+                hit = d64 <= ell64;
+            }
+        }
+        R seg = hit ? d_b : ell;
+        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+            seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
+        }
         R x_new = x + ox * seg;
         if (hit && kind == HIT_XLO) x_new = R(0);
         if (hit && kind == HIT_XHI) x_new = Lp;

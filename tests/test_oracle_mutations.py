@@ -1,0 +1,68 @@
+"""The pins must be able to fail: plant one plausible mistake at a time in a
+copy of the oracle's C source (never in the oracle itself), compile it, and
+check that the pin guarding that step rejects it while the unmodified oracle
+passes the same check."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+def _psi_pin_ok(oracle, analytic, library):
+    n = 2_000_000
+    r = oracle.run(W.gray_slab(n_particles=n, kn=1.0, n_bins=0), library=library)
+    pin = analytic.slab_solution(1.0, n_bins=50, M=100)["psi"]
+    return abs(r["psi"] - pin) < 4.0 * np.sqrt(pin * (1 - pin) / n)
+
+
+def _film_pin_ok(oracle, analytic, library):
+    r = oracle.run(W.silicon_film(n_particles=400_000, precision="fp64", max_events=1), library=library)
+    return abs(r["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 100e-9)) < 4.0 * r["kappa_se"]
+
+
+def _bulk_pin_ok(oracle, analytic, library):
+    mat = dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0)
+    r = oracle.run(W.bulk(n_particles=400_000, material=mat, max_events=8), library=library)
+    return abs(r["kappa"] - 7.0 * 9.0 * 2.5 / 3.0) < 4.0 * r["kappa_se"]
+
+
+def _nongray_pin_ok(oracle, analytic, library):
+    mat = dict(W.SILICON_LIKE, n_bins=10)
+    _, v, tau, C = analytic.mode_table(mat)
+    pin = analytic.slab_multimode_psi(v * tau, C * v, C / tau, 100e-9, M=60)
+    p = W.gray_slab(n_particles=400_000, n_bins=0)
+    p["material"] = mat
+    p["geometry"]["L"] = 100e-9
+    r = oracle.run(p, library=library)
+    return abs(r["psi"] - pin) < 4.0 * r["psi_se"]
+
+
+MUTATIONS = [
+    # (name, original text, planted mistake, pin that must catch it)
+    # (a law that only folds directions into one z hemisphere is invisible to
+    # every steady estimator here: the gradient source emits equal numbers of
+    # each sign and a hemisphere projects onto x like the sphere; the planted
+    # law below is genuinely anisotropic)
+    ("scattering not isotropic", "dir_axis(2, 2.0 * u[2] - 1.0, u[3]", "dir_axis(2, 2.0 * u[2] * u[2] - 1.0, u[3]",
+     _psi_pin_ok),
+    ("bulk flight with wrong mean free path", "double dist = m->Lambda[s.mode] * -log(u[0]);",
+     "double dist = 0.5 * m->Lambda[s.mode] * -log(u[0]);", _bulk_pin_ok),
+    ("wall emission not cosine weighted", "int lo = u[0] * (wlo + whi) < wlo;\n        double mu = sqrt(u[2]);",
+     "int lo = u[0] * (wlo + whi) < wlo;\n        double mu = u[2];", _psi_pin_ok),
+    ("Eq. 2 redraw from the emission law", "s.mode = draw_mode(m->cdf_scat", "s.mode = draw_mode(m->cdf_emit",
+     _nongray_pin_ok),
+    ("gradient-source sign flipped", "(p->dTdz > 0.0 ? -1.0 : 1.0)", "(p->dTdz > 0.0 ? 1.0 : -1.0)", _film_pin_ok),
+    ("flight drawn with the wrong mean free path", "double dist = m->Lambda[s.mode] * -log(u[0]);",
+     "double dist = m->tau[s.mode] * -log(u[0]);", _film_pin_ok),
+    ("density of states missing a factor k", "double dos = k * k / (2.0 * ORC_PI * ORC_PI * vg);",
+     "double dos = k / (2.0 * ORC_PI * ORC_PI * vg);", _film_pin_ok),
+]
+
+
+@pytest.mark.parametrize("name,orig,bad,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(oracle, analytic, tmp_path, name, orig, bad, pin):
+    text = oracle.source_text()
+    assert text.count(orig) == 1, name
+    assert pin(oracle, analytic, None), "the unmodified oracle must pass " + pin.__name__
+    lib = oracle.compile_variant(text.replace(orig, bad), str(tmp_path / "mutant.so"))
+    assert not pin(oracle, analytic, lib), f"pin {pin.__name__} missed: {name}"
