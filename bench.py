@@ -228,7 +228,8 @@ def batched_measurement(P, torch, dev, stream, steps, launch):
         cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         cfg = bt.autotune(stream, cache_path=cache)
-        bt.set_config(dict(cfg, use_graph=True))
+        cfg = dict(cfg, use_graph=True)
+        bt.set_config(cfg)
         bt.launch(stream)  # capture + warm-up
         bt.wait()
         ms, segs, launches = [], 0, 0
@@ -396,6 +397,7 @@ def main():
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     segs, kern_ms, launches, flags, kappas = 0, [], 0, 0, []
+    e2e_launches = 0
     for h in handles:
         t = P.le_mc_read_tallies(h)
         segs += t["segments"]
@@ -426,7 +428,7 @@ def main():
         h = P.le_mc_run(m, g, rd, stream)
         t = P.le_mc_read_tallies(h)
         e2e_segs += t["segments"]
-        launches += t["kernel_launches"]
+        e2e_launches += t["kernel_launches"]
         P.le_mc_destroy_run(h)
         P.le_mc_destroy_geometry(g)
         P.le_mc_destroy_material(m)
@@ -462,7 +464,7 @@ def main():
                    "kappa_W_per_mK": statistics.mean(kappas), "device": name, "sms": sms,
                    "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps},
+                "steps": e2e_steps, "gpu_launches": e2e_launches},
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
@@ -473,9 +475,7 @@ def main():
         "device_flags": flags,
     }
     if not args.no_batched:
-        bm = batched_measurement(P, torch, dev, stream, args.steps, launch)
-        line["gpu_launches"] += bm.pop("gpu_launches")
-        line["batched"] = bm
+        line["batched"] = batched_measurement(P, torch, dev, stream, args.steps, launch)
     if args.served_seconds > 0:
         line["served"] = served_measurement(P, args.served_seconds)
     if not args.no_cpu_baseline:
