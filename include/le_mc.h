@@ -137,7 +137,7 @@ LE_MC_API le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le
 LE_MC_API le_mc_status le_mc_destroy_geometry(le_mc_geometry g);
 
 /* ---- run: sources (step I), termination (step VI), estimators (step V) ---- */
-enum { LE_MC_SRC_WALLS = 0, LE_MC_SRC_GRADIENT = 1, LE_MC_SRC_PULSE = 2 };
+enum { LE_MC_SRC_WALLS = 0, LE_MC_SRC_GRADIENT = 1, LE_MC_SRC_PULSE = 2, LE_MC_SRC_INITIAL = 3 };
 enum { LE_MC_PREC_FP64 = 0, LE_MC_PREC_FP32 = 1 };
 
 typedef struct {
@@ -148,7 +148,12 @@ typedef struct {
                         * GRADIENT: the volumetric source of Eq. 5 / Eq. 6 for a
                         *   uniform dT/dz, equal numbers of each sign.
                         * PULSE (POROUS only): surface heat pulse on x = L,
-                        *   Gaussian in (y, z) and in time, all signs positive.   */
+                        *   Gaussian in (y, z) and in time, all signs positive.
+                        * INITIAL (POROUS only): initial condition
+                        *   C_{w,p} |T_i - T_eq| delta(t) of the text after the
+                        *   algorithm: a uniform excess init_dT in the layer
+                        *   init_x_lo < x < init_x_hi at t = 0, modes weighted
+                        *   by C_b, isotropic directions.                       */
     int32_t precision; /* FP64: every step in FP64.  FP32: trajectory geometry and
                         *   times in FP32, per-particle sums carried compensated,
                         *   tally accumulation in FP64.                          */
@@ -190,6 +195,8 @@ typedef struct {
     uint32_t first_particle;        /* particle ids traced are first_particle ..
                                      * first_particle + n_particles - 1 (< 2^32),
                                      * so a problem can be traced in pieces      */
+    double init_dT;                 /* INITIAL: T_i - T_eq [K], nonzero          */
+    double init_x_lo, init_x_hi;    /* INITIAL: heated layer, 0 <= lo < hi <= L  */
 } le_mc_run_desc;
 
 typedef struct le_mc_run_s* le_mc_run_handle;
@@ -211,7 +218,7 @@ typedef struct {
     double P_total;     /* source power: W per m^2 of wall (WALLS), W over the solid
                          * part of the reference volume (GRADIENT)                */
     double E_eff_dot;   /* steady: effective deviational power per particle (Eq. 4) */
-    double E_eff;       /* PULSE: deviational energy per particle (Eq. 3)          */
+    double E_eff;       /* PULSE, INITIAL: deviational energy per particle (Eq. 3) */
     double C_tot;       /* sum_b C_b                                               */
     double sum_sL, sum_sL2; /* sum over particles of s L and (s L)^2, L the total
                              * algebraic length along the flux axis (x for WALLS,

@@ -39,7 +39,7 @@
 enum { ORC_MAT_GRAY = 0, ORC_MAT_QUADRATIC = 1 };
 enum { ORC_GEOM_PLANES = 0, ORC_GEOM_BULK = 1, ORC_GEOM_POROUS = 2 };
 enum { ORC_WALL_BLACK = 0, ORC_WALL_DIFFUSE = 1, ORC_WALL_SPECULAR = 2 };
-enum { ORC_SRC_WALLS = 0, ORC_SRC_GRADIENT = 1, ORC_SRC_PULSE = 2 };
+enum { ORC_SRC_WALLS = 0, ORC_SRC_GRADIENT = 1, ORC_SRC_PULSE = 2, ORC_SRC_INITIAL = 3 };
 enum { ORC_FATE_ABSORBED = 0, ORC_FATE_MAX_SCATTER = 1, ORC_FATE_MAX_EVENTS = 2,
        ORC_FATE_T_FINAL = 3 };
 
@@ -66,6 +66,8 @@ typedef struct {
     double dTdz;          /* GRADIENT                                   */
     double pulse_sigma_x, pulse_sigma_t, pulse_t_center, pulse_energy;
     double pulse_y0, pulse_z0;
+    double init_dT;       /* INITIAL: T_i - T_eq inside init_x_lo < x < init_x_hi at t = 0 */
+    double init_x_lo, init_x_hi;
     /* run */
     uint64_t n_particles;
     uint64_t seed;
@@ -158,13 +160,14 @@ typedef struct {
     double* Lambda;
     double* cdf_emit; /* cumulative of C_b v_b  (boundary, gradient, pulse sources) */
     double* cdf_scat; /* cumulative of C_b / tau_b  (Eq. 2)                         */
+    double* cdf_init; /* cumulative of C_b  (initial-condition source)               */
     double C_tot, Cv_sum;
 } orc_mat;
 
 static void mat_free(orc_mat* m)
 {
     free(m->omega); free(m->v); free(m->tau); free(m->C); free(m->Lambda);
-    free(m->cdf_emit); free(m->cdf_scat);
+    free(m->cdf_emit); free(m->cdf_scat); free(m->cdf_init);
     memset(m, 0, sizeof(*m));
 }
 
@@ -178,7 +181,8 @@ static int mat_alloc(orc_mat* m, int n)
     m->Lambda = calloc(n, sizeof(double));
     m->cdf_emit = calloc(n, sizeof(double));
     m->cdf_scat = calloc(n, sizeof(double));
-    return (m->omega && m->v && m->tau && m->C && m->Lambda && m->cdf_emit && m->cdf_scat) ? 0 : -1;
+    m->cdf_init = calloc(n, sizeof(double));
+    return (m->omega && m->v && m->tau && m->C && m->Lambda && m->cdf_emit && m->cdf_scat && m->cdf_init) ? 0 : -1;
 }
 
 /* Isotropic dispersion omega(k) = c1 k + c2 k^2 per branch, n_bins equal-width
@@ -231,6 +235,7 @@ static int mat_build(const orc_problem* p, orc_mat* m)
         cs += m->C[i] / m->tau[i];
         m->cdf_emit[i] = ce;
         m->cdf_scat[i] = cs;
+        m->cdf_init[i] = m->C_tot + m->C[i];
         m->C_tot += m->C[i];
     }
     m->Cv_sum = ce;
@@ -378,6 +383,29 @@ static void emit(const orc_problem* p, const orc_mat* m, uint64_t pid, orc_state
                 s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;
                 if (!in_pore(p, yl, zl)) break;
             }
+        }
+    } else if (p->src_kind == ORC_SRC_INITIAL) {
+        /* Initial condition C_{w,p} |T_i - T_eq| delta(t) (text after the
+         * algorithm): at t = 0, uniform in the region init_x_lo < x <
+         * init_x_hi (solid part), mode weight C_b, isotropic direction, sign
+         * sgn(T_i - T_eq).  u1 mode, u2 polar cosine (2u - 1 about z), u3
+         * azimuth; blocks 1.. the lateral position as for the gradient source. */
+        s->mode = draw_mode(m->cdf_init, m->n, u[1]);
+        s->sign = p->init_dT >= 0.0 ? 1 : -1;
+        s->x = p->init_x_lo + u[0] * (p->init_x_hi - p->init_x_lo);
+        dir_axis(2, 2.0 * u[2] - 1.0, u[3], &s->ox, &s->oy, &s->oz);
+        s->t = 0.0;
+        for (uint32_t b = 1; b <= ORC_MAX_TRIES; ++b) {
+            double v[4];
+            draw4(p, 0u, b, pid, v);
+            double Y = v[0] * p->pitch * p->cells_y;
+            double Z = v[1] * p->pitch * p->cells_z;
+            int64_t cy = (int64_t)floor(Y / p->pitch), cz = (int64_t)floor(Z / p->pitch);
+            if (cy >= p->cells_y) cy = p->cells_y - 1;
+            if (cz >= p->cells_z) cz = p->cells_z - 1;
+            double yl = Y - cy * p->pitch, zl = Z - cz * p->pitch;
+            s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;
+            if (!in_pore(p, yl, zl)) break;
         }
     } else { /* ORC_SRC_PULSE: surface heat pulse on the top face x = L */
         s->sign = 1;
@@ -679,10 +707,14 @@ static int validate(const orc_problem* p)
 {
     if (p->max_events < 1) return -1;
     if (p->geom_kind < 0 || p->geom_kind > 2) return -1;
-    if (p->src_kind < 0 || p->src_kind > 2) return -1;
+    if (p->src_kind < 0 || p->src_kind > 3) return -1;
     if (p->geom_kind != ORC_GEOM_BULK && !(p->L > 0.0)) return -1;
     if (p->src_kind == ORC_SRC_WALLS && p->geom_kind != ORC_GEOM_PLANES) return -1;
     if (p->src_kind == ORC_SRC_PULSE && p->geom_kind != ORC_GEOM_POROUS) return -1;
+    if (p->src_kind == ORC_SRC_INITIAL &&
+        (p->geom_kind != ORC_GEOM_POROUS || !(p->t_final > 0.0) || p->init_dT == 0.0 ||
+         !(p->init_x_lo >= 0.0) || !(p->init_x_hi <= p->L) || !(p->init_x_hi > p->init_x_lo)))
+        return -1;
     if (p->geom_kind == ORC_GEOM_POROUS &&
         (!(p->pitch > 0.0) || p->radius < 0.0 || 2.0 * p->radius >= p->pitch || p->cells_y < 1 || p->cells_z < 1))
         return -1;
@@ -776,6 +808,11 @@ int orc_run(const orc_problem* p, orc_result* res, double* T_mean, double* T_se,
         res->P_total = P;
         res->E_eff_dot = P / Nd;
         res->E_eff = p->src_kind == ORC_SRC_PULSE ? p->pulse_energy / Nd : 0.0;
+        if (p->src_kind == ORC_SRC_INITIAL) {
+            /* deviational energy of the initial condition: C_tot |T_i - T_eq| V */
+            double area = (p->pitch * p->pitch - ORC_PI * p->radius * p->radius) * p->cells_y * p->cells_z;
+            res->E_eff = m.C_tot * fabs(p->init_dT) * (p->init_x_hi - p->init_x_lo) * area / Nd;
+        }
         res->C_tot = m.C_tot;
         res->sum_sL = tot.sum_sL;
         res->sum_sL2 = tot.sum_sL2;
@@ -871,7 +908,8 @@ int orc_draw_modes(const orc_problem* p, int which, const double* u, int n, int3
     orc_mat m;
     memset(&m, 0, sizeof(m));
     if (mat_build(p, &m)) { mat_free(&m); return -1; }
-    for (int i = 0; i < n; ++i) out[i] = draw_mode(which ? m.cdf_scat : m.cdf_emit, m.n, u[i]);
+    const double* cdf = which == 2 ? m.cdf_init : (which ? m.cdf_scat : m.cdf_emit);
+    for (int i = 0; i < n; ++i) out[i] = draw_mode(cdf, m.n, u[i]);
     mat_free(&m);
     return 0;
 }

@@ -39,7 +39,7 @@ _LIB = os.path.join(_HERE, "liblemc_oracle.so")
 MAT = {"gray": 0, "quadratic": 1}
 GEOM = {"planes": 0, "bulk": 1, "porous": 2}
 WALL = {"black": 0, "diffuse": 1, "specular": 2}
-SRC = {"walls": 0, "gradient": 1, "pulse": 2}
+SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
 FATE = {0: "absorbed", 1: "max_scatter", 2: "max_events", 3: "t_final"}
 
 
@@ -56,6 +56,7 @@ class Problem(C.Structure):
         ("dT_lo", C.c_double), ("dT_hi", C.c_double), ("dTdz", C.c_double),
         ("pulse_sigma_x", C.c_double), ("pulse_sigma_t", C.c_double), ("pulse_t_center", C.c_double),
         ("pulse_energy", C.c_double), ("pulse_y0", C.c_double), ("pulse_z0", C.c_double),
+        ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double),
         ("n_particles", C.c_uint64), ("seed", C.c_uint64),
         ("instance_id", C.c_uint32), ("max_scatter", C.c_uint32), ("max_events", C.c_uint32),
         ("n_bins_x", C.c_int32), ("n_batch", C.c_int32),
@@ -179,6 +180,8 @@ def to_problem(prob, n_threads=None, record_particles=False):
     p.pulse_sigma_x, p.pulse_sigma_t = s.get("sigma_x", 0.0), s.get("sigma_t", 0.0)
     p.pulse_t_center, p.pulse_energy = s.get("t_center", 0.0), s.get("energy", 0.0)
     p.pulse_y0, p.pulse_z0 = s.get("y0", 0.0), s.get("z0", 0.0)
+    p.init_dT = s.get("dT", 0.0)
+    p.init_x_lo, p.init_x_hi = s.get("x_lo", 0.0), s.get("x_hi", 0.0)
     p.n_particles, p.seed, p.instance_id = r["n_particles"], r["seed"], r.get("instance_id", 0)
     p.max_scatter, p.max_events = r.get("max_scatter", 0), r.get("max_events", 1 << 20)
     p.n_bins_x, p.n_batch = r.get("n_bins_x", 0), r.get("n_batch", 32)
@@ -246,11 +249,12 @@ def material(prob):
 
 
 def draw_modes(prob, which, u):
-    """Inverse-CDF mode draws for uniforms ``u``: which = 'emit' or 'scatter'."""
+    """Inverse-CDF mode draws for uniforms ``u``: which = 'emit', 'scatter' or 'initial'."""
     p = to_problem(prob)
     u = np.ascontiguousarray(u, dtype=np.float64)
     out = np.zeros(u.size, dtype=np.int32)
-    rc = lib().orc_draw_modes(C.byref(p), 1 if which == "scatter" else 0, u.ctypes.data, u.size,
+    code = {"emit": 0, "scatter": 1, "initial": 2}[which]
+    rc = lib().orc_draw_modes(C.byref(p), code, u.ctypes.data, u.size,
                               out.ctypes.data)
     if rc:
         raise ValueError("bad material")

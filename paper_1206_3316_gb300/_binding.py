@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "TIMEOUT", 5: "
 MAT = {"gray": 0, "quadratic": 1, "tabulated": 2}
 GEOM = {"planes": 0, "bulk": 1, "porous": 2}
 WALL = {"black": 0, "diffuse": 1, "specular": 2}
-SRC = {"walls": 0, "gradient": 1, "pulse": 2}
+SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
 PREC = {"fp64": 0, "fp32": 1}
 ARRAY = {"T": 0, "T_se": 1, "q": 2, "q_se": 3, "H": 4, "H_se": 5, "grid": 6, "particles": 7}
 MAX_BRANCHES = 4
@@ -64,7 +64,8 @@ class RunDesc(C.Structure):
                 ("n_hj", C.c_int32), ("record_particles", C.c_int32),
                 ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32),
                 ("schedule", C.c_int32), ("refill_min", C.c_int32), ("long_mfp_cut", C.c_double),
-                ("chunk", C.c_int32), ("first_particle", C.c_uint32)]
+                ("chunk", C.c_int32), ("first_particle", C.c_uint32),
+                ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double)]
 
 
 class Tallies(C.Structure):
@@ -244,6 +245,8 @@ def run_desc(src, run, launch=None):
     r.refill_min = int(launch.get("refill_min", run.get("refill_min", 0)))
     r.chunk = int(launch.get("chunk", run.get("chunk", 0)))
     r.first_particle = int(run.get("first_particle", 0))
+    r.init_dT = float(src.get("dT", 0.0)) if src["kind"] == "initial" else 0.0
+    r.init_x_lo, r.init_x_hi = float(src.get("x_lo", 0.0)), float(src.get("x_hi", 0.0))
     return r
 
 

@@ -70,6 +70,7 @@ struct le_mc_material_s {
     void* d_props64 = nullptr;   // double2[n]
     uint2* d_alias_scat = nullptr;
     uint2* d_alias_emit = nullptr;
+    uint2* d_alias_init = nullptr;
 };
 
 struct le_mc_geometry_s {
@@ -115,6 +116,7 @@ void material_release(le_mc_material m)
     if (m->d_props64) cudaFreeAsync(m->d_props64, 0);
     if (m->d_alias_scat) cudaFreeAsync(m->d_alias_scat, 0);
     if (m->d_alias_emit) cudaFreeAsync(m->d_alias_emit, 0);
+    if (m->d_alias_init) cudaFreeAsync(m->d_alias_init, 0);
     cudaSetDevice(cur);
     delete m;
 }
@@ -140,6 +142,7 @@ bool material_view(le_mc_material m, MaterialView* out)
     out->props64 = m->d_props64;
     out->alias_scat = m->d_alias_scat;
     out->alias_emit = m->d_alias_emit;
+    out->alias_init = m->d_alias_init;
     out->n_modes = m->n_modes;
     out->device = m->device;
     out->sums = m->sums;
@@ -251,14 +254,16 @@ le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_materi
         props32[2 * i] = (float)lam;
         props32[2 * i + 1] = (float)m->v[i];
     }
-    std::vector<uint32_t> thr_e(n), al_e(n), thr_s(n), al_s(n);
+    std::vector<uint32_t> thr_e(n), al_e(n), thr_s(n), al_s(n), thr_i(n), al_i(n);
     st = build_alias(w_emit.data(), n, thr_e.data(), al_e.data(), &why);
     if (st == LE_MC_OK) st = build_alias(w_scat.data(), n, thr_s.data(), al_s.data(), &why);
+    if (st == LE_MC_OK) st = build_alias(m->C.data(), n, thr_i.data(), al_i.data(), &why);  // initial condition
     if (st != LE_MC_OK) { delete m; return fail((le_mc_status)st, "le_mc_create_material", why); }
-    std::vector<uint2> ae(n), as(n);
+    std::vector<uint2> ae(n), as(n), ai(n);
     for (int i = 0; i < n; ++i) {
         ae[i] = make_uint2(thr_e[i], al_e[i]);
         as[i] = make_uint2(thr_s[i], al_s[i]);
+        ai[i] = make_uint2(thr_i[i], al_i[i]);
     }
     // stream-ordered pool on the legacy stream, complete before returning
     cudaError_t e = cudaGetDevice(&m->device);
@@ -266,10 +271,12 @@ le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_materi
     if (e == cudaSuccess) e = cudaMallocAsync(&m->d_props64, props64.size() * sizeof(double), 0);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_scat, n * sizeof(uint2), 0);
     if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_emit, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_init, n * sizeof(uint2), 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props32, props32.data(), props32.size() * sizeof(float), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props64, props64.data(), props64.size() * sizeof(double), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_scat, as.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_emit, ae.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_init, ai.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         material_release(m);
@@ -377,6 +384,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.props = fp32 ? m->d_props32 : m->d_props64;
     P.alias_scat = m->d_alias_scat;
     P.alias_emit = m->d_alias_emit;
+    P.alias_init = m->d_alias_init;
     P.n_modes = m->n_modes;
     const le_mc_geometry_desc& G = g->desc;
     P.geom = G.kind;
@@ -397,6 +405,9 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.p_tc = r.pulse_t_center;
     P.p_y0 = r.pulse_y0;
     P.p_z0 = r.pulse_z0;
+    P.init_dT = r.init_dT;
+    P.init_x_lo = r.init_x_lo;
+    P.init_x_hi = r.init_x_hi;
     P.n_particles = (uint32_t)r.n_particles;
     P.key0 = (uint32_t)r.seed;
     P.key1 = (uint32_t)(r.seed >> 32);
@@ -413,7 +424,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.gz = r.grid_nz;
     P.n_samples = r.n_samples;
     P.sample_dt = r.sample_dt;
-    P.t_final = r.source == LE_MC_SRC_PULSE ? r.t_final : 0.0;
+    P.t_final = (r.source == LE_MC_SRC_PULSE || r.source == LE_MC_SRC_INITIAL) ? r.t_final : 0.0;
     P.grid = reinterpret_cast<int32_t*>(h->dev + h->off_grid);
     P.records = r.record_particles ? reinterpret_cast<le_mc_particle*>(h->dev + h->off_records) : nullptr;
     P.sums = reinterpret_cast<double*>(h->dev + h->off_sums);

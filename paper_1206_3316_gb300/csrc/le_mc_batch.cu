@@ -185,7 +185,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", why);
         if (geoms[i].kind != LE_MC_GEOM_PLANES)
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "batches take PLANES geometries");
-        if (runs[i].source == LE_MC_SRC_PULSE)
+        if (runs[i].source == LE_MC_SRC_PULSE || runs[i].source == LE_MC_SRC_INITIAL)
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "batches take WALLS or GRADIENT sources");
         if (runs[i].first_particle != 0)
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "batch instances start at particle 0");

@@ -184,6 +184,16 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
     case LE_MC_SRC_GRADIENT:
         if (!(r->dTdz != 0.0) || !isfinite(r->dTdz)) { *why = "GRADIENT source needs dTdz != 0"; return LE_MC_ERR_INVALID; }
         break;
+    case LE_MC_SRC_INITIAL:
+        if (g->kind != LE_MC_GEOM_POROUS) { *why = "INITIAL source needs POROUS geometry"; return LE_MC_ERR_INVALID; }
+        if (!(r->init_dT != 0.0) || !isfinite(r->init_dT)) { *why = "INITIAL needs init_dT != 0"; return LE_MC_ERR_INVALID; }
+        if (!(r->init_x_lo >= 0.0) || !(r->init_x_hi <= g->L) || !(r->init_x_hi > r->init_x_lo)) {
+            *why = "INITIAL needs 0 <= init_x_lo < init_x_hi <= L";
+            return LE_MC_ERR_INVALID;
+        }
+        if (r->n_particles > 0x7FFFFFFFull) { *why = "INITIAL n_particles must be < 2^31"; return LE_MC_ERR_INVALID; }
+        if (!(r->t_final > 0.0)) { *why = "INITIAL needs t_final > 0"; return LE_MC_ERR_INVALID; }
+        break;
     case LE_MC_SRC_PULSE:
         if (g->kind != LE_MC_GEOM_POROUS) { *why = "PULSE source needs POROUS geometry"; return LE_MC_ERR_INVALID; }
         if (!(r->pulse_sigma_x > 0.0) || !(r->pulse_sigma_t > 0.0) || !(r->pulse_energy > 0.0)) {
@@ -205,7 +215,10 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
     if (r->n_hj < 0 || r->n_hj > LE_MC_MAX_HJ) { *why = "n_hj out of range"; return LE_MC_ERR_INVALID; }
     if (r->n_samples < 0) { *why = "n_samples < 0"; return LE_MC_ERR_INVALID; }
     if (r->n_samples > 0) {
-        if (r->source != LE_MC_SRC_PULSE) { *why = "grid samples need the PULSE source"; return LE_MC_ERR_INVALID; }
+        if (r->source != LE_MC_SRC_PULSE && r->source != LE_MC_SRC_INITIAL) {
+            *why = "grid samples need the PULSE or INITIAL source";
+            return LE_MC_ERR_INVALID;
+        }
         if (r->grid_nx < 1 || r->grid_ny < 1 || r->grid_nz < 1 || !(r->sample_dt > 0.0)) {
             *why = "grid needs nx, ny, nz >= 1 and sample_dt > 0";
             return LE_MC_ERR_INVALID;
@@ -268,6 +281,12 @@ void normalize(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const Mate
     out->P_total = P;
     out->E_eff_dot = P / N;
     out->E_eff = r->source == LE_MC_SRC_PULSE ? r->pulse_energy / N : 0.0;
+    if (r->source == LE_MC_SRC_INITIAL) {
+        // deviational energy of the initial condition: C_tot |T_i - T_eq| V (solid part of the layer)
+        const double pi = 3.141592653589793;
+        const double area = (g->pitch * g->pitch - pi * g->radius * g->radius) * g->cells_y * g->cells_z;
+        out->E_eff = ms.C_tot * fabs(r->init_dT) * (r->init_x_hi - r->init_x_lo) * area / N;
+    }
     out->C_tot = ms.C_tot;
     out->sum_sL = sums[0];
     out->sum_sL2 = sums[1];

@@ -47,6 +47,7 @@ struct TraceParams {
     const void* props;        // float2 or double2 [n_modes]: (Lambda_b, v_b)
     const uint2* alias_scat;  // [n_modes] (threshold, alias) for C_b / tau_b
     const uint2* alias_emit;  // [n_modes] (threshold, alias) for C_b v_b
+    const uint2* alias_init;  // [n_modes] (threshold, alias) for C_b (initial condition)
     int32_t n_modes;
     // geometry
     int32_t geom, wall_lo, wall_hi, pore_wall;
@@ -56,6 +57,7 @@ struct TraceParams {
     int32_t src;
     double dT_lo, dT_hi, dTdz;
     double p_sx, p_st, p_tc, p_y0, p_z0;
+    double init_dT, init_x_lo, init_x_hi;
     // run
     uint32_t n_particles, key0, key1, inst, max_scatter, max_events;
     // slab profile: [4][n_batch][n_bins_x + 1] (T direct, T difference,
@@ -114,6 +116,7 @@ struct MaterialView {
     const void* props64;
     const uint2* alias_scat;
     const uint2* alias_emit;
+    const uint2* alias_init;
     int n_modes;
     int device;
     MaterialSums sums;

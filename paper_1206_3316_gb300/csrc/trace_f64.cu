@@ -50,6 +50,8 @@ cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t*
         return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_GRADIENT, false>(__VA_ARGS__);                        \
     if (geom == LE_MC_GEOM_POROUS && src == LE_MC_SRC_PULSE)                                         \
         return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_PULSE, false>(__VA_ARGS__);                           \
+    if (geom == LE_MC_GEOM_POROUS && src == LE_MC_SRC_INITIAL)                                       \
+        return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_INITIAL, false>(__VA_ARGS__);                         \
     return cudaErrorInvalidValue;
 
 cudaError_t launch_trace_f64(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,

@@ -196,6 +196,32 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
                 if (!(dy * dy + dz * dz < r2)) { ok = true; break; }
             }
         }
+    } else if constexpr (SRC == LE_MC_SRC_INITIAL) {
+        // initial condition: uniform in the heated layer (solid part), modes
+        // weighted by C_b (table passed by the caller), isotropic, t = 0
+        sign = P.init_dT >= 0.0 ? 1 : -1;
+        const R mu = R(2) * u2 - R(1);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        ox = st * cs;
+        oy = st * sn;
+        oz = mu;
+        x = (R)P.init_x_lo + u0 * (R)(P.init_x_hi - P.init_x_lo);
+        const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
+        ok = false;
+        for (uint32_t b = 1; b <= kMaxTries; ++b) {
+            const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
+            const R Y = M::uniform(q.x) * pitch * (R)P.cells_y;
+            const R Z = M::uniform(q.y) * pitch * (R)P.cells_z;
+            int iy = (int)M::floor_(Y / pitch), iz = (int)M::floor_(Z / pitch);
+            iy = min(max(iy, 0), P.cells_y - 1);
+            iz = min(max(iz, 0), P.cells_z - 1);
+            y = Y - (R)iy * pitch;
+            z = Z - (R)iz * pitch;
+            cy = (uint32_t)iy;
+            cz = (uint32_t)iz;
+            const R dy = y - half, dz = z - half;
+            if (!(dy * dy + dz * dz < r2)) { ok = true; break; }
+        }
     } else {  // PULSE on the top face x = L, all signs positive
         sign = 1;
         const R mu = M::sqrt_(u2);
@@ -242,7 +268,7 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
 
 template <typename R, int SRC, bool PROFILE>
 struct FusedTable {
-    static constexpr bool value = sizeof(R) == 4 && SRC != LE_MC_SRC_PULSE && !PROFILE;
+    static constexpr bool value = sizeof(R) == 4 && SRC != LE_MC_SRC_PULSE && SRC != LE_MC_SRC_INITIAL && !PROFILE;
 };
 
 // Bytes of the per-mode tables at the start of shared memory (16-aligned).
@@ -259,7 +285,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     using M = DMath<R>;
     using Buf = BufferOf<R, GEOM, SRC, BATCH>;
     constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
-    constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE);
+    constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
     // Kernels whose estimators never need the group velocity (steady path
     // integrals) keep one 16-byte word per mode: (threshold, alias,
@@ -456,7 +482,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                     R ex, ey, ez, eox, eoy, eoz, et;
                     uint32_t em, ecy, ecz;
                     int es;
-                    if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es,
+                    if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es,
                                                      ecy, ecz))
                         flags |= FLAG_REJECTION_EXHAUSTED;
                     const int slot = cnt + __popc(vmask & lanemask_lt);
@@ -471,7 +497,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                         buf.z.v[slot] = ez;
                         buf.cell.v[slot] = ecy | (ecz << 16);
                     }
-                    if constexpr (TRANSIENT) buf.t.v[slot] = et;
+                    if constexpr (SRC == LE_MC_SRC_PULSE) buf.t.v[slot] = et;
                     if constexpr (BATCH) buf.inst.v[slot] = eb;
                 }
                 cnt += __popc(vmask);
@@ -494,7 +520,8 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                         cy = (int)(cell & 0xFFFFu);
                         cz = (int)(cell >> 16);
                     }
-                    if constexpr (TRANSIENT) t = buf.t.v[slot];
+                    if constexpr (SRC == LE_MC_SRC_PULSE) t = buf.t.v[slot];
+                    if constexpr (SRC == LE_MC_SRC_INITIAL) t = R(0);
                     if constexpr (BATCH) {
                         bidx = buf.inst.v[slot];
                         const BatchInstance& bi = P.instances[bidx];
@@ -814,7 +841,8 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
                 cut = (R)P.instances[b].lam_cut;
             }
             const uint4 r = philox4x32_10(make_uint4(0u, 0u, id, inst), args.rk);
-            const uint32_t mode = alias_draw(P.alias_emit, (uint32_t)P.n_modes, r.y);
+            const uint2* table = P.src == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit;
+            const uint32_t mode = alias_draw(table, (uint32_t)P.n_modes, r.y);
             R lam, vg;
             load_props<R>(P.props, mode, lam, vg);
             is_long = lam > cut;

@@ -260,3 +260,29 @@ def test_pieces_add_up(P):
         assert a[k] + b[k] == whole[k]
     assert a["sum_sL"] + b["sum_sL"] == pytest.approx(whole["sum_sL"], rel=1e-9, abs=1e-20)
     assert a["sum_sL2"] + b["sum_sL2"] == pytest.approx(whole["sum_sL2"], rel=1e-9)
+
+
+def test_gray_initial_condition_grid_bit_exact(P, oracle):
+    prob = W.porous_initial(n_particles=3000, precision="fp64", x_range=(150e-9, 300e-9), radius=20e-9,
+                            material=dict(W.GRAY_UNIT, tau=1e-11, v=3000.0), grid=(8, 6, 6), n_samples=30,
+                            sample_dt=20e-12, t_final=6e-10)
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"], atol=3e-8 * 1e-6)
+    assert np.array_equal(g["grid"].astype(np.int64), o["grid"])
+    assert g["E_eff"] == pytest.approx(o["E_eff"], rel=1e-12)
+
+
+def test_initial_condition_fp32_conserves_and_stays_uniform(P):
+    from tests.test_oracle_porous import uniform_equilibrium_pvalues
+    n = 2_000_000
+    prob = W.porous_initial(n_particles=n, precision="fp32")
+    g = P.simulate(prob)
+    sums = g["grid"].reshape(g["grid"].shape[0], -1).sum(axis=1)
+    assert np.all(sums == n)
+    assert min(uniform_equilibrium_pvalues(g["grid"], prob["geometry"])) > 1e-4
+    # a heated top layer relaxes: its share of the energy falls toward the layer's volume share
+    top = W.porous_initial(n_particles=n, precision="fp32", x_range=(250e-9, 300e-9))
+    h = P.simulate(top)["grid"].astype(np.float64)
+    share = h[:, :, :, -3:].sum(axis=(1, 2, 3)) / n   # top 3 of 16 x-cells
+    assert share[0] > 0.8 and share[-1] < share[0] and abs(share[-1] - 3 / 16) < 0.1

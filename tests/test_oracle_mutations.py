@@ -37,13 +37,24 @@ def _nongray_pin_ok(oracle, analytic, library):
     return abs(r["psi"] - pin) < 4.0 * r["psi_se"]
 
 
+def _uniform_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_porous import uniform_equilibrium_pvalues
+    p = W.porous_initial(n_particles=200_000, precision="fp64", radius=0.0)
+    r = oracle.run(p, library=library)
+    return min(uniform_equilibrium_pvalues(r["grid"], p["geometry"])) > 1e-4
+
+
 MUTATIONS = [
+    ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
+     "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
     # (name, original text, planted mistake, pin that must catch it)
     # (a law that only folds directions into one z hemisphere is invisible to
     # every steady estimator here: the gradient source emits equal numbers of
     # each sign and a hemisphere projects onto x like the sphere; the planted
     # law below is genuinely anisotropic)
-    ("scattering not isotropic", "dir_axis(2, 2.0 * u[2] - 1.0, u[3]", "dir_axis(2, 2.0 * u[2] * u[2] - 1.0, u[3]",
+    ("scattering not isotropic",
+     "s.mode = draw_mode(m->cdf_scat, m->n, u[1]);\n            dir_axis(2, 2.0 * u[2] - 1.0, u[3]",
+     "s.mode = draw_mode(m->cdf_scat, m->n, u[1]);\n            dir_axis(2, 2.0 * u[2] * u[2] - 1.0, u[3]",
      _psi_pin_ok),
     ("bulk flight with wrong mean free path", "double dist = m->Lambda[s.mode] * -log(u[0]);",
      "double dist = 0.5 * m->Lambda[s.mode] * -log(u[0]);", _bulk_pin_ok),

@@ -108,3 +108,64 @@ def test_transient_energy_conservation(oracle):
     assert np.array_equal(grid.reshape(40, -1).sum(axis=1), emitted)
     assert np.all(grid >= 0)
     assert np.all(rec["fate"] == 3)
+
+
+def _solid_fraction_yz(geo, ny, nz, sub=64):
+    """Solid area fraction of each (y, z) grid column of the periodic domain."""
+    Dy, Dz = geo["pitch"] * geo["cells_y"], geo["pitch"] * geo["cells_z"]
+    frac = np.zeros((nz, ny))
+    for iz in range(nz):
+        for iy in range(ny):
+            ys = (iy + (np.arange(sub) + 0.5) / sub) * Dy / ny
+            zs = (iz + (np.arange(sub) + 0.5) / sub) * Dz / nz
+            Y, Z = np.meshgrid(np.mod(ys, geo["pitch"]) - 0.5 * geo["pitch"],
+                               np.mod(zs, geo["pitch"]) - 0.5 * geo["pitch"])
+            frac[iz, iy] = np.mean(Y * Y + Z * Z >= geo["radius"] ** 2)
+    return frac
+
+
+def uniform_equilibrium_pvalues(grid, geo, times=(0, 10, 25, 49)):
+    """p-values of 'counts are proportional to solid volume' at sample times."""
+    from scipy import stats
+    ns, nz, ny, nx = grid.shape
+    w = np.repeat(_solid_fraction_yz(geo, ny, nz)[:, :, None], nx, axis=2)
+    out = []
+    for k in times:
+        c = grid[k].astype(np.float64)
+        e = c.sum() * w / w.sum()
+        m = e > 0
+        chi2 = (((c - e) ** 2)[m] / e[m]).sum()
+        out.append(stats.chi2.sf(chi2, m.sum() - 1))
+    return out
+
+
+def test_initial_condition_energy_and_modes(oracle, analytic):
+    n = 20_000
+    p = W.porous_initial(n_particles=n, precision="fp64", x_range=(200e-9, 300e-9))
+    r = oracle.run(p, record_particles=True)
+    assert np.all(r["grid"].reshape(r["grid"].shape[0], -1).sum(axis=1) == n)  # exact, adiabatic walls
+    rec = r["particles_rec"]
+    assert np.all(rec["t0"] == 0.0) and np.all((rec["x0"] > 200e-9) & (rec["x0"] < 300e-9))
+    area = (100e-9 ** 2 - np.pi * 30e-9 ** 2)
+    assert r["E_eff"] == pytest.approx(r["C_tot"] * 1.0 * 100e-9 * area / n, rel=1e-12)
+    # modes of the initial condition follow C_b (not C_b v_b)
+    from scipy import stats
+    _, v, tau, C = analytic.mode_table(W.SILICON_LIKE)
+    u = (np.random.default_rng(4).integers(0, 2 ** 32, 400_000, dtype=np.uint64) + 0.5) / 2.0 ** 32
+    modes = oracle.draw_modes(p, "initial", u)
+    counts = np.bincount(modes, minlength=C.size)
+    e = C / C.sum() * u.size
+    keep = e > 20
+    chi2 = ((counts[keep] - e[keep]) ** 2 / e[keep]).sum() + (counts[~keep].sum() - e[~keep].sum()) ** 2 / e[~keep].sum()
+    assert stats.chi2.sf(chi2, keep.sum()) > 1e-4
+
+
+@pytest.mark.parametrize("radius", [0.0, 30e-9])
+def test_uniform_initial_excess_stays_uniform(oracle, radius):
+    # A uniform, isotropic excess with mode weights C_b is the linearized
+    # equilibrium shape: free flights, Eq. 2 redraws and Lambertian walls must
+    # all preserve it, so the counts stay proportional to the solid volume.
+    p = W.porous_initial(n_particles=200_000, precision="fp64", radius=radius)
+    r = oracle.run(p)
+    pv = uniform_equilibrium_pvalues(r["grid"], p["geometry"])
+    assert min(pv) > 1e-4, pv

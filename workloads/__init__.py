@@ -147,6 +147,26 @@ def porous_pulse(n_particles=100_000_000, seed=0x5EED_0000_0005, precision="fp32
     }
 
 
+def porous_initial(n_particles=1_000_000, seed=0x5EED_0000_0007, precision="fp32", dT=1.0,
+                   x_range=None, grid=(16, 8, 8), n_samples=50, sample_dt=20e-12, t_final=1e-9,
+                   cells=(1, 1), material=None, thickness=300e-9, pitch=100e-9, radius=30e-9,
+                   max_events=1 << 20):
+    """Transient relaxation of an initial temperature excess dT in the layer
+    x_range (default: the whole thickness) of a periodic porous film with
+    adiabatic diffuse walls; particle counts on a grid at n_samples times."""
+    lo, hi = x_range if x_range is not None else (0.0, thickness)
+    return {
+        "material": copy.deepcopy(material or SILICON_LIKE),
+        "geometry": {"kind": "porous", "L": float(thickness), "wall_lo": "diffuse",
+                     "wall_hi": "diffuse", "pitch": float(pitch), "radius": float(radius),
+                     "pore_wall": "diffuse", "cells_y": int(cells[0]), "cells_z": int(cells[1])},
+        "source": {"kind": "initial", "dT": float(dT), "x_lo": float(lo), "x_hi": float(hi)},
+        "run": _run(n_particles=n_particles, seed=seed, max_scatter=0, max_events=max_events,
+                    precision=precision, t_final=float(t_final), sample_dt=float(sample_dt),
+                    grid=tuple(int(g) for g in grid), n_samples=int(n_samples)),
+    }
+
+
 def batched_films(n_instances=256, seed=2012, n_min=1e4, n_max=1e7, L_min=10e-9, L_max=100e-6,
                   precision="fp32"):
     """Many silicon-like films of uneven size: thickness log-uniform in
