@@ -527,7 +527,9 @@ static void tally_transient(const orc_problem* p, const orc_mat* m, orc_tally* t
 {
     double dts = p->sample_dt;
     double t_end = t_b < p->t_final ? t_b : p->t_final;
-    long k = (long)ceil(t_a / dts - 0.5);
+    /* the rounded quotient can land one past the first t'_k >= t_a; start one
+     * early and let the exact comparisons below decide */
+    long k = (long)ceil(t_a / dts - 0.5) - 1;
     if (k < 0) k = 0;
     double Dy = p->pitch * p->cells_y, Dz = p->pitch * p->cells_z;
     double vg = m->v[s->mode];

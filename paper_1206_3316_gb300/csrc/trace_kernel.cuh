@@ -279,7 +279,9 @@ __host__ __device__ inline size_t table_bytes(int n_modes)
     return ((size_t)n_modes * per_mode + 15) & ~(size_t)15;
 }
 
-template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false>
+// DIFF: every wall (both planes, and the pores) is diffuse, so the wall law
+// needs no per-wall lookup and no specular or absorbing branch.
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
 {
     using M = DMath<R>;
@@ -607,12 +609,18 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         if (hit && kind == HIT_XLO) x_new = R(0);
         if (hit && kind == HIT_XHI) x_new = Lp;
 
+        // end time of the segment, computed once: the sample windows [t, t_b)
+        // of consecutive segments must tile time exactly (no sample lost or
+        // counted twice), so the particle's next start is this same value
+        R t_b = t;
+        if constexpr (TRANSIENT) t_b = t + seg / vg;
         // step V: contribution of the segment
         if constexpr (TRANSIENT) {
             const R dts = (R)P.sample_dt;
-            const R t_b = t + seg / vg;
             const R t_end = fmin(t_b, (R)P.t_final);
-            int k = (int)ceil(t / dts - R(0.5));
+            // first candidate sample, one early: the rounded quotient may
+            // overshoot by one, and the comparisons below decide exactly
+            int k = (int)ceil(t / dts - R(0.5)) - 1;
             k = max(k, 0);
             const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
             const int wy = cy % P.cells_y, wz = cz % P.cells_z;
@@ -686,11 +694,13 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             y += oy * seg;
             z += oz * seg;
         }
-        if constexpr (TRANSIENT) t += seg / vg;
+        if constexpr (TRANSIENT) t = t_b;
         ++n_seg;
         const bool scat = !hit;
         int wall = -1;
-        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+        if constexpr (DIFF) {
+            wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
+        } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
             wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
             if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
             wall = hit ? wall : -1;
