@@ -328,7 +328,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--n-particles", type=int, default=N_PARTICLES)
-    ap.add_argument("--threads-per-block", type=int, default=256)
+    ap.add_argument("--threads-per-block", type=int, default=0, help="0 = library default")
+    ap.add_argument("--refill-min", type=int, default=0, help="0 = library default")
+    ap.add_argument("--chunk", type=int, default=0, help="0 = library default")
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
@@ -359,7 +361,8 @@ def main():
     __graft_entry__.build()
     import paper_1206_3316_gb300 as P
     prob = rank_problem(problem, rank, world)
-    launch = {"threads_per_block": args.threads_per_block, "blocks_per_sm": args.blocks_per_sm}
+    launch = {"threads_per_block": args.threads_per_block, "blocks_per_sm": args.blocks_per_sm,
+              "refill_min": args.refill_min, "chunk": args.chunk}
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > 129 MB L2
 
@@ -459,8 +462,9 @@ def main():
         "config": {"workload": WORKLOAD, "n_particles": args.n_particles, "form": "plain",
                    "tallies": "per-particle FP32 sums, FP64 accumulation",
                    "l2": "flushed between steps (256 MiB write)",
-                   "launch": {"threads_per_block": args.threads_per_block or 256,
-                              "blocks_per_sm": args.blocks_per_sm or "occupancy"},
+                   "launch": {"threads_per_block": args.threads_per_block or 512,
+                              "blocks_per_sm": args.blocks_per_sm or "occupancy",
+                              "refill_min": args.refill_min or 4, "chunk": args.chunk or 256},
                    "kappa_W_per_mK": statistics.mean(kappas), "device": name, "sms": sms,
                    "wall_s_timed_region": wall},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

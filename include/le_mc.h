@@ -178,7 +178,7 @@ typedef struct {
     int32_t n_hj;                   /* flux split by scattering index j (0 = off) */
     int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
     int32_t blocks_per_sm;          /* launch shape (0 = library default)        */
-    int32_t threads_per_block;      /* 0 = default; multiple of 32, <= 512       */
+    int32_t threads_per_block;      /* 0 = default (512); multiple of 32, <= 512 */
     int32_t schedule;               /* particle order: 0 auto, 1 long-first,
                                      * 2 natural id order.  Long-first serves
                                      * particles emitted in modes with a mean
@@ -188,10 +188,10 @@ typedef struct {
                                      * do not depend on the order (up to FP64
                                      * summation order).                       */
     int32_t refill_min;             /* a warp refills idle lanes once this many
-                                     * are idle (0 = 1: at once)                 */
+                                     * are idle (0 = library default, 4)         */
     double long_mfp_cut;            /* [m]; 0 = 32 L (PLANES, POROUS)            */
     int32_t chunk;                  /* queue positions a warp claims per atomic,
-                                     * multiple of 32 (0 = 32)                   */
+                                     * multiple of 32 (0 = library default, 256) */
     uint32_t first_particle;        /* particle ids traced are first_particle ..
                                      * first_particle + n_particles - 1 (< 2^32),
                                      * so a problem can be traced in pieces      */

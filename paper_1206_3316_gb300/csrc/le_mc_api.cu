@@ -19,6 +19,8 @@ cudaError_t launch_trace_f64(const KernelArgs& a, int geom, int src, bool profil
                              size_t smem, cudaStream_t st);
 cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
 cudaError_t occupancy_trace_f64(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
+cudaError_t occupancy_trace_for_f32(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm);
+cudaError_t occupancy_trace_for_f64(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm);
 cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
                            size_t* bytes);
 cudaError_t smem_trace_f64(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
@@ -431,8 +433,8 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.counters = reinterpret_cast<unsigned long long*>(h->dev + h->off_counters);
     P.queue = reinterpret_cast<unsigned int*>(h->dev + h->off_queue);
     P.flags = reinterpret_cast<unsigned int*>(h->dev + h->off_flags);
-    P.refill_min = r.refill_min > 0 ? r.refill_min : 1;
-    P.chunk = r.chunk > 0 ? r.chunk : 32;
+    P.refill_min = r.refill_min > 0 ? r.refill_min : kDefaultRefillMin;
+    P.chunk = r.chunk > 0 ? r.chunk : kDefaultChunk;
     P.first = r.first_particle;
     for (int i = 0; i < 10; ++i) {
         a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
@@ -447,7 +449,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     }
 
     // launch shape: persistent grid of (SMs x resident blocks)
-    int threads = r.threads_per_block > 0 ? r.threads_per_block : 512;
+    int threads = r.threads_per_block > 0 ? r.threads_per_block : kDefaultThreads;
     if (threads > 512) threads = 512;
     size_t smem = 0;
     e = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, threads, (int)h->prof_len, (int)h->hj_len, &smem)
@@ -456,8 +458,8 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     int per_sm = 0;
     if (e == cudaSuccess)
-        e = fp32 ? occupancy_trace_f32(G.kind, r.source, profile, threads, smem, &per_sm)
-                 : occupancy_trace_f64(G.kind, r.source, profile, threads, smem, &per_sm);
+        e = fp32 ? occupancy_trace_for_f32(P, profile, threads, smem, &per_sm)
+                 : occupancy_trace_for_f64(P, profile, threads, smem, &per_sm);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess && r.blocks_per_sm > 0 && r.blocks_per_sm < per_sm) per_sm = r.blocks_per_sm;
     int blocks = sms * per_sm;

@@ -16,10 +16,12 @@
 #include "trace_kernel.cuh"
 
 namespace lemc {
-cudaError_t batch_attr_f32(int src, int threads, size_t smem, int* per_sm);
-cudaError_t batch_attr_f64(int src, int threads, size_t smem, int* per_sm);
-cudaError_t batch_launch_f32(const KernelArgs& a, int src, int blocks, int threads, size_t smem, cudaStream_t st);
-cudaError_t batch_launch_f64(const KernelArgs& a, int src, int blocks, int threads, size_t smem, cudaStream_t st);
+cudaError_t batch_attr_f32(int src, bool diff, int threads, size_t smem, int* per_sm);
+cudaError_t batch_attr_f64(int src, bool diff, int threads, size_t smem, int* per_sm);
+cudaError_t batch_launch_f32(const KernelArgs& a, int src, bool diff, int blocks, int threads, size_t smem,
+                             cudaStream_t st);
+cudaError_t batch_launch_f64(const KernelArgs& a, int src, bool diff, int blocks, int threads, size_t smem,
+                             cudaStream_t st);
 cudaError_t launch_classify_f32(const KernelArgs& a, int blocks, cudaStream_t st);
 cudaError_t launch_classify_f64(const KernelArgs& a, int blocks, cudaStream_t st);
 size_t batch_smem_f32(int src, int n_modes, int threads, int n_instances);
@@ -71,6 +73,13 @@ void drop_graph(le_mc_batch b)
 }
 
 bool fp32(const le_mc_batch b) { return b->run0.precision == LE_MC_PREC_FP32; }
+
+// gradient-driven films whose walls are all diffuse use the specialised kernel
+bool all_diffuse(const le_mc_batch b)
+{
+    return b->run0.source == LE_MC_SRC_GRADIENT && b->geo0.wall_lo == LE_MC_WALL_DIFFUSE &&
+           b->geo0.wall_hi == LE_MC_WALL_DIFFUSE;
+}
 
 // Kernel arguments for the whole batch.
 KernelArgs make_args(le_mc_batch b)
@@ -134,7 +143,8 @@ cudaError_t shape(le_mc_batch b, int* blocks, int* threads, size_t* smem)
     const int src = b->run0.source;
     const size_t sm = fp32(b) ? batch_smem_f32(src, b->mv.n_modes, t, b->n) : batch_smem_f64(src, b->mv.n_modes, t, b->n);
     int per_sm = 0;
-    cudaError_t e = fp32(b) ? batch_attr_f32(src, t, sm, &per_sm) : batch_attr_f64(src, t, sm, &per_sm);
+    const bool d = all_diffuse(b);
+    cudaError_t e = fp32(b) ? batch_attr_f32(src, d, t, sm, &per_sm) : batch_attr_f64(src, d, t, sm, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (b->cfg.blocks_per_sm > 0 && b->cfg.blocks_per_sm < per_sm) per_sm = b->cfg.blocks_per_sm;
@@ -152,8 +162,8 @@ cudaError_t enqueue(le_mc_batch b, cudaStream_t st, int blocks, int threads, siz
     if (e == cudaSuccess && b->long_cap > 0)
         e = fp32(b) ? launch_classify_f32(a, b->sms * 8, st) : launch_classify_f64(a, b->sms * 8, st);
     if (e == cudaSuccess)
-        e = fp32(b) ? batch_launch_f32(a, b->run0.source, blocks, threads, smem, st)
-                    : batch_launch_f64(a, b->run0.source, blocks, threads, smem, st);
+        e = fp32(b) ? batch_launch_f32(a, b->run0.source, all_diffuse(b), blocks, threads, smem, st)
+                    : batch_launch_f64(a, b->run0.source, all_diffuse(b), blocks, threads, smem, st);
     return e;
 }
 

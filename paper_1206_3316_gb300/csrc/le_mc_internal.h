@@ -40,7 +40,15 @@ struct BatchInstance {
     uint32_t n_particles;
 };
 
-constexpr int kBatchSmemMax = 512;  // batches up to this size accumulate per block in shared memory
+constexpr int kBatchSmemMax = 512;
+
+// Default launch shape of le_mc_run: 512 threads per block, refill idle
+// lanes once 4 of a warp's 32 are idle, claim queue positions 256 at a time
+// (a GB300 sweep of the 1e7-particle film found this fastest; results do not
+// depend on the shape).
+constexpr int kDefaultThreads = 512;
+constexpr int kDefaultRefillMin = 4;
+constexpr int kDefaultChunk = 256;  // batches up to this size accumulate per block in shared memory
 
 struct TraceParams {
     // material tables (device pointers)

@@ -7,10 +7,10 @@
 namespace lemc {
 
 namespace {
-template <int G, int S, bool PR>
+template <int G, int S, bool PR, bool DF = false>
 cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem, cudaStream_t st)
 {
-    auto k = trace_kernel<float, G, S, PR>;
+    auto k = trace_kernel<float, G, S, PR, false, DF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (blocks <= 0) return cudaSuccess;
@@ -18,10 +18,10 @@ cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem
     return cudaGetLastError();
 }
 
-template <int G, int S, bool PR>
+template <int G, int S, bool PR, bool DF = false>
 cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
 {
-    auto k = trace_kernel<float, G, S, PR>;
+    auto k = trace_kernel<float, G, S, PR, false, DF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
@@ -54,15 +54,40 @@ cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t*
         return FN<LE_MC_GEOM_POROUS, LE_MC_SRC_INITIAL, false>(__VA_ARGS__);                         \
     return cudaErrorInvalidValue;
 
+// Films and porous films driven by a gradient with every wall diffuse use
+// the DIFF specialisation (same arithmetic, no wall-type lookups).
+static bool all_diffuse(const TraceParams& p)
+{
+    return p.src == LE_MC_SRC_GRADIENT && (p.geom == LE_MC_GEOM_PLANES || p.geom == LE_MC_GEOM_POROUS) &&
+           p.wall_lo == LE_MC_WALL_DIFFUSE && p.wall_hi == LE_MC_WALL_DIFFUSE &&
+           (p.geom != LE_MC_GEOM_POROUS || p.pore_wall == LE_MC_WALL_DIFFUSE);
+}
+
 cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
                               size_t smem, cudaStream_t st)
 {
+    if (all_diffuse(a.p) && !profile) {
+        if (geom == LE_MC_GEOM_PLANES)
+            return launch_one<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(a, blocks, threads, smem, st);
+        return launch_one<LE_MC_GEOM_POROUS, LE_MC_SRC_GRADIENT, false, true>(a, blocks, threads, smem, st);
+    }
     LEMC_DISPATCH(launch_one, a, blocks, threads, smem, st)
 }
 
 cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm)
 {
     LEMC_DISPATCH(occupancy_one, threads, smem, per_sm)
+}
+
+// Occupancy of the kernel that launch_trace picks for these parameters.
+cudaError_t occupancy_trace_for_f32(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm)
+{
+    if (all_diffuse(p) && !profile) {
+        if (p.geom == LE_MC_GEOM_PLANES)
+            return occupancy_one<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(threads, smem, per_sm);
+        return occupancy_one<LE_MC_GEOM_POROUS, LE_MC_SRC_GRADIENT, false, true>(threads, smem, per_sm);
+    }
+    return occupancy_trace_f32(p.geom, p.src, profile, threads, smem, per_sm);
 }
 
 cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
@@ -72,9 +97,10 @@ cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int thr
 }
 
 // Batch mode: PLANES geometry with the WALLS or GRADIENT source.
-cudaError_t batch_attr_f32(int src, int threads, size_t smem, int* per_sm)
+cudaError_t batch_attr_f32(int src, bool diff, int threads, size_t smem, int* per_sm)
 {
     auto k = src == LE_MC_SRC_WALLS ? trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>
+             : diff                 ? trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>
                                     : trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -82,11 +108,14 @@ cudaError_t batch_attr_f32(int src, int threads, size_t smem, int* per_sm)
 }
 
 // Launch only (no attribute calls), so it can be captured into a graph.
-cudaError_t batch_launch_f32(const KernelArgs& a, int src, int blocks, int threads, size_t smem, cudaStream_t st)
+cudaError_t batch_launch_f32(const KernelArgs& a, int src, bool diff, int blocks, int threads, size_t smem,
+                              cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
     if (src == LE_MC_SRC_WALLS)
         trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true><<<blocks, threads, smem, st>>>(a);
+    else if (diff)
+        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true><<<blocks, threads, smem, st>>>(a);
     else
         trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
