@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests.tolerances import sum_order_rtol
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +65,7 @@ def test_results_same_alone_and_in_mix(P):
             assert a[k] == m[k], k
         assert a["epochs"] == m["epochs"]
         key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
-        assert m[key] == pytest.approx(a[key], rel=1e-9)
+        assert m[key] == pytest.approx(a[key], rel=sum_order_rtol(a, prob["run"]["precision"], key))
         assert m["rel_err"] <= target or m["particles"] == prob["run"]["n_particles"]
 
 
