@@ -183,6 +183,31 @@ def fuchs_sondheimer_quadrature(delta):
     return 1.5 * val
 
 
+def fuchs_sondheimer_specular(delta, p):
+    """S(delta, p) for walls that reflect specularly with probability p and
+    diffusely otherwise, from the first-flight picture: a particle emitted
+    uniformly across the film keeps its in-plane velocity through specular
+    reflections and loses it (in expectation) at its first diffuse event, so
+    with mu = |Omega_x| its mean path to that event is Lambda g_p(mu),
+    g_p(mu) = 1 - (1 - p)(mu/delta)(1 - e^{-delta/mu}) / (1 - p e^{-delta/mu}),
+    and S = 3/2 int_0^1 (1 - mu^2) g_p(mu) dmu."""
+    def g(mu):
+        if mu <= 0.0:
+            return 1.0
+        e = math.exp(-delta / mu)
+        return 1.0 - (1.0 - p) * (mu / delta) * (-math.expm1(-delta / mu)) / (1.0 - p * e)
+    val, _ = integrate.quad(lambda mu: (1 - mu * mu) * g(mu), 0.0, 1.0, limit=400, epsabs=1e-14)
+    return 1.5 * val
+
+
+def fuchs_sondheimer_specular_t(delta, p):
+    """The same S(delta, p) in the form usually quoted for films:
+    1 - 3(1 - p)/(2 delta) int_1^inf (t^-3 - t^-5)(1 - e^{-delta t})/(1 - p e^{-delta t}) dt."""
+    f = lambda t: (t ** -3 - t ** -5) * (-math.expm1(-delta * t)) / (1.0 - p * math.exp(-delta * t))
+    val, _ = integrate.quad(f, 1.0, np.inf, limit=400, epsabs=1e-14)
+    return 1.0 - 1.5 * (1.0 - p) / delta * val
+
+
 def mode_table(mat):
     """(omega, v, tau, C) per mode from a workload material dict (numpy)."""
     T = mat["T_eq"]
@@ -215,10 +240,16 @@ def kappa_bulk(mat):
     return float(np.sum(C * v * v * tau) / 3.0)
 
 
-def kappa_film(mat, L):
+def kappa_film(mat, L, specularity=0.0):
+    """In-plane film conductivity; walls diffuse, or specular with
+    probability ``specularity`` (the same on both walls)."""
     _, v, tau, C = mode_table(mat)
     lam = v * tau
-    return float(np.sum(C * v * v * tau / 3.0 * fuchs_sondheimer(L / lam)))
+    if specularity == 0.0:
+        S = fuchs_sondheimer(L / lam)
+    else:
+        S = np.array([fuchs_sondheimer_specular(d, specularity) for d in L / lam])
+    return float(np.sum(C * v * v * tau / 3.0 * S))
 
 
 # --------------------------------------------------------------------------

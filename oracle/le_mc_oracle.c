@@ -38,10 +38,10 @@
 /* ------------------------------------------------------------------------ */
 enum { ORC_MAT_GRAY = 0, ORC_MAT_QUADRATIC = 1 };
 enum { ORC_GEOM_PLANES = 0, ORC_GEOM_BULK = 1, ORC_GEOM_POROUS = 2 };
-enum { ORC_WALL_BLACK = 0, ORC_WALL_DIFFUSE = 1, ORC_WALL_SPECULAR = 2 };
+enum { ORC_WALL_BLACK = 0, ORC_WALL_DIFFUSE = 1, ORC_WALL_SPECULAR = 2, ORC_WALL_PARTIAL = 3 };
 enum { ORC_SRC_WALLS = 0, ORC_SRC_GRADIENT = 1, ORC_SRC_PULSE = 2, ORC_SRC_INITIAL = 3 };
 enum { ORC_FATE_ABSORBED = 0, ORC_FATE_MAX_SCATTER = 1, ORC_FATE_MAX_EVENTS = 2,
-       ORC_FATE_T_FINAL = 3 };
+       ORC_FATE_T_FINAL = 3, ORC_FATE_MAX_COLLISIONS = 4 };
 
 typedef struct {
     /* material */
@@ -59,6 +59,9 @@ typedef struct {
     double L;             /* film / slab thickness along x [m]         */
     double pitch, radius; /* porous: square lattice in (y,z)           */
     int32_t cells_y, cells_z;
+    /* PARTIAL walls: probability of a specular reflection at x = 0, x = L and
+     * on the pores (the remainder is diffuse) */
+    double spec_lo, spec_hi, spec_pore;
     /* source */
     int32_t src_kind;
     int32_t pad1;
@@ -74,6 +77,8 @@ typedef struct {
     uint32_t instance_id;
     uint32_t max_scatter; /* terminate at this scattering event; 0 = no cap */
     uint32_t max_events;  /* terminate after this many segments (>= 1)    */
+    uint32_t max_collisions; /* terminate at this many scatterings + wall
+                                hits (periodic faces excluded); 0 = no cap */
     int32_t n_bins_x;     /* slab profile bins along x (0 = off)          */
     int32_t n_batch;      /* batch groups for the profile error bars      */
     int32_t grid_nx, grid_ny, grid_nz, n_samples;
@@ -602,9 +607,14 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
         int absorbed = 0;
         if (hit) {
             int wall_type = -1;
-            if (kind == HIT_XLO) wall_type = p->wall_lo;
-            else if (kind == HIT_XHI) wall_type = p->wall_hi;
-            else if (kind == HIT_CYL) wall_type = p->pore_wall;
+            double spec = 0.0;
+            if (kind == HIT_XLO) { wall_type = p->wall_lo; spec = p->spec_lo; }
+            else if (kind == HIT_XHI) { wall_type = p->wall_hi; spec = p->spec_hi; }
+            else if (kind == HIT_CYL) { wall_type = p->pore_wall; spec = p->spec_pore; }
+            /* partially specular wall: specular with probability spec, else
+             * diffuse; the draw is the flight's second uniform, which only a
+             * relaxation event uses otherwise */
+            if (wall_type == ORC_WALL_PARTIAL) wall_type = u[1] < spec ? ORC_WALL_SPECULAR : ORC_WALL_DIFFUSE;
             if (wall_type >= 0) {
                 ++n_wall;
                 if (wall_type == ORC_WALL_BLACK) {
@@ -655,6 +665,9 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
         if (absorbed) { fate = ORC_FATE_ABSORBED; break; }
         if (transient && s.t > p->t_final) { fate = ORC_FATE_T_FINAL; break; }
         if (p->max_scatter > 0 && n_scat >= p->max_scatter) { fate = ORC_FATE_MAX_SCATTER; break; }
+        /* first-free-path style truncation: a collision is a relaxation or a
+         * wall / pore hit, not a crossing of a periodic unit-cell face */
+        if (p->max_collisions > 0 && n_scat + n_wall >= p->max_collisions) { fate = ORC_FATE_MAX_COLLISIONS; break; }
         if (n_seg >= p->max_events) { fate = ORC_FATE_MAX_EVENTS; break; }
     }
     if (p->n_hj > 0 && n_scat < (uint32_t)p->n_hj && h_run != 0.0) {
@@ -670,7 +683,7 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
     tl->wall_hits += n_wall;
     tl->periodic += n_per;
     if (fate == ORC_FATE_ABSORBED) tl->absorbed += 1;
-    if (fate == ORC_FATE_MAX_SCATTER || fate == ORC_FATE_MAX_EVENTS) tl->truncated += 1;
+    if (fate == ORC_FATE_MAX_SCATTER || fate == ORC_FATE_MAX_EVENTS || fate == ORC_FATE_MAX_COLLISIONS) tl->truncated += 1;
     if (rec) {
         rec->sign = (int8_t)s.sign;
         rec->fate = (int8_t)fate;
@@ -725,6 +738,11 @@ static int validate(const orc_problem* p)
                              p->grid_nx < 1 || p->grid_ny < 1 || p->grid_nz < 1))
         return -1;
     if (p->n_particles > 0xFFFFFFFFull) return -1;
+    if (p->wall_lo < 0 || p->wall_lo > 3 || p->wall_hi < 0 || p->wall_hi > 3) return -1;
+    if (p->pore_wall < 1 || p->pore_wall > 3) return -1;
+    if (!(p->spec_lo >= 0.0 && p->spec_lo <= 1.0) || !(p->spec_hi >= 0.0 && p->spec_hi <= 1.0) ||
+        !(p->spec_pore >= 0.0 && p->spec_pore <= 1.0))
+        return -1;
     return 0;
 }
 

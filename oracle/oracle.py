@@ -38,9 +38,9 @@ _LIB = os.path.join(_HERE, "liblemc_oracle.so")
 
 MAT = {"gray": 0, "quadratic": 1}
 GEOM = {"planes": 0, "bulk": 1, "porous": 2}
-WALL = {"black": 0, "diffuse": 1, "specular": 2}
+WALL = {"black": 0, "diffuse": 1, "specular": 2, "partial": 3}
 SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
-FATE = {0: "absorbed", 1: "max_scatter", 2: "max_events", 3: "t_final"}
+FATE = {0: "absorbed", 1: "max_scatter", 2: "max_events", 3: "t_final", 4: "max_collisions"}
 
 
 class Problem(C.Structure):
@@ -52,6 +52,7 @@ class Problem(C.Structure):
         ("geom_kind", C.c_int32), ("wall_lo", C.c_int32), ("wall_hi", C.c_int32), ("pore_wall", C.c_int32),
         ("L", C.c_double), ("pitch", C.c_double), ("radius", C.c_double),
         ("cells_y", C.c_int32), ("cells_z", C.c_int32),
+        ("spec_lo", C.c_double), ("spec_hi", C.c_double), ("spec_pore", C.c_double),
         ("src_kind", C.c_int32), ("pad1", C.c_int32),
         ("dT_lo", C.c_double), ("dT_hi", C.c_double), ("dTdz", C.c_double),
         ("pulse_sigma_x", C.c_double), ("pulse_sigma_t", C.c_double), ("pulse_t_center", C.c_double),
@@ -59,6 +60,7 @@ class Problem(C.Structure):
         ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double),
         ("n_particles", C.c_uint64), ("seed", C.c_uint64),
         ("instance_id", C.c_uint32), ("max_scatter", C.c_uint32), ("max_events", C.c_uint32),
+        ("max_collisions", C.c_uint32),
         ("n_bins_x", C.c_int32), ("n_batch", C.c_int32),
         ("grid_nx", C.c_int32), ("grid_ny", C.c_int32), ("grid_nz", C.c_int32), ("n_samples", C.c_int32),
         ("n_hj", C.c_int32),
@@ -175,6 +177,7 @@ def to_problem(prob, n_threads=None, record_particles=False):
     p.pore_wall = WALL[g.get("pore_wall", "diffuse")]
     p.pitch, p.radius = g.get("pitch", 0.0), g.get("radius", 0.0)
     p.cells_y, p.cells_z = g.get("cells_y", 1), g.get("cells_z", 1)
+    p.spec_lo, p.spec_hi, p.spec_pore = g.get("spec_lo", 0.0), g.get("spec_hi", 0.0), g.get("spec_pore", 0.0)
     p.src_kind = SRC[s["kind"]]
     p.dT_lo, p.dT_hi, p.dTdz = s.get("dT_lo", 0.0), s.get("dT_hi", 0.0), s.get("dTdz", 0.0)
     p.pulse_sigma_x, p.pulse_sigma_t = s.get("sigma_x", 0.0), s.get("sigma_t", 0.0)
@@ -184,6 +187,7 @@ def to_problem(prob, n_threads=None, record_particles=False):
     p.init_x_lo, p.init_x_hi = s.get("x_lo", 0.0), s.get("x_hi", 0.0)
     p.n_particles, p.seed, p.instance_id = r["n_particles"], r["seed"], r.get("instance_id", 0)
     p.max_scatter, p.max_events = r.get("max_scatter", 0), r.get("max_events", 1 << 20)
+    p.max_collisions = r.get("max_collisions", 0)
     p.n_bins_x, p.n_batch = r.get("n_bins_x", 0), r.get("n_batch", 32)
     gx, gy, gz = r.get("grid", (0, 0, 0))
     p.grid_nx, p.grid_ny, p.grid_nz = gx, gy, gz

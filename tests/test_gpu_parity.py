@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import workloads as W
+from tests.tolerances import lane_sum_error, sum_atol, sum_order_rtol
 
 pytestmark = pytest.mark.gpu
 
@@ -220,7 +221,7 @@ def test_launch_shape_does_not_change_results(P):
         assert np.array_equal(o["particles_rec"], outs[0]["particles_rec"])
         for k in ("segments", "scatters", "wall_hits", "truncated"):
             assert o[k] == outs[0][k]
-        assert o["kappa"] == pytest.approx(outs[0]["kappa"], rel=1e-9)
+        assert o["kappa"] == pytest.approx(outs[0]["kappa"], rel=sum_order_rtol(outs[0], "fp32"))
 
 
 def test_empty_run(P):
@@ -258,8 +259,9 @@ def test_pieces_add_up(P):
     b = P.simulate(W.with_run(prob, n_particles=70_001, first_particle=50_000), arrays=False)
     for k in ("particles", "segments", "scatters", "wall_hits", "truncated"):
         assert a[k] + b[k] == whole[k]
-    assert a["sum_sL"] + b["sum_sL"] == pytest.approx(whole["sum_sL"], rel=1e-9, abs=1e-20)
-    assert a["sum_sL2"] + b["sum_sL2"] == pytest.approx(whole["sum_sL2"], rel=1e-9)
+    n = whole["particles"]
+    assert abs(a["sum_sL"] + b["sum_sL"] - whole["sum_sL"]) <= sum_atol(whole["sum_sL2"], n, "fp32", runs=3)
+    assert abs(a["sum_sL2"] + b["sum_sL2"] - whole["sum_sL2"]) <= 3 * lane_sum_error("fp32", n) * whole["sum_sL2"]
 
 
 def test_gray_initial_condition_grid_bit_exact(P, oracle):

@@ -44,6 +44,20 @@ def _uniform_pin_ok(oracle, analytic, library):
     return min(uniform_equilibrium_pvalues(r["grid"], p["geometry"])) > 1e-4
 
 
+def _specular_pin_ok(oracle, analytic, library):
+    r = oracle.run(W.silicon_film(n_particles=1_000_000, precision="fp64", specularity=0.25), library=library)
+    return abs(r["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 100e-9, 0.25)) < 4.0 * r["kappa_se"]
+
+
+def _first_path_pin_ok(oracle, analytic, library):
+    r = oracle.run(W.with_run(W.silicon_film(n_particles=400_000, precision="fp64"), max_collisions=1),
+                   library=library)
+    # (the film is symmetric enough that stopping at the first relaxation is
+    # also exact, so the one-segment-per-particle count is what tells them apart)
+    return (abs(r["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 100e-9)) < 4.0 * r["kappa_se"]
+            and r["segments"] == r["particles"])
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -65,6 +79,12 @@ MUTATIONS = [
     ("gradient-source sign flipped", "(p->dTdz > 0.0 ? -1.0 : 1.0)", "(p->dTdz > 0.0 ? 1.0 : -1.0)", _film_pin_ok),
     ("flight drawn with the wrong mean free path", "double dist = m->Lambda[s.mode] * -log(u[0]);",
      "double dist = m->tau[s.mode] * -log(u[0]);", _film_pin_ok),
+    ("partial wall specular with probability 1 - p", "wall_type = u[1] < spec ? ORC_WALL_SPECULAR",
+     "wall_type = u[1] >= spec ? ORC_WALL_SPECULAR", _specular_pin_ok),
+    ("specular reflection also flips the in-plane direction", "if (wall_type == ORC_WALL_SPECULAR) s.ox = -s.ox;",
+     "if (wall_type == ORC_WALL_SPECULAR) { s.ox = -s.ox; s.oz = -s.oz; }", _specular_pin_ok),
+    ("first-free-path cap counts only relaxations", "n_scat + n_wall >= p->max_collisions",
+     "n_scat >= p->max_collisions", _first_path_pin_ok),
     ("density of states missing a factor k", "double dos = k * k / (2.0 * ORC_PI * ORC_PI * vg);",
      "double dos = k / (2.0 * ORC_PI * ORC_PI * vg);", _film_pin_ok),
 ]

@@ -9,6 +9,7 @@
   contribution after the first event (first-event truncation is exact for
   the film, scattering-index tallies H_j, j >= 1, average to zero).
 """
+import math
 import numpy as np
 import pytest
 
@@ -87,6 +88,53 @@ def test_silicon_film_fuchs_sondheimer(oracle, analytic):
     pin = analytic.kappa_film(mat, 100e-9)
     r = oracle.run(W.silicon_film(n_particles=1_000_000, thickness=100e-9, precision="fp64"))
     assert _z(r["kappa"], pin, r["kappa_se"]) < 4.0, (r["kappa"], pin)
+
+
+def test_specular_film_factor_forms(analytic):
+    # the first-flight derivation and the usual t-integral agree, reduce to the
+    # diffuse closed form at p = 0 and to the bulk (S = 1) at p = 1
+    for d in (0.02, 0.3, 1.0, 4.0):
+        assert analytic.fuchs_sondheimer_specular(d, 0.0) == pytest.approx(float(analytic.fuchs_sondheimer(d)),
+                                                                           rel=1e-10)
+        assert analytic.fuchs_sondheimer_specular(d, 1.0) == pytest.approx(1.0, rel=1e-12)
+        for p in (0.25, 0.6):
+            assert analytic.fuchs_sondheimer_specular(d, p) == pytest.approx(
+                analytic.fuchs_sondheimer_specular_t(d, p), rel=1e-9)
+
+
+def test_partially_specular_film(oracle, analytic):
+    # Walls specular with probability p (the rest diffuse): Fuchs-Sondheimer
+    # with specularity p.  Truncation stays unbiased: a relaxation or a diffuse
+    # hit leaves a zero mean in-plane velocity, and 4096 segments without a
+    # diffuse hit have probability p^4096.
+    mat = W.SILICON_LIKE
+    pin = analytic.kappa_film(mat, 100e-9, 0.25)
+    r = oracle.run(W.silicon_film(n_particles=4_000_000, precision="fp64", specularity=0.25))
+    assert _z(r["kappa"], pin, r["kappa_se"]) < 4.0, (r["kappa"], pin)
+    # the pin tells this specularity from its complement and from diffuse walls
+    assert abs(analytic.kappa_film(mat, 100e-9, 0.75) - pin) > 10 * r["kappa_se"]
+    assert abs(analytic.kappa_film(mat, 100e-9) - pin) > 10 * r["kappa_se"]
+    # fully specular walls never end an in-plane flight: the bulk value
+    gray = dict(W.GRAY_UNIT)
+    r = oracle.run(W.silicon_film(n_particles=1_000_000, thickness=1.0, material=gray, precision="fp64",
+                                  specularity=1.0, dTdz=-1.0, max_scatter=1, max_events=1 << 20))
+    assert _z(r["kappa"], 1.0 / 3.0, r["kappa_se"]) < 4.0
+
+
+def test_first_collision_truncation(oracle, analytic):
+    # Stopping at the first relaxation or wall hit (the first free path) is
+    # exact for the diffuse film; every particle then has exactly one segment.
+    pin = analytic.kappa_film(W.SILICON_LIKE, 100e-9)
+    r = oracle.run(W.with_run(W.silicon_film(n_particles=2_000_000, precision="fp64"), max_collisions=1))
+    assert _z(r["kappa"], pin, r["kappa_se"]) < 4.0, (r["kappa"], pin)
+    assert r["segments"] == r["particles"] == r["truncated"]
+    # In the pored film a pore wall re-emits a particle back against the flux
+    # on average, so following only the first free path (crossings of the
+    # periodic unit-cell faces do not end it) overestimates the conductivity.
+    full = oracle.run(W.porous_film(n_particles=400_000, precision="fp64"))
+    first = oracle.run(W.with_run(W.porous_film(n_particles=400_000, precision="fp64"), max_collisions=1))
+    assert first["periodic"] > 0 and first["scatters"] + first["wall_hits"] == first["particles"]
+    assert first["kappa"] - full["kappa"] > 5.0 * math.hypot(first["kappa_se"], full["kappa_se"])
 
 
 def test_bulk_conductivity(oracle, analytic):

@@ -84,12 +84,17 @@ def gray_slab(n_particles=100_000, kn=1.0, n_bins=50, seed=0x5EED_0000_0001,
 
 def silicon_film(n_particles=10_000_000, thickness=100e-9, seed=0x5EED_0000_0002,
                  precision="fp32", max_scatter=40, max_events=4096, dTdz=-1.0e6,
-                 material=None, walls=("diffuse", "diffuse"), n_hj=0):
+                 material=None, walls=("diffuse", "diffuse"), n_hj=0, specularity=None):
     """Thin film with diffuse walls at x = 0 and x = thickness, driven by a
-    uniform temperature gradient along z (in plane): in-plane conductivity."""
+    uniform temperature gradient along z (in plane): in-plane conductivity.
+    ``specularity`` = p makes both walls partially specular (specular with
+    probability p, diffuse otherwise)."""
+    geo = {"kind": "planes", "L": float(thickness), "wall_lo": walls[0], "wall_hi": walls[1]}
+    if specularity is not None:
+        geo.update(wall_lo="partial", wall_hi="partial", spec_lo=float(specularity), spec_hi=float(specularity))
     return {
         "material": copy.deepcopy(material or SILICON_LIKE),
-        "geometry": {"kind": "planes", "L": float(thickness), "wall_lo": walls[0], "wall_hi": walls[1]},
+        "geometry": geo,
         "source": {"kind": "gradient", "dTdz": float(dTdz)},
         "run": _run(n_particles=n_particles, seed=seed, max_scatter=max_scatter,
                     max_events=max_events, precision=precision, n_hj=n_hj),
