@@ -42,7 +42,7 @@ extern "C" {
 #define LE_MC_API
 #endif
 
-#define LE_MC_ABI_VERSION 1
+#define LE_MC_ABI_VERSION 2
 #define LE_MC_MAX_BRANCHES 4
 #define LE_MC_MAX_MODES 4096        /* mode tables live in shared memory       */
 #define LE_MC_MAX_BINS_X 256        /* slab profile bins                       */
@@ -83,6 +83,12 @@ typedef struct {
     const double* tab_v;
     const double* tab_tau;
     const double* tab_C;
+    /* Direction change at a relaxation event (step IVb): 0 keeps the paper's
+     * isotropic redraw; a nonzero g in (-1, 1) draws the new direction from
+     * the Henyey-Greenstein law of mean cosine g about the incoming one (the
+     * generalisation the paper allows; the mode is still redrawn from the
+     * normalised Eq. 2, independently of the direction).                     */
+    double scatter_g;
 } le_mc_material_desc;
 
 typedef struct le_mc_material_s* le_mc_material;
@@ -111,7 +117,12 @@ LE_MC_API le_mc_status le_mc_alias_table(const double* weights, int32_t n, uint3
 
 /* ---- geometry (step III boundary search, step IVa wall response) --------- */
 enum { LE_MC_GEOM_PLANES = 0, LE_MC_GEOM_BULK = 1, LE_MC_GEOM_POROUS = 2 };
-enum { LE_MC_WALL_BLACK = 0, LE_MC_WALL_DIFFUSE = 1, LE_MC_WALL_SPECULAR = 2 };
+/* Wall laws (step IVa): BLACK absorbs (isothermal wall, the particle ends);
+ * DIFFUSE re-emits with a cosine law about the inward normal, mode kept;
+ * SPECULAR mirrors the direction; PARTIAL is specular with probability
+ * spec_* and diffuse otherwise (the choice uses the flight's second uniform,
+ * which only a relaxation event uses otherwise). */
+enum { LE_MC_WALL_BLACK = 0, LE_MC_WALL_DIFFUSE = 1, LE_MC_WALL_SPECULAR = 2, LE_MC_WALL_PARTIAL = 3 };
 
 typedef struct {
     int32_t kind;      /* PLANES: walls at x = 0 and x = L, unbounded in y, z (slab, film)
@@ -123,11 +134,14 @@ typedef struct {
                         *         re-inserted on the opposite face)               */
     int32_t wall_lo;   /* wall type at x = 0 (LE_MC_WALL_*)                     */
     int32_t wall_hi;   /* wall type at x = L                                   */
-    int32_t pore_wall; /* POROUS: pore surface type (DIFFUSE or SPECULAR)       */
+    int32_t pore_wall; /* POROUS: pore surface type (DIFFUSE, SPECULAR, PARTIAL) */
     double L;          /* thickness along x [m] (> 0 unless BULK)               */
     double pitch;      /* POROUS: lattice pitch [m]                            */
     double radius;     /* POROUS: pore radius [m], 0 <= 2 radius < pitch         */
     int32_t cells_y, cells_z; /* POROUS: periodic domain in unit cells (>= 1)   */
+    double spec_lo, spec_hi;  /* PARTIAL walls at x = 0, x = L: probability of a
+                               * specular reflection, in [0, 1]               */
+    double spec_pore;         /* PARTIAL pore surface: the same               */
 } le_mc_geometry_desc;
 
 typedef struct le_mc_geometry_s* le_mc_geometry;
@@ -178,7 +192,8 @@ typedef struct {
     int32_t n_hj;                   /* flux split by scattering index j (0 = off) */
     int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
     int32_t blocks_per_sm;          /* launch shape (0 = library default)        */
-    int32_t threads_per_block;      /* 0 = default (512); multiple of 32, <= 512 */
+    int32_t threads_per_block;      /* 0 = default: 512, or 256 when that keeps more
+                                     * warps resident; else a multiple of 32, <= 512 */
     int32_t schedule;               /* particle order: 0 auto, 1 long-first,
                                      * 2 natural id order.  Long-first serves
                                      * particles emitted in modes with a mean
@@ -197,6 +212,11 @@ typedef struct {
                                      * so a problem can be traced in pieces      */
     double init_dT;                 /* INITIAL: T_i - T_eq [K], nonzero          */
     double init_x_lo, init_x_hi;    /* INITIAL: heated layer, 0 <= lo < hi <= L  */
+    uint32_t max_collisions;        /* terminate at this many relaxations + wall
+                                     * hits, crossings of periodic unit-cell
+                                     * faces not counted (0 = none); 1 follows
+                                     * each particle over its first free path
+                                     * only (the first-free-path estimate)     */
 } le_mc_run_desc;
 
 typedef struct le_mc_run_s* le_mc_run_handle;

@@ -240,6 +240,23 @@ def kappa_bulk(mat):
     return float(np.sum(C * v * v * tau) / 3.0)
 
 
+def kappa_bulk_anisotropic(mat, g):
+    """Bulk conductivity when a relaxation event turns the direction with
+    mean cosine g about the incoming one (the mode is still redrawn from the
+    normalised Eq. 2, independently of the direction).  A particle emitted by
+    the gradient source in mode b with |cos| law about z contributes its first
+    flight Lambda_b mu, and after its j-th relaxation a flight of mean length
+    <Lambda>_s = sum_b (C_b/tau_b) Lambda_b / sum_b C_b/tau_b along a direction
+    whose mean z-cosine is g^j mu, so
+    kappa = 1/3 sum_b C_b v_b Lambda_b + 1/3 (sum_b C_b v_b) g <Lambda>_s / (1 - g),
+    which is (1/3) C v Lambda / (1 - g) for a gray medium and the usual bulk
+    value at g = 0."""
+    _, v, tau, C = mode_table(mat)
+    lam = v * tau
+    lam_s = float(np.sum(C / tau * lam) / np.sum(C / tau))
+    return float(np.sum(C * v * lam) / 3.0 + np.sum(C * v) / 3.0 * g * lam_s / (1.0 - g))
+
+
 def kappa_film(mat, L, specularity=0.0):
     """In-plane film conductivity; walls diffuse, or specular with
     probability ``specularity`` (the same on both walls)."""

@@ -53,6 +53,9 @@ typedef struct {
     double gray_v, gray_tau, gray_C;
     double c1[4], c2[4], degeneracy[4];
     double a_lattice, A, B, Cexp;
+    double scatter_g;     /* mean cosine of the direction change at a relaxation
+                             event: 0 isotropic (the paper's law), else the
+                             Henyey-Greenstein law about the incoming direction */
     /* geometry */
     int32_t geom_kind;
     int32_t wall_lo, wall_hi, pore_wall;
@@ -281,6 +284,33 @@ static void dir_axis(int axis, double mu, double u_phi, double* ox, double* oy, 
     double c = cos(phi), sn = sin(phi);
     if (axis == 0) { *ox = mu; *oy = s * c; *oz = s * sn; }
     else { *ox = s * c; *oy = s * sn; *oz = mu; }
+}
+
+/* Anisotropic generalisation of the relaxation event's direction (the paper
+ * uses an isotropic redraw and notes that other laws fit the same scheme):
+ * the Henyey-Greenstein law with mean cosine g != 0 about the incoming
+ * direction n.  The cosine mu = Omega'.n inverts the law's CDF
+ * F(mu) = (1 - g^2)/(2g) [(1 + g^2 - 2 g mu)^(-1/2) - (1 + g)^(-1)] at u_mu;
+ * the azimuth is 2 pi u_phi in the frame (b1, b2, n) of Duff et al.,
+ * "Building an Orthonormal Basis, Revisited", JCGT 6(1), 2017. */
+static void hg_direction(double g, double u_mu, double u_phi, double nx, double ny, double nz, double* ox,
+                         double* oy, double* oz)
+{
+    double q = (1.0 - g * g) / (1.0 - g + 2.0 * g * u_mu);
+    double mu = (1.0 + g * g - q * q) / (2.0 * g);
+    if (mu > 1.0) mu = 1.0;
+    if (mu < -1.0) mu = -1.0;
+    double s = sqrt(fmax(0.0, 1.0 - mu * mu));
+    double phi = ORC_TWO_PI * u_phi;
+    double c = cos(phi), sn = sin(phi);
+    double sg = nz >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + nz);
+    double b = nx * ny * a;
+    double b1x = 1.0 + sg * nx * nx * a, b1y = sg * b, b1z = -sg * nx;
+    double b2x = b, b2y = sg + ny * ny * a, b2z = -ny;
+    *ox = mu * nx + s * (c * b1x + sn * b2x);
+    *oy = mu * ny + s * (c * b1y + sn * b2y);
+    *oz = mu * nz + s * (c * b1z + sn * b2z);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -658,8 +688,10 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
                 tl->h_sum2[n_scat - 1] += h_run * h_run;
             }
             h_run = 0.0;
+            double in_x = s.ox, in_y = s.oy, in_z = s.oz;
             s.mode = draw_mode(m->cdf_scat, m->n, u[1]);
             dir_axis(2, 2.0 * u[2] - 1.0, u[3], &s.ox, &s.oy, &s.oz);
+            if (p->scatter_g != 0.0) hg_direction(p->scatter_g, u[2], u[3], in_x, in_y, in_z, &s.ox, &s.oy, &s.oz);
         }
         /* step VI and the truncation rules */
         if (absorbed) { fate = ORC_FATE_ABSORBED; break; }
@@ -740,6 +772,7 @@ static int validate(const orc_problem* p)
     if (p->n_particles > 0xFFFFFFFFull) return -1;
     if (p->wall_lo < 0 || p->wall_lo > 3 || p->wall_hi < 0 || p->wall_hi > 3) return -1;
     if (p->pore_wall < 1 || p->pore_wall > 3) return -1;
+    if (!(p->scatter_g > -1.0 && p->scatter_g < 1.0)) return -1;
     if (!(p->spec_lo >= 0.0 && p->spec_lo <= 1.0) || !(p->spec_hi >= 0.0 && p->spec_hi <= 1.0) ||
         !(p->spec_pore >= 0.0 && p->spec_pore <= 1.0))
         return -1;
@@ -965,6 +998,14 @@ int orc_emit(const orc_problem* p, uint64_t first, int n, double* out, int32_t* 
     }
     mat_free(&m);
     return 0;
+}
+
+/* The relaxation-event direction law for sampler tests: in = incoming
+ * direction (unit), u_mu and u_phi the flight's third and fourth uniforms. */
+void orc_scatter_direction(double g, const double in[3], double u_mu, double u_phi, double out[3])
+{
+    dir_axis(2, 2.0 * u_mu - 1.0, u_phi, &out[0], &out[1], &out[2]);
+    if (g != 0.0) hg_direction(g, u_mu, u_phi, in[0], in[1], in[2], &out[0], &out[1], &out[2]);
 }
 
 int orc_sizeof_problem(void) { return (int)sizeof(orc_problem); }

@@ -49,6 +49,7 @@ class Problem(C.Structure):
         ("T_eq", C.c_double), ("gray_v", C.c_double), ("gray_tau", C.c_double), ("gray_C", C.c_double),
         ("c1", C.c_double * 4), ("c2", C.c_double * 4), ("degeneracy", C.c_double * 4),
         ("a_lattice", C.c_double), ("A", C.c_double), ("B", C.c_double), ("Cexp", C.c_double),
+        ("scatter_g", C.c_double),
         ("geom_kind", C.c_int32), ("wall_lo", C.c_int32), ("wall_hi", C.c_int32), ("pore_wall", C.c_int32),
         ("L", C.c_double), ("pitch", C.c_double), ("radius", C.c_double),
         ("cells_y", C.c_int32), ("cells_z", C.c_int32),
@@ -147,6 +148,8 @@ def lib():
         _lib.orc_draw_modes.argtypes = [C.POINTER(Problem), C.c_int, C.c_void_p, C.c_int, C.c_void_p]
         _lib.orc_first_boundary.restype = C.c_double
         _lib.orc_first_boundary.argtypes = [C.POINTER(Problem), C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
+        _lib.orc_scatter_direction.restype = None
+        _lib.orc_scatter_direction.argtypes = [C.c_double, C.c_void_p, C.c_double, C.c_double, C.c_void_p]
         _lib.orc_emit.restype = C.c_int
         _lib.orc_emit.argtypes = [C.POINTER(Problem), C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]
         assert _lib.orc_sizeof_problem() == C.sizeof(Problem)
@@ -170,6 +173,7 @@ def to_problem(prob, n_threads=None, record_particles=False):
             p.c1[i], p.c2[i], p.degeneracy[i] = b["c1"], b["c2"], b["degeneracy"]
         p.n_bins_omega = m["n_bins"]
         p.a_lattice, p.A, p.B, p.Cexp = m["a_lattice"], m["A"], m["B"], m["C"]
+    p.scatter_g = m.get("scatter_g", 0.0)
     p.geom_kind = GEOM[g["kind"]]
     p.L = g.get("L", 0.0)
     p.wall_lo = WALL[g.get("wall_lo", "diffuse")]
@@ -262,6 +266,16 @@ def draw_modes(prob, which, u):
                               out.ctypes.data)
     if rc:
         raise ValueError("bad material")
+    return out
+
+
+def scatter_direction(g, incoming, u_mu, u_phi):
+    """Direction after a relaxation event (isotropic for g = 0, else the
+    Henyey-Greenstein law of mean cosine g about ``incoming``)."""
+    lib()
+    inc = np.ascontiguousarray(incoming, dtype=np.float64)
+    out = np.zeros(3)
+    _lib.orc_scatter_direction(float(g), inc.ctypes.data, float(u_mu), float(u_phi), out.ctypes.data)
     return out
 
 

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "OK", 1: "INVALID", 2: "NOMEM", 3: "CUDA", 4: "TIMEOUT", 5: "
 
 MAT = {"gray": 0, "quadratic": 1, "tabulated": 2}
 GEOM = {"planes": 0, "bulk": 1, "porous": 2}
-WALL = {"black": 0, "diffuse": 1, "specular": 2}
+WALL = {"black": 0, "diffuse": 1, "specular": 2, "partial": 3}
 SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
 PREC = {"fp64": 0, "fp32": 1}
 ARRAY = {"T": 0, "T_se": 1, "q": 2, "q_se": 3, "H": 4, "H_se": 5, "grid": 6, "particles": 7}
@@ -42,13 +42,14 @@ class MaterialDesc(C.Structure):
                 ("degeneracy", C.c_double * MAX_BRANCHES),
                 ("a_lattice", C.c_double), ("A", C.c_double), ("B", C.c_double), ("C_exp", C.c_double),
                 ("tab_v", C.POINTER(C.c_double)), ("tab_tau", C.POINTER(C.c_double)),
-                ("tab_C", C.POINTER(C.c_double))]
+                ("tab_C", C.POINTER(C.c_double)), ("scatter_g", C.c_double)]
 
 
 class GeometryDesc(C.Structure):
     _fields_ = [("kind", C.c_int32), ("wall_lo", C.c_int32), ("wall_hi", C.c_int32), ("pore_wall", C.c_int32),
                 ("L", C.c_double), ("pitch", C.c_double), ("radius", C.c_double),
-                ("cells_y", C.c_int32), ("cells_z", C.c_int32)]
+                ("cells_y", C.c_int32), ("cells_z", C.c_int32),
+                ("spec_lo", C.c_double), ("spec_hi", C.c_double), ("spec_pore", C.c_double)]
 
 
 class RunDesc(C.Structure):
@@ -65,7 +66,8 @@ class RunDesc(C.Structure):
                 ("blocks_per_sm", C.c_int32), ("threads_per_block", C.c_int32),
                 ("schedule", C.c_int32), ("refill_min", C.c_int32), ("long_mfp_cut", C.c_double),
                 ("chunk", C.c_int32), ("first_particle", C.c_uint32),
-                ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double)]
+                ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double),
+                ("max_collisions", C.c_uint32)]
 
 
 class Tallies(C.Structure):
@@ -186,6 +188,7 @@ def material_desc(mat):
     d = MaterialDesc()
     d.kind = MAT[mat["kind"]]
     d.T_eq = float(mat.get("T_eq", 300.0))
+    d.scatter_g = float(mat.get("scatter_g", 0.0))
     keep = []
     if mat["kind"] == "gray":
         d.gray_v, d.gray_tau, d.gray_C = mat["v"], mat["tau"], mat["C"]
@@ -216,6 +219,9 @@ def geometry_desc(geo):
     g.radius = float(geo.get("radius", 0.0))
     g.cells_y = int(geo.get("cells_y", 1))
     g.cells_z = int(geo.get("cells_z", 1))
+    g.spec_lo = float(geo.get("spec_lo", 0.0))
+    g.spec_hi = float(geo.get("spec_hi", 0.0))
+    g.spec_pore = float(geo.get("spec_pore", 0.0))
     return g
 
 
@@ -245,6 +251,7 @@ def run_desc(src, run, launch=None):
     r.refill_min = int(launch.get("refill_min", run.get("refill_min", 0)))
     r.chunk = int(launch.get("chunk", run.get("chunk", 0)))
     r.first_particle = int(run.get("first_particle", 0))
+    r.max_collisions = int(run.get("max_collisions", 0))
     r.init_dT = float(src.get("dT", 0.0)) if src["kind"] == "initial" else 0.0
     r.init_x_lo, r.init_x_hi = float(src.get("x_lo", 0.0)), float(src.get("x_hi", 0.0))
     return r

@@ -148,6 +148,7 @@ bool material_view(le_mc_material m, MaterialView* out)
     out->n_modes = m->n_modes;
     out->device = m->device;
     out->sums = m->sums;
+    out->scatter_g = m->desc.scatter_g;
     return true;
 }
 
@@ -388,11 +389,15 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.alias_emit = m->d_alias_emit;
     P.alias_init = m->d_alias_init;
     P.n_modes = m->n_modes;
+    P.scatter_g = m->desc.scatter_g;
     const le_mc_geometry_desc& G = g->desc;
     P.geom = G.kind;
     P.wall_lo = G.wall_lo;
     P.wall_hi = G.wall_hi;
     P.pore_wall = G.pore_wall;
+    P.spec_lo = G.spec_lo;
+    P.spec_hi = G.spec_hi;
+    P.spec_pore = G.spec_pore;
     P.cells_y = G.kind == LE_MC_GEOM_POROUS ? G.cells_y : 1;
     P.cells_z = G.kind == LE_MC_GEOM_POROUS ? G.cells_z : 1;
     P.L = G.kind == LE_MC_GEOM_BULK ? 1.0 : G.L;
@@ -416,6 +421,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.inst = r.instance_id;
     P.max_scatter = r.max_scatter;
     P.max_events = r.max_events;
+    P.max_collisions = r.max_collisions;
     P.n_bins_x = r.n_bins_x;
     P.n_batch = profile ? r.n_batch : 1;
     P.prof = reinterpret_cast<double*>(h->dev + h->off_prof);
@@ -447,19 +453,39 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
         P.long_cap = h->long_cap;
         P.lam_cut = r.long_mfp_cut > 0.0 ? r.long_mfp_cut : 32.0 * G.L;
     }
+    fill_consts(P);
 
-    // launch shape: persistent grid of (SMs x resident blocks)
+    // launch shape: persistent grid of (SMs x resident blocks).  By default
+    // 512 threads per block, or 256 when that keeps more warps resident (a
+    // kernel instance whose registers leave room for only one 512-thread
+    // block per SM)
+    auto shape_for = [&](int t, size_t* sm_bytes, int* resident) {
+        cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, (int)h->prof_len,
+                                                (int)h->hj_len, sm_bytes)
+                               : smem_trace_f64(G.kind, r.source, profile, m->n_modes, t, (int)h->prof_len,
+                                                (int)h->hj_len, sm_bytes);
+        if (err == cudaSuccess)
+            err = fp32 ? occupancy_trace_for_f32(P, profile, t, *sm_bytes, resident)
+                       : occupancy_trace_for_f64(P, profile, t, *sm_bytes, resident);
+        return err;
+    };
     int threads = r.threads_per_block > 0 ? r.threads_per_block : kDefaultThreads;
     if (threads > 512) threads = 512;
     size_t smem = 0;
-    e = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, threads, (int)h->prof_len, (int)h->hj_len, &smem)
-             : smem_trace_f64(G.kind, r.source, profile, m->n_modes, threads, (int)h->prof_len, (int)h->hj_len, &smem);
+    int per_sm = 0;
+    e = shape_for(threads, &smem, &per_sm);
+    if (e == cudaSuccess && r.threads_per_block <= 0) {
+        size_t smem2 = 0;
+        int per_sm2 = 0;
+        e = shape_for(256, &smem2, &per_sm2);
+        if (e == cudaSuccess && per_sm2 * 256 > per_sm * threads) {
+            threads = 256;
+            smem = smem2;
+            per_sm = per_sm2;
+        }
+    }
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int per_sm = 0;
-    if (e == cudaSuccess)
-        e = fp32 ? occupancy_trace_for_f32(P, profile, threads, smem, &per_sm)
-                 : occupancy_trace_for_f64(P, profile, threads, smem, &per_sm);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess && r.blocks_per_sm > 0 && r.blocks_per_sm < per_sm) per_sm = r.blocks_per_sm;
     int blocks = sms * per_sm;

@@ -78,7 +78,7 @@ bool fp32(const le_mc_batch b) { return b->run0.precision == LE_MC_PREC_FP32; }
 bool all_diffuse(const le_mc_batch b)
 {
     return b->run0.source == LE_MC_SRC_GRADIENT && b->geo0.wall_lo == LE_MC_WALL_DIFFUSE &&
-           b->geo0.wall_hi == LE_MC_WALL_DIFFUSE;
+           b->geo0.wall_hi == LE_MC_WALL_DIFFUSE && b->mv.scatter_g == 0.0;
 }
 
 // Kernel arguments for the whole batch.
@@ -92,10 +92,13 @@ KernelArgs make_args(le_mc_batch b)
     P.alias_scat = b->mv.alias_scat;
     P.alias_emit = b->mv.alias_emit;
     P.n_modes = b->mv.n_modes;
+    P.scatter_g = b->mv.scatter_g;
     P.geom = LE_MC_GEOM_PLANES;
     P.wall_lo = b->geo0.wall_lo;
     P.wall_hi = b->geo0.wall_hi;
     P.pore_wall = LE_MC_WALL_DIFFUSE;
+    P.spec_lo = b->geo0.spec_lo;
+    P.spec_hi = b->geo0.spec_hi;
     P.cells_y = P.cells_z = 1;
     P.L = b->geo0.L;
     P.pitch = 1.0;
@@ -110,6 +113,7 @@ KernelArgs make_args(le_mc_batch b)
     P.inst = 0;
     P.max_scatter = r.max_scatter;
     P.max_events = r.max_events;
+    P.max_collisions = r.max_collisions;
     P.n_batch = 1;
     P.sums = nullptr;
     P.counters = nullptr;
@@ -129,6 +133,7 @@ KernelArgs make_args(le_mc_batch b)
     P.first = 0;
     P.inst_sums = reinterpret_cast<double*>(b->dev + b->off_sums);
     P.inst_counters = reinterpret_cast<unsigned long long*>(b->dev + b->off_counters);
+    fill_consts(P);
     for (int i = 0; i < 10; ++i) {
         a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
         a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
@@ -170,9 +175,10 @@ cudaError_t enqueue(le_mc_batch b, cudaStream_t st, int blocks, int threads, siz
 bool same_family(const le_mc_geometry_desc& g, const le_mc_geometry_desc& g0, const le_mc_run_desc& r,
                  const le_mc_run_desc& r0)
 {
-    return g.kind == g0.kind && g.wall_lo == g0.wall_lo && g.wall_hi == g0.wall_hi && r.source == r0.source &&
-           r.precision == r0.precision && r.seed == r0.seed && r.max_scatter == r0.max_scatter &&
-           r.max_events == r0.max_events;
+    return g.kind == g0.kind && g.wall_lo == g0.wall_lo && g.wall_hi == g0.wall_hi && g.spec_lo == g0.spec_lo &&
+           g.spec_hi == g0.spec_hi && r.source == r0.source && r.precision == r0.precision && r.seed == r0.seed &&
+           r.max_scatter == r0.max_scatter && r.max_events == r0.max_events &&
+           r.max_collisions == r0.max_collisions;
 }
 
 }  // namespace
@@ -264,6 +270,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
         inst[i].lam_cut = runs[i].long_mfp_cut > 0.0 ? runs[i].long_mfp_cut : 32.0 * geoms[i].L;
         inst[i].inst_id = runs[i].instance_id;
         inst[i].n_particles = (uint32_t)runs[i].n_particles;
+        fill_instance32(inst[i]);
         offsets[i + 1] = offsets[i] + runs[i].n_particles;
     }
     b->sums.assign((size_t)n * 2, 0.0);
@@ -383,8 +390,8 @@ le_mc_status le_mc_batch_autotune(le_mc_batch b, void* stream, const char* cache
     cudaError_t e = cudaGetDeviceProperties(&prop, b->device);
     if (e != cudaSuccess) return set_cuda_error(e, "le_mc_batch_autotune");
     char key[512];
-    snprintf(key, sizeof(key), "geom=%d src=%d prec=%d modes=%d gpu=%s", b->geo0.kind, b->run0.source,
-             b->run0.precision, b->mv.n_modes, prop.name);
+    snprintf(key, sizeof(key), "geom=%d walls=%d,%d src=%d prec=%d modes=%d gpu=%s", b->geo0.kind, b->geo0.wall_lo,
+             b->geo0.wall_hi, b->run0.source, b->run0.precision, b->mv.n_modes, prop.name);
     for (char* c = key; *c; ++c)
         if (*c == '\n' || *c == '|') *c = ' ';
     const int use_graph = b->cfg.use_graph;

@@ -28,6 +28,7 @@ int build_mode_table(const le_mc_material_desc* d, double* omega, double* v, dou
 {
     if (!d) { *why = "null material descriptor"; return LE_MC_ERR_INVALID; }
     if (!(d->T_eq > 0.0)) { *why = "T_eq must be > 0"; return LE_MC_ERR_INVALID; }
+    if (!(d->scatter_g > -1.0 && d->scatter_g < 1.0)) { *why = "scatter_g must be in (-1, 1)"; return LE_MC_ERR_INVALID; }
     int n = 0;
     if (d->kind == LE_MC_MAT_GRAY) {
         if (!(d->gray_v > 0.0) || !(d->gray_tau > 0.0) || !(d->gray_C > 0.0)) {
@@ -138,21 +139,77 @@ int build_alias(const double* w, int n, uint32_t* thr, uint32_t* alias, const ch
     return LE_MC_OK;
 }
 
+template <typename R>
+static void fill_one(const TraceParams& P, Consts<R>& c)
+{
+    c.L = (R)P.L;
+    c.pitch = (R)P.pitch;
+    c.half = (R)(0.5 * P.pitch);
+    c.rad = (R)P.radius;
+    c.rad2 = (R)(P.radius * P.radius);
+    c.Dy = (R)P.pitch * (R)P.cells_y;
+    c.Dz = (R)P.pitch * (R)P.cells_z;
+    c.spec_lo = (R)P.spec_lo;
+    c.spec_hi = (R)P.spec_hi;
+    c.spec_pore = (R)P.spec_pore;
+    c.wlo = (R)fabs(P.dT_lo);
+    c.whi = (R)fabs(P.dT_hi);
+    c.grad_dir = P.dTdz > 0.0 ? R(-1) : R(1);
+    c.init_lo = (R)P.init_x_lo;
+    c.init_span = (R)(P.init_x_hi - P.init_x_lo);
+    c.p_sx = (R)P.p_sx;
+    c.p_st = (R)P.p_st;
+    c.p_tc = (R)P.p_tc;
+    c.p_y0 = (R)P.p_y0;
+    c.p_z0 = (R)P.p_z0;
+    c.t_final = (R)P.t_final;
+    c.sample_dt = (R)P.sample_dt;
+    c.lam_cut = (R)P.lam_cut;
+    c.g = (R)P.scatter_g;
+}
+
+void fill_consts(TraceParams& P)
+{
+    P.sign_lo = P.dT_lo >= 0.0 ? 1 : -1;
+    P.sign_hi = P.dT_hi >= 0.0 ? 1 : -1;
+    P.init_sign = P.init_dT >= 0.0 ? 1 : -1;
+    P.aniso = P.scatter_g != 0.0 ? 1 : 0;
+    fill_one<float>(P, P.c32);
+    fill_one<double>(P, P.c64);
+}
+
+void fill_instance32(BatchInstance& b)
+{
+    b.L32 = (float)b.L;
+    b.wlo32 = (float)fabs(b.dT_lo);
+    b.whi32 = (float)fabs(b.dT_hi);
+    b.dir32 = b.dTdz > 0.0 ? -1.0f : 1.0f;
+    b.lam_cut32 = (float)b.lam_cut;
+    b.sign_lo = b.dT_lo >= 0.0 ? 1 : -1;
+    b.sign_hi = b.dT_hi >= 0.0 ? 1 : -1;
+}
+
 int check_geometry(const le_mc_geometry_desc* g, const char** why)
 {
     if (!g) { *why = "null geometry descriptor"; return LE_MC_ERR_INVALID; }
-    auto wall_ok = [](int w) { return w == LE_MC_WALL_BLACK || w == LE_MC_WALL_DIFFUSE || w == LE_MC_WALL_SPECULAR; };
+    auto wall_ok = [](int w) { return w >= LE_MC_WALL_BLACK && w <= LE_MC_WALL_PARTIAL; };
+    auto prob_ok = [](double p) { return p >= 0.0 && p <= 1.0; };
     if (g->kind == LE_MC_GEOM_BULK) return LE_MC_OK;
     if (g->kind != LE_MC_GEOM_PLANES && g->kind != LE_MC_GEOM_POROUS) { *why = "unknown geometry kind"; return LE_MC_ERR_INVALID; }
     if (!(g->L > 0.0) || !isfinite(g->L)) { *why = "thickness L must be > 0"; return LE_MC_ERR_INVALID; }
     if (!wall_ok(g->wall_lo) || !wall_ok(g->wall_hi)) { *why = "unknown wall type"; return LE_MC_ERR_INVALID; }
+    if (!prob_ok(g->spec_lo) || !prob_ok(g->spec_hi) || !prob_ok(g->spec_pore)) {
+        *why = "specularities must be in [0, 1]";
+        return LE_MC_ERR_INVALID;
+    }
     if (g->kind == LE_MC_GEOM_POROUS) {
         if (!(g->pitch > 0.0) || !(g->radius >= 0.0) || !(2.0 * g->radius < g->pitch)) {
             *why = "porous geometry needs pitch > 0 and 0 <= 2 radius < pitch";
             return LE_MC_ERR_INVALID;
         }
-        if (g->pore_wall != LE_MC_WALL_DIFFUSE && g->pore_wall != LE_MC_WALL_SPECULAR) {
-            *why = "pore walls must be diffuse or specular";
+        if (g->pore_wall != LE_MC_WALL_DIFFUSE && g->pore_wall != LE_MC_WALL_SPECULAR &&
+            g->pore_wall != LE_MC_WALL_PARTIAL) {
+            *why = "pore walls must be diffuse, specular or partially specular";
             return LE_MC_ERR_INVALID;
         }
         if (g->cells_y < 1 || g->cells_z < 1 || g->cells_y > 65535 || g->cells_z > 65535) {

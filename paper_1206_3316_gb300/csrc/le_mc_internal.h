@@ -21,7 +21,7 @@ enum { CNT_PARTICLES = 0, CNT_SEGMENTS, CNT_SCATTERS, CNT_WALL, CNT_PERIODIC, CN
        CNT_ABSORBED, CNT_N };
 
 // Fates recorded per particle (same meaning as le_mc_particle::fate).
-enum { FATE_ABSORBED = 0, FATE_MAX_SCATTER = 1, FATE_MAX_EVENTS = 2, FATE_T_FINAL = 3 };
+enum { FATE_ABSORBED = 0, FATE_MAX_SCATTER = 1, FATE_MAX_EVENTS = 2, FATE_T_FINAL = 3, FATE_MAX_COLLISIONS = 4 };
 
 // Random-stream layout: Philox4x32-10 with key = seed and counter
 // (event, block, particle id, instance id).  Event 0 is emission (block 0:
@@ -38,6 +38,26 @@ struct BatchInstance {
     double lam_cut;        // long-first threshold for this instance
     uint32_t inst_id;      // 4th Philox counter word
     uint32_t n_particles;
+    // the same in FP32 for FP32 kernels: L, |dT_lo|, |dT_hi|, the gradient
+    // source's direction factor (-1 if dT/dz > 0, else +1), lam_cut
+    float L32, wlo32, whi32, dir32, lam_cut32;
+    int32_t sign_lo, sign_hi;  // WALLS: sign of dT_lo, dT_hi
+};
+
+// Problem constants in one trajectory precision, converted once on the host
+// (fill_consts), so that FP32 kernels never convert a double inside the loop:
+// on GB300 the FP64 pipe that executes such conversions is narrow, and a
+// conversion there stalls the warp for many cycles.
+template <typename R>
+struct Consts {
+    R L, pitch, half, rad, rad2, Dy, Dz;  // geometry
+    R spec_lo, spec_hi, spec_pore;        // PARTIAL walls
+    R wlo, whi;                           // WALLS: |dT_lo|, |dT_hi|
+    R grad_dir;                           // GRADIENT: -1 if dT/dz > 0, else +1
+    R init_lo, init_span;                 // INITIAL: heated layer
+    R p_sx, p_st, p_tc, p_y0, p_z0;       // PULSE
+    R t_final, sample_dt, lam_cut;
+    R g;                                  // scattering mean cosine (0 isotropic)
 };
 
 constexpr int kBatchSmemMax = 512;
@@ -57,17 +77,23 @@ struct TraceParams {
     const uint2* alias_emit;  // [n_modes] (threshold, alias) for C_b v_b
     const uint2* alias_init;  // [n_modes] (threshold, alias) for C_b (initial condition)
     int32_t n_modes;
+    double scatter_g;         // relaxation-event direction law: 0 isotropic, else Henyey-Greenstein
     // geometry
     int32_t geom, wall_lo, wall_hi, pore_wall;
     int32_t cells_y, cells_z;
     double L, pitch, radius;
+    double spec_lo, spec_hi, spec_pore;  // PARTIAL walls: specular probability
     // source
     int32_t src;
     double dT_lo, dT_hi, dTdz;
     double p_sx, p_st, p_tc, p_y0, p_z0;
     double init_dT, init_x_lo, init_x_hi;
+    int32_t sign_lo, sign_hi, init_sign;  // WALLS: sign of dT_lo, dT_hi; INITIAL: of init_dT
+    int32_t aniso;                        // scatter_g != 0
+    Consts<float> c32;                    // filled by fill_consts from the doubles
+    Consts<double> c64;
     // run
-    uint32_t n_particles, key0, key1, inst, max_scatter, max_events;
+    uint32_t n_particles, key0, key1, inst, max_scatter, max_events, max_collisions;
     // slab profile: [4][n_batch][n_bins_x + 1] (T direct, T difference,
     // q direct, q difference), FP64
     int32_t n_bins_x, n_batch;
@@ -112,6 +138,11 @@ int build_mode_table(const le_mc_material_desc* d, double* omega, double* v, dou
 int build_alias(const double* w, int n, uint32_t* thr, uint32_t* alias, const char** why);
 int check_geometry(const le_mc_geometry_desc* g, const char** why);
 int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes, const char** why);
+// Derived constants (signs, both Consts) from the double fields of P; call
+// after every double field is set.
+void fill_consts(TraceParams& P);
+// FP32 fields of a batch instance from its double fields.
+void fill_instance32(BatchInstance& b);
 
 struct MaterialSums {
     double C_tot, Cv_sum;
@@ -128,6 +159,7 @@ struct MaterialView {
     int n_modes;
     int device;
     MaterialSums sums;
+    double scatter_g;
 };
 bool material_view(le_mc_material m, MaterialView* out);
 void material_retain(le_mc_material m);

@@ -127,10 +127,14 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     P.alias_scat = mv.alias_scat;
     P.alias_emit = mv.alias_emit;
     P.n_modes = mv.n_modes;
+    P.scatter_g = mv.scatter_g;
     P.geom = G.kind;
     P.wall_lo = G.wall_lo;
     P.wall_hi = G.wall_hi;
     P.pore_wall = G.pore_wall;
+    P.spec_lo = G.spec_lo;
+    P.spec_hi = G.spec_hi;
+    P.spec_pore = G.spec_pore;
     P.cells_y = G.kind == LE_MC_GEOM_POROUS ? G.cells_y : 1;
     P.cells_z = G.kind == LE_MC_GEOM_POROUS ? G.cells_z : 1;
     P.L = G.kind == LE_MC_GEOM_BULK ? 1.0 : G.L;
@@ -146,6 +150,7 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     P.inst = r.instance_id;
     P.max_scatter = r.max_scatter;
     P.max_events = r.max_events;
+    P.max_collisions = r.max_collisions;
     P.n_batch = 1;
     P.sums = d_sums;
     P.counters = d_counters;
@@ -161,6 +166,7 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     P.refill_min = r.refill_min > 0 ? r.refill_min : 1;
     P.chunk = r.chunk > 0 ? r.chunk : 32;
     P.first = r.first_particle;
+    fill_consts(P);
     for (int i = 0; i < 10; ++i) {
         a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
         a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;

@@ -50,7 +50,7 @@ struct Slots<T, 0> {};
 // are kept only for POROUS geometries, the emission time only for PULSE, the
 // batch instance only in batch mode.
 template <typename R, bool YZ, bool TIME, bool INST>
-struct EmitBuffer {
+struct alignas(16) EmitBuffer {
     R x[kBufSlots];
     R ox[kBufSlots], oy[kBufSlots], oz[kBufSlots];
     uint32_t pid[kBufSlots];
@@ -60,6 +60,10 @@ struct EmitBuffer {
     Slots<R, TIME ? kBufSlots : 0> t;
     Slots<uint32_t, INST ? kBufSlots : 0> inst;
 };
+
+// warps with at most this many busy lanes at the end get their random words
+// precomputed by the idle lanes (see the lifetime-tail branch of trace_kernel)
+constexpr int kTailLanes = 8;
 
 template <typename R, int GEOM, int SRC, bool BATCH = false>
 using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE, BATCH>;
@@ -99,31 +103,56 @@ __device__ __forceinline__ void load_props(const void* props, uint32_t mode, R& 
     }
 }
 
+// Problem constants in the trajectory precision (converted on the host).
+template <typename R>
+__device__ __forceinline__ const Consts<R>& consts_of(const TraceParams& P)
+{
+    if constexpr (sizeof(R) == 4) return P.c32;
+    else return P.c64;
+}
+
 // What step I needs to know about the problem a particle belongs to: the
-// run itself, or one instance of a batch.
+// run itself, or one instance of a batch (thickness, wall-source weights and
+// signs, gradient direction factor), in the trajectory precision.
+template <typename R>
 struct EmitCtx {
-    double L, dT_lo, dT_hi, dTdz;
+    R L, wlo, whi, dir;
+    int s_lo, s_hi;
     uint32_t inst;
 };
 
-__device__ __forceinline__ EmitCtx run_ctx(const TraceParams& P)
+template <typename R>
+__device__ __forceinline__ EmitCtx<R> run_ctx(const TraceParams& P)
 {
-    EmitCtx c;
-    c.L = P.L;
-    c.dT_lo = P.dT_lo;
-    c.dT_hi = P.dT_hi;
-    c.dTdz = P.dTdz;
+    const Consts<R>& K = consts_of<R>(P);
+    EmitCtx<R> c;
+    c.L = K.L;
+    c.wlo = K.wlo;
+    c.whi = K.whi;
+    c.dir = K.grad_dir;
+    c.s_lo = P.sign_lo;
+    c.s_hi = P.sign_hi;
     c.inst = P.inst;
     return c;
 }
 
-__device__ __forceinline__ EmitCtx batch_ctx(const BatchInstance& b)
+template <typename R>
+__device__ __forceinline__ EmitCtx<R> batch_ctx(const BatchInstance& b)
 {
-    EmitCtx c;
-    c.L = b.L;
-    c.dT_lo = b.dT_lo;
-    c.dT_hi = b.dT_hi;
-    c.dTdz = b.dTdz;
+    EmitCtx<R> c;
+    if constexpr (sizeof(R) == 4) {
+        c.L = b.L32;
+        c.wlo = b.wlo32;
+        c.whi = b.whi32;
+        c.dir = b.dir32;
+    } else {
+        c.L = b.L;
+        c.wlo = fabs(b.dT_lo);
+        c.whi = fabs(b.dT_hi);
+        c.dir = b.dTdz > 0.0 ? -1.0 : 1.0;
+    }
+    c.s_lo = b.sign_lo;
+    c.s_hi = b.sign_hi;
     c.inst = b.inst_id;
     return c;
 }
@@ -143,12 +172,13 @@ __device__ __forceinline__ uint32_t batch_find(const unsigned long long* offsets
 // emission alias table is read from global memory (once per particle, cached
 // in L1), which leaves shared memory to the per-flight tables.
 template <typename R, int GEOM, int SRC>
-__device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCtx& E, const RoundKeys& rk,
+__device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCtx<R>& E, const RoundKeys& rk,
                                               const uint2* alias_emit, uint32_t pid, R& x, R& y, R& z, R& ox,
                                               R& oy, R& oz, R& t, uint32_t& mode, int& sign, uint32_t& cy,
                                               uint32_t& cz)
 {
     using M = DMath<R>;
+    const Consts<R>& K = consts_of<R>(P);
     const uint4 r = philox4x32_10(make_uint4(0u, 0u, pid, E.inst), rk);
     mode = alias_draw(alias_emit, (uint32_t)P.n_modes, r.y);
     const R u0 = M::uniform(r.x), u2 = M::uniform(r.z), u3 = M::uniform(r.w);
@@ -159,27 +189,26 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
     bool ok = true;
     if constexpr (SRC == LE_MC_SRC_WALLS) {
         // isothermal walls: wall picked by |T_b - T_eq|, cosine law into the domain
-        const R wlo = (R)fabs(E.dT_lo), whi = (R)fabs(E.dT_hi);
-        const bool lo = u0 * (wlo + whi) < wlo;
+        const bool lo = u0 * (E.wlo + E.whi) < E.wlo;
         const R mu = M::sqrt_(u2);
         const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
         ox = lo ? mu : -mu;
         oy = st * cs;
         oz = st * sn;
-        x = lo ? R(0) : (R)E.L;
-        sign = lo ? (E.dT_lo >= 0.0 ? 1 : -1) : (E.dT_hi >= 0.0 ? 1 : -1);
+        x = lo ? R(0) : E.L;
+        sign = lo ? E.s_lo : E.s_hi;
     } else if constexpr (SRC == LE_MC_SRC_GRADIENT) {
         // Eq. 6: |cos| law about z, sign sgn(-cos dT/dz), even ids positive
         sign = (pid & 1u) ? -1 : 1;
-        const R dir = (R)sign * (E.dTdz > 0.0 ? R(-1) : R(1));
+        const R dir = (R)sign * E.dir;
         const R mu = dir * M::sqrt_(u2);
         const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
         ox = st * cs;
         oy = st * sn;
         oz = mu;
-        x = (GEOM == LE_MC_GEOM_BULK) ? R(0) : u0 * (R)E.L;
+        x = (GEOM == LE_MC_GEOM_BULK) ? R(0) : u0 * E.L;
         if constexpr (GEOM == LE_MC_GEOM_POROUS) {
-            const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
+            const R pitch = K.pitch, half = K.half, r2 = K.rad2;
             ok = false;
             for (uint32_t b = 1; b <= kMaxTries; ++b) {
                 const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
@@ -199,14 +228,14 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
     } else if constexpr (SRC == LE_MC_SRC_INITIAL) {
         // initial condition: uniform in the heated layer (solid part), modes
         // weighted by C_b (table passed by the caller), isotropic, t = 0
-        sign = P.init_dT >= 0.0 ? 1 : -1;
+        sign = P.init_sign;
         const R mu = R(2) * u2 - R(1);
         const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
         ox = st * cs;
         oy = st * sn;
         oz = mu;
-        x = (R)P.init_x_lo + u0 * (R)(P.init_x_hi - P.init_x_lo);
-        const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
+        x = K.init_lo + u0 * K.init_span;
+        const R pitch = K.pitch, half = K.half, r2 = K.rad2;
         ok = false;
         for (uint32_t b = 1; b <= kMaxTries; ++b) {
             const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
@@ -229,17 +258,17 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
         ox = -mu;
         oy = st * cs;
         oz = st * sn;
-        x = (R)E.L;
-        const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, r2 = (R)(P.radius * P.radius);
-        const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
+        x = E.L;
+        const R pitch = K.pitch, half = K.half, r2 = K.rad2;
+        const R Dy = K.Dy, Dz = K.Dz;
         ok = false;
         for (uint32_t b = 1; b <= kMaxTries; ++b) {
             const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
-            const R rad = (R)P.p_sx * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x)));
+            const R rad = K.p_sx * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x)));
             R s2, c2;
             M::sincos_2pi(M::uniform(q.y), &s2, &c2);
-            R Y = (R)P.p_y0 + rad * c2;
-            R Z = (R)P.p_z0 + rad * s2;
+            R Y = K.p_y0 + rad * c2;
+            R Z = K.p_z0 + rad * s2;
             Y -= Dy * M::floor_(Y / Dy);
             Z -= Dz * M::floor_(Z / Dz);
             int iy = (int)M::floor_(Y / pitch), iz = (int)M::floor_(Z / pitch);
@@ -252,13 +281,13 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
             const R dy = y - half, dz = z - half;
             if (!(dy * dy + dz * dz < r2)) { ok = true; break; }
         }
-        t = (R)P.p_tc;
+        t = K.p_tc;
         bool tok = false;
         for (uint32_t b = kTimeBlock0; b < kTimeBlock0 + kMaxTries; ++b) {
             const uint4 q = philox4x32_10(make_uint4(0u, b, pid, E.inst), rk);
             R s2, c2;
             M::sincos_2pi(M::uniform(q.y), &s2, &c2);
-            const R t0 = (R)P.p_tc + (R)P.p_st * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x))) * c2;
+            const R t0 = K.p_tc + K.p_st * M::sqrt_(R(2) * M::neg_log(M::uniform(q.x))) * c2;
             if (t0 >= R(0)) { t = t0; tok = true; break; }
         }
         ok = ok && tok;
@@ -279,13 +308,17 @@ __host__ __device__ inline size_t table_bytes(int n_modes)
     return ((size_t)n_modes * per_mode + 15) & ~(size_t)15;
 }
 
-// DIFF: every wall (both planes, and the pores) is diffuse, so the wall law
-// needs no per-wall lookup and no specular or absorbing branch.
+// DIFF: every wall (both planes, and the pores) is diffuse and relaxation
+// events are isotropic (the paper's base case), so the wall law needs no
+// per-wall lookup and no specular, absorbing or partial branch, and the
+// direction law no anisotropic branch.
 template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
 {
     using M = DMath<R>;
     using Buf = BufferOf<R, GEOM, SRC, BATCH>;
+    static_assert(sizeof(Buf) >= 32 * sizeof(uint4) && sizeof(Buf) % 16 == 0,
+                  "the lifetime-tail branch keeps 32 random words in a warp's emission buffer");
     constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
     constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
@@ -350,9 +383,16 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     const uint32_t n_long = P.long_list ? min(*P.long_count, P.long_cap) : 0u;
     const unsigned long long q_total = (unsigned long long)n_long + n_pos;
     const int refill_min = P.refill_min > 1 ? P.refill_min : 1;
-    const R L = (R)P.L;
-    const R pitch = (R)P.pitch, half = R(0.5) * (R)P.pitch, rad = (R)P.radius, rad2 = (R)(P.radius * P.radius);
+    const Consts<R>& K = consts_of<R>(P);
+    const R L = K.L;
+    const R pitch = K.pitch, half = K.half, rad = K.rad, rad2 = K.rad2;
     const R big = M::big();
+    // anisotropic relaxation-event direction law (kernel-uniform)
+    const bool aniso = !DIFF && P.aniso != 0;
+    const R hg = K.g;
+    // partially specular walls present (kernel-uniform)
+    const bool any_partial = !DIFF && (P.wall_lo == LE_MC_WALL_PARTIAL || P.wall_hi == LE_MC_WALL_PARTIAL ||
+                                       (POROUS && P.pore_wall == LE_MC_WALL_PARTIAL));
 
     // particle state
     R x = 0, y = 0, z = 0, ox = 0, oy = 0, oz = 1, t = 0, lam = 1, vg = 1;
@@ -372,8 +412,15 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     int cnt = 0;         // emission buffer fill (warp-uniform)
     bool qdone = false;  // particle queue exhausted (warp-uniform)
     // queue positions this warp has claimed but not yet emitted (warp-uniform);
-    // claims are `chunk` positions at a time
+    // claims are `chunk` positions at a time, except inside the long-first
+    // list: there a claim is 32 positions, one particle per lane, because
+    // each listed particle can run for as long as a lane's whole share of the
+    // ordinary ones, and a larger claim would queue several of them behind
+    // one another on one lane (claims much smaller than a warp spread them
+    // over every warp instead, which leaves a few busy lanes per warp at the
+    // end: measured slower on the film)
     const unsigned long long chunk = P.chunk >= 32 ? (unsigned long long)P.chunk : 32ull;
+    const unsigned long long long_claim = 32ull;
     unsigned long long w_next = 0, w_end = 0;
     uint32_t cur_b = 0xFFFFFFFFu;  // batch instance the lane accumulators belong to
 
@@ -398,6 +445,258 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
         c_part = c_seg = c_scat = c_wall = c_per = c_trunc = c_abs = 0;
     };
 
+    // ---- one segment: steps II-VI, from the segment's four random words r
+    // (counter (n_seg + 1, 0, pid, instance): known before the segment runs)
+    auto segment = [&](const uint4 r) {
+            // step II: flight to the next relaxation event (as a length)
+            const R ell = lam * M::neg_log(M::uniform(r.x));
+            // step III: first boundary along the ray
+            R d_b = big;
+            int kind = HIT_NONE;
+            if constexpr (GEOM != LE_MC_GEOM_BULK) {
+                // distance to the wall ahead; a flight parallel to the walls gets
+                // an infinite (or NaN, never <= ell) distance and no hit
+                const bool up = ox > R(0);
+                d_b = M::div(up ? (Lp - x) : x, fabs(ox));
+                kind = up ? HIT_XHI : HIT_XLO;
+            }
+            if constexpr (POROUS) {
+                if (rad > R(0)) {
+                    const R ry = y - half, rz = z - half;
+                    const R a = oy * oy + oz * oz;
+                    const R b = ry * oy + rz * oz;
+                    const R c = ry * ry + rz * rz - rad2;
+                    if (a > R(0) && b < R(0)) {
+                        const R disc = b * b - a * c;
+                        if (disc >= R(0)) {
+                            R tc = M::div(c, M::sqrt_(disc) - b);
+                            tc = fmax(tc, R(0));
+                            if (tc < d_b) { d_b = tc; kind = HIT_CYL; }
+                        }
+                    }
+                }
+                if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
+                else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
+                if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
+                else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
+            }
+            bool hit = (kind != HIT_NONE) && (d_b <= ell);
+            if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+                // Absorbing walls decide a particle's fate: when the FP32 flight
+                // and wall distances are within a few ulp of each other (grazing
+                // flights make the wall distance large and its rounding
+                // relatively coarse), redo the comparison in FP64 from the same
+                // inputs.
+                const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
+                if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
+                    const double u = (double)M::uniform(r.x);
+                    const double ell64 = (double)lam * -log(u);
+                    const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
+                    hit = d64 <= ell64;
+                }
+            }
+            R seg = hit ? d_b : ell;
+            if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+                seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
+            }
+            R x_new = x + ox * seg;
+            if (hit && kind == HIT_XLO) x_new = R(0);
+            if (hit && kind == HIT_XHI) x_new = Lp;
+
+            // end time of the segment, computed once: the sample windows [t, t_b)
+            // of consecutive segments must tile time exactly (no sample lost or
+            // counted twice), so the particle's next start is this same value
+            R t_b = t;
+            if constexpr (TRANSIENT) t_b = t + seg / vg;
+            // step V: contribution of the segment
+            if constexpr (TRANSIENT) {
+                const R dts = K.sample_dt;
+                const R t_end = fmin(t_b, K.t_final);
+                // first candidate sample, one early: the rounded quotient may
+                // overshoot by one, and the comparisons below decide exactly
+                int k = (int)ceil(t / dts - R(0.5)) - 1;
+                k = max(k, 0);
+                const R Dy = K.Dy, Dz = K.Dz;
+                const int wy = cy % P.cells_y, wz = cz % P.cells_z;
+                const R Yc = (R)(wy < 0 ? wy + P.cells_y : wy) * pitch;
+                const R Zc = (R)(wz < 0 ? wz + P.cells_z : wz) * pitch;
+                for (; k < P.n_samples; ++k) {
+                    const R ts = ((R)k + R(0.5)) * dts;
+                    if (ts < t) continue;
+                    if (ts >= t_b || ts > t_end) break;
+                    const R d = vg * (ts - t);
+                    const R px = x + ox * d, py = Yc + (y + oy * d), pz = Zc + (z + oz * d);
+                    int ix = (int)M::floor_(px / L * (R)P.gx);
+                    int iy = (int)M::floor_(py / Dy * (R)P.gy);
+                    int iz = (int)M::floor_(pz / Dz * (R)P.gz);
+                    ix = min(max(ix, 0), P.gx - 1);
+                    iy = min(max(iy, 0), P.gy - 1);
+                    iz = min(max(iz, 0), P.gz - 1);
+                    const size_t cell = (((size_t)k * P.gz + iz) * P.gy + iy) * P.gx + ix;
+                    atomicAdd(&P.grid[cell], sign);
+                }
+            }
+            if constexpr (PROFILE) {
+                // time and x-displacement spent in each bin along x (slab)
+                const int nb = P.n_bins_x;
+                const R dx = L / (R)nb;
+                const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
+                const size_t stride = (size_t)nb + 1;
+                double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
+                double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
+                double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
+                double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
+                const R lo = fmin(x, x_new), hi = fmax(x, x_new);
+                int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
+                k0 = min(max(k0, 0), nb - 1);
+                k1 = min(max(k1, 0), nb - 1);
+                const double s = (double)sign;
+                if (ox == R(0)) {
+                    atomicAdd(&Td[k0], s * (double)(seg / vg));
+                } else {
+                    const R w = R(1) / (vg * fabs(ox));  // time per unit x
+                    const R qs = ox > R(0) ? R(1) : R(-1);
+                    if (k0 == k1) {
+                        const R len = hi - lo;
+                        atomicAdd(&Td[k0], s * (double)(len * w));
+                        atomicAdd(&qd[k0], s * (double)(len * qs));
+                    } else {
+                        const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
+                        const R lb = hi - (R)k1 * dx;        // partial last bin
+                        atomicAdd(&Td[k0], s * (double)(la * w));
+                        atomicAdd(&qd[k0], s * (double)(la * qs));
+                        atomicAdd(&Td[k1], s * (double)(lb * w));
+                        atomicAdd(&qd[k1], s * (double)(lb * qs));
+                        if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
+                            atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
+                            atomicAdd(&Tr[k1], -s * (double)(dx * w));
+                            atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
+                            atomicAdd(&qr[k1], -s * (double)(dx * qs));
+                        }
+                    }
+                }
+            }
+            const R dL = AXIS_X ? (x_new - x) : oz * seg;
+            Lacc += dL;
+            hrun += dL;
+
+            // steps IVa / IVb.  Every lane evaluates the same straight-line code
+            // and keeps its own outcome through selects, so walls and relaxation
+            // events do not split the warp.
+            x = x_new;
+            if constexpr (POROUS) {
+                y += oy * seg;
+                z += oz * seg;
+            }
+            if constexpr (TRANSIENT) t = t_b;
+            ++n_seg;
+            const bool scat = !hit;
+            int wall = -1;
+            if constexpr (DIFF) {
+                wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
+            } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
+                wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
+                if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
+                wall = hit ? wall : -1;
+                // partially specular wall: specular with probability p, decided by
+                // the flight's second uniform (a relaxation's mode draw otherwise)
+                if (any_partial && wall == LE_MC_WALL_PARTIAL) {
+                    const R p = (kind == HIT_XLO) ? K.spec_lo : ((kind == HIT_XHI) ? K.spec_hi : K.spec_pore);
+                    wall = (M::uniform(r.y) < p) ? (int)LE_MC_WALL_SPECULAR : (int)LE_MC_WALL_DIFFUSE;
+                }
+            }
+            const bool on_wall = wall >= 0;
+            const bool absorbed = wall == LE_MC_WALL_BLACK;
+            const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
+            const bool periodic = hit && !on_wall;
+            // Eq. 2 redraw (kept only on a relaxation event)
+            if constexpr (FUSED) {
+                const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
+                const uint4 e = s_fused[(uint32_t)(mm >> 32)];
+                const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
+                lam = scat ? lam_new : lam;
+            } else {
+                const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+                const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
+                lam = scat ? lam_new : lam;
+                vg = scat ? vg_new : vg;
+            }
+            // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
+            const R u2 = M::uniform(r.z);
+            R sn, cs;
+            M::sincos_2pi(M::uniform(r.w), &sn, &cs);
+            const R mu = scat ? (R(2) * u2 - R(1)) : M::sqrt_(u2);
+            const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+            const R a = st * cs, b = st * sn;
+            // direction after a relaxation: isotropic (a, b, mu) about z, or the
+            // Henyey-Greenstein law of mean cosine g about the incoming direction,
+            // its cosine from the inverted CDF and its azimuth in the
+            // orthonormal frame of Duff et al. (JCGT 2017) built on (ox, oy, oz)
+            R sx = a, sy = b, sz = mu;
+            if (aniso && scat) {
+                const R q = M::div(R(1) - hg * hg, R(1) - hg + R(2) * hg * u2);
+                R mh = M::div(R(1) + hg * hg - q * q, R(2) * hg);
+                mh = fmin(fmax(mh, R(-1)), R(1));
+                const R sh = M::sqrt_(fmax(R(0), R(1) - mh * mh));
+                const R sg = oz >= R(0) ? R(1) : R(-1);
+                const R fa = M::div(R(-1), sg + oz);
+                const R fb = ox * oy * fa;
+                sx = mh * ox + sh * (cs * (R(1) + sg * ox * ox * fa) + sn * fb);
+                sy = mh * oy + sh * (cs * (sg * fb) + sn * (sg + oy * oy * fa));
+                sz = mh * oz + sh * (cs * (-sg * ox) + sn * (-oy));
+            }
+            R nox = sx, noy = sy, noz = sz;
+            if constexpr (GEOM != LE_MC_GEOM_BULK) {
+                // x walls: Lambertian about +-x, or mirror
+                const R wox = diffuse ? ((kind == HIT_XLO) ? mu : -mu) : -ox;
+                const R woy = diffuse ? a : oy;
+                const R woz = diffuse ? b : oz;
+                if constexpr (POROUS) {
+                    // pore wall: normal from the axis to the hit point
+                    const R ny = (y - half) / rad, nz = (z - half) / rad;
+                    const R dn = oy * ny + oz * nz;
+                    const R cox = diffuse ? a : ox;
+                    const R coy = diffuse ? (mu * ny - b * nz) : (oy - R(2) * dn * ny);
+                    const R coz = diffuse ? (mu * nz + b * ny) : (oz - R(2) * dn * nz);
+                    const bool cyl = kind == HIT_CYL;
+                    nox = scat ? sx : (periodic ? ox : (cyl ? cox : wox));
+                    noy = scat ? sy : (periodic ? oy : (cyl ? coy : woy));
+                    noz = scat ? sz : (periodic ? oz : (cyl ? coz : woz));
+                    // periodic unit-cell face: re-insert on the opposite face
+                    const bool yhi = periodic && kind == HIT_YHI, ylo = periodic && kind == HIT_YLO;
+                    const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
+                    y = yhi ? R(0) : (ylo ? pitch : y);
+                    z = zhi ? R(0) : (zlo ? pitch : z);
+                    cy += (int)yhi - (int)ylo;
+                    cz += (int)zhi - (int)zlo;
+                } else {
+                    nox = scat ? sx : wox;
+                    noy = scat ? sy : woy;
+                    noz = scat ? sz : woz;
+                }
+            }
+            ox = nox;
+            oy = noy;
+            oz = noz;
+            n_scat += scat ? 1u : 0u;
+            n_wall += on_wall ? 1u : 0u;
+            n_per += periodic ? 1u : 0u;
+            if (P.n_hj > 0 && scat) {
+                if (n_scat - 1u < (uint32_t)P.n_hj) {
+                    atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
+                    atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
+                }
+                hrun = R(0);
+            }
+            // step VI and truncation
+            if (absorbed) { fate = FATE_ABSORBED; alive = false; }
+            else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
+            else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
+            else if (P.max_collisions > 0u && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
+            else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
+            if (!alive) pending = true;
+    };
+
     for (;;) {
         const unsigned dead = __ballot_sync(FULL, !alive);
         // refill once refill_min lanes are idle (or at once near the end)
@@ -417,7 +716,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                 c_scat += n_scat;
                 c_wall += n_wall;
                 c_per += n_per;
-                c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS) ? 1u : 0u;
+                c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
                 c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
                 if (P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
                     atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
@@ -445,10 +744,11 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                 // step I for the next 32 claimed queue positions, whole warp
                 if (w_next >= w_end) {
                     unsigned long long base = 0;
-                    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), chunk);
+                    const unsigned long long claim = (w_end < n_long) ? long_claim : chunk;
+                    if (lane == 0) base = atomicAdd(reinterpret_cast<unsigned long long*>(P.queue), claim);
                     base = __shfl_sync(FULL, base, 0);
                     w_next = base;
-                    w_end = min(base + chunk, q_total);
+                    w_end = min(base + claim, q_total);
                     if (base >= q_total) {
                         qdone = true;
                         break;
@@ -472,14 +772,14 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                 const unsigned vmask = __ballot_sync(FULL, valid);
                 if (valid) {
                     uint32_t id = pos, eb = 0;
-                    EmitCtx ctx;
+                    EmitCtx<R> ctx;
                     if constexpr (BATCH) {
                         eb = batch_find(P.offsets, (uint32_t)P.n_instances, pos);
                         id = (uint32_t)(pos - P.offsets[eb]);
-                        ctx = batch_ctx(P.instances[eb]);
+                        ctx = batch_ctx<R>(P.instances[eb]);
                     } else {
                         id = P.first + pos;
-                        ctx = run_ctx(P);
+                        ctx = run_ctx<R>(P);
                     }
                     R ex, ey, ez, eox, eoy, eoz, et;
                     uint32_t em, ecy, ecz;
@@ -527,7 +827,8 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                     if constexpr (BATCH) {
                         bidx = buf.inst.v[slot];
                         const BatchInstance& bi = P.instances[bidx];
-                        Lp = (R)bi.L;
+                        if constexpr (sizeof(R) == 4) Lp = bi.L32;
+                        else Lp = bi.L;
                         instw = bi.inst_id;
                     }
                     mode0 = ms & 0x7FFFFFFFu;
@@ -550,233 +851,37 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             __syncwarp();
             if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
         }
+        // Lifetime tail: with the queue exhausted and the buffer empty, a warp
+        // left with a few long trajectories runs at the latency of one lane.
+        // Its idle lanes then compute the random words of the busy lanes' next
+        // segments (the counters are known in advance) into the emission
+        // buffer's storage, so the busy lanes trace without Philox on their
+        // critical path.  Each segment uses the same words as otherwise.
+        if (qdone && cnt == 0) {
+            const unsigned m = __ballot_sync(FULL, alive);
+            const int n_a = __popc(m);
+            if (n_a > 0 && n_a <= kTailLanes) {
+                const int steps = 32 / n_a;
+                const int a = lane % n_a, s = lane / n_a;
+                unsigned mm = m;
+                for (int i = 0; i < a; ++i) mm &= mm - 1u;
+                const int src = __ffs((int)mm) - 1;
+                const uint32_t seg_a = __shfl_sync(FULL, n_seg, src);
+                const uint32_t pid_a = __shfl_sync(FULL, pid, src);
+                const uint32_t inst_a = __shfl_sync(FULL, instw, src);
+                uint4* words = reinterpret_cast<uint4*>(&buf);
+                if (s < steps) words[s * n_a + a] = philox4x32_10(make_uint4(seg_a + 1u + (uint32_t)s, 0u, pid_a, inst_a), rk);
+                __syncwarp();
+                if (alive) {
+                    const int my_a = __popc(m & lanemask_lt);
+                    for (int k = 0; k < steps && alive; ++k) segment(words[k * n_a + my_a]);
+                }
+                __syncwarp();
+                continue;
+            }
+        }
         if (!alive) continue;
-
-        // ---- one segment: steps II-VI ------------------------------------
-        const uint4 r = philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk);
-        // step II: flight to the next relaxation event (as a length)
-        const R ell = lam * M::neg_log(M::uniform(r.x));
-        // step III: first boundary along the ray
-        R d_b = big;
-        int kind = HIT_NONE;
-        if constexpr (GEOM != LE_MC_GEOM_BULK) {
-            // distance to the wall ahead; a flight parallel to the walls gets
-            // an infinite (or NaN, never <= ell) distance and no hit
-            const bool up = ox > R(0);
-            d_b = M::div(up ? (Lp - x) : x, fabs(ox));
-            kind = up ? HIT_XHI : HIT_XLO;
-        }
-        if constexpr (POROUS) {
-            if (rad > R(0)) {
-                const R ry = y - half, rz = z - half;
-                const R a = oy * oy + oz * oz;
-                const R b = ry * oy + rz * oz;
-                const R c = ry * ry + rz * rz - rad2;
-                if (a > R(0) && b < R(0)) {
-                    const R disc = b * b - a * c;
-                    if (disc >= R(0)) {
-                        R tc = M::div(c, M::sqrt_(disc) - b);
-                        tc = fmax(tc, R(0));
-                        if (tc < d_b) { d_b = tc; kind = HIT_CYL; }
-                    }
-                }
-            }
-            if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
-            else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
-            if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
-            else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
-        }
-        bool hit = (kind != HIT_NONE) && (d_b <= ell);
-        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
-            // Absorbing walls decide a particle's fate: when the FP32 flight
-            // and wall distances are within a few ulp of each other (grazing
-            // flights make the wall distance large and its rounding
-            // relatively coarse), redo the comparison in FP64 from the same
-            // inputs.
-            const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
-            if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
-                const double u = (double)M::uniform(r.x);
-                const double ell64 = (double)lam * -log(u);
-                const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
-                hit = d64 <= ell64;
-            }
-        }
-        R seg = hit ? d_b : ell;
-        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
-            seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
-        }
-        R x_new = x + ox * seg;
-        if (hit && kind == HIT_XLO) x_new = R(0);
-        if (hit && kind == HIT_XHI) x_new = Lp;
-
-        // end time of the segment, computed once: the sample windows [t, t_b)
-        // of consecutive segments must tile time exactly (no sample lost or
-        // counted twice), so the particle's next start is this same value
-        R t_b = t;
-        if constexpr (TRANSIENT) t_b = t + seg / vg;
-        // step V: contribution of the segment
-        if constexpr (TRANSIENT) {
-            const R dts = (R)P.sample_dt;
-            const R t_end = fmin(t_b, (R)P.t_final);
-            // first candidate sample, one early: the rounded quotient may
-            // overshoot by one, and the comparisons below decide exactly
-            int k = (int)ceil(t / dts - R(0.5)) - 1;
-            k = max(k, 0);
-            const R Dy = pitch * (R)P.cells_y, Dz = pitch * (R)P.cells_z;
-            const int wy = cy % P.cells_y, wz = cz % P.cells_z;
-            const R Yc = (R)(wy < 0 ? wy + P.cells_y : wy) * pitch;
-            const R Zc = (R)(wz < 0 ? wz + P.cells_z : wz) * pitch;
-            for (; k < P.n_samples; ++k) {
-                const R ts = ((R)k + R(0.5)) * dts;
-                if (ts < t) continue;
-                if (ts >= t_b || ts > t_end) break;
-                const R d = vg * (ts - t);
-                const R px = x + ox * d, py = Yc + (y + oy * d), pz = Zc + (z + oz * d);
-                int ix = (int)M::floor_(px / L * (R)P.gx);
-                int iy = (int)M::floor_(py / Dy * (R)P.gy);
-                int iz = (int)M::floor_(pz / Dz * (R)P.gz);
-                ix = min(max(ix, 0), P.gx - 1);
-                iy = min(max(iy, 0), P.gy - 1);
-                iz = min(max(iz, 0), P.gz - 1);
-                const size_t cell = (((size_t)k * P.gz + iz) * P.gy + iy) * P.gx + ix;
-                atomicAdd(&P.grid[cell], sign);
-            }
-        }
-        if constexpr (PROFILE) {
-            // time and x-displacement spent in each bin along x (slab)
-            const int nb = P.n_bins_x;
-            const R dx = L / (R)nb;
-            const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
-            const size_t stride = (size_t)nb + 1;
-            double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
-            double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
-            double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
-            double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
-            const R lo = fmin(x, x_new), hi = fmax(x, x_new);
-            int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
-            k0 = min(max(k0, 0), nb - 1);
-            k1 = min(max(k1, 0), nb - 1);
-            const double s = (double)sign;
-            if (ox == R(0)) {
-                atomicAdd(&Td[k0], s * (double)(seg / vg));
-            } else {
-                const R w = R(1) / (vg * fabs(ox));  // time per unit x
-                const R qs = ox > R(0) ? R(1) : R(-1);
-                if (k0 == k1) {
-                    const R len = hi - lo;
-                    atomicAdd(&Td[k0], s * (double)(len * w));
-                    atomicAdd(&qd[k0], s * (double)(len * qs));
-                } else {
-                    const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
-                    const R lb = hi - (R)k1 * dx;        // partial last bin
-                    atomicAdd(&Td[k0], s * (double)(la * w));
-                    atomicAdd(&qd[k0], s * (double)(la * qs));
-                    atomicAdd(&Td[k1], s * (double)(lb * w));
-                    atomicAdd(&qd[k1], s * (double)(lb * qs));
-                    if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
-                        atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
-                        atomicAdd(&Tr[k1], -s * (double)(dx * w));
-                        atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
-                        atomicAdd(&qr[k1], -s * (double)(dx * qs));
-                    }
-                }
-            }
-        }
-        const R dL = AXIS_X ? (x_new - x) : oz * seg;
-        Lacc += dL;
-        hrun += dL;
-
-        // steps IVa / IVb.  Every lane evaluates the same straight-line code
-        // and keeps its own outcome through selects, so walls and relaxation
-        // events do not split the warp.
-        x = x_new;
-        if constexpr (POROUS) {
-            y += oy * seg;
-            z += oz * seg;
-        }
-        if constexpr (TRANSIENT) t = t_b;
-        ++n_seg;
-        const bool scat = !hit;
-        int wall = -1;
-        if constexpr (DIFF) {
-            wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
-        } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
-            wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
-            if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
-            wall = hit ? wall : -1;
-        }
-        const bool on_wall = wall >= 0;
-        const bool absorbed = wall == LE_MC_WALL_BLACK;
-        const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
-        const bool periodic = hit && !on_wall;
-        // Eq. 2 redraw (kept only on a relaxation event)
-        if constexpr (FUSED) {
-            const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
-            const uint4 e = s_fused[(uint32_t)(mm >> 32)];
-            const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
-            lam = scat ? lam_new : lam;
-        } else {
-            const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
-            const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
-            lam = scat ? lam_new : lam;
-            vg = scat ? vg_new : vg;
-        }
-        // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
-        const R u2 = M::uniform(r.z);
-        R sn, cs;
-        M::sincos_2pi(M::uniform(r.w), &sn, &cs);
-        const R mu = scat ? (R(2) * u2 - R(1)) : M::sqrt_(u2);
-        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
-        const R a = st * cs, b = st * sn;
-        R nox = a, noy = b, noz = mu;
-        if constexpr (GEOM != LE_MC_GEOM_BULK) {
-            // x walls: Lambertian about +-x, or mirror
-            const R wox = diffuse ? ((kind == HIT_XLO) ? mu : -mu) : -ox;
-            const R woy = diffuse ? a : oy;
-            const R woz = diffuse ? b : oz;
-            if constexpr (POROUS) {
-                // pore wall: normal from the axis to the hit point
-                const R ny = (y - half) / rad, nz = (z - half) / rad;
-                const R dn = oy * ny + oz * nz;
-                const R cox = diffuse ? a : ox;
-                const R coy = diffuse ? (mu * ny - b * nz) : (oy - R(2) * dn * ny);
-                const R coz = diffuse ? (mu * nz + b * ny) : (oz - R(2) * dn * nz);
-                const bool cyl = kind == HIT_CYL;
-                nox = scat ? a : (periodic ? ox : (cyl ? cox : wox));
-                noy = scat ? b : (periodic ? oy : (cyl ? coy : woy));
-                noz = scat ? mu : (periodic ? oz : (cyl ? coz : woz));
-                // periodic unit-cell face: re-insert on the opposite face
-                const bool yhi = periodic && kind == HIT_YHI, ylo = periodic && kind == HIT_YLO;
-                const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
-                y = yhi ? R(0) : (ylo ? pitch : y);
-                z = zhi ? R(0) : (zlo ? pitch : z);
-                cy += (int)yhi - (int)ylo;
-                cz += (int)zhi - (int)zlo;
-            } else {
-                nox = scat ? a : wox;
-                noy = scat ? b : woy;
-                noz = scat ? mu : woz;
-            }
-        }
-        ox = nox;
-        oy = noy;
-        oz = noz;
-        n_scat += scat ? 1u : 0u;
-        n_wall += on_wall ? 1u : 0u;
-        n_per += periodic ? 1u : 0u;
-        if (P.n_hj > 0 && scat) {
-            if (n_scat - 1u < (uint32_t)P.n_hj) {
-                atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
-                atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
-            }
-            hrun = R(0);
-        }
-        // step VI and truncation
-        if (absorbed) { fate = FATE_ABSORBED; alive = false; }
-        else if (TRANSIENT && t > (R)P.t_final) { fate = FATE_T_FINAL; alive = false; }
-        else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
-        else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
-        if (!alive) pending = true;
+        segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk));
     }
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
@@ -843,12 +948,13 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
         bool is_long = false;
         if (pid < N) {
             uint32_t id = batch ? pid : P.first + pid, inst = P.inst;
-            R cut = (R)P.lam_cut;
+            R cut = consts_of<R>(P).lam_cut;
             if (batch) {
                 const uint32_t b = batch_find(P.offsets, (uint32_t)P.n_instances, pid);
                 id = (uint32_t)(pid - P.offsets[b]);
                 inst = P.instances[b].inst_id;
-                cut = (R)P.instances[b].lam_cut;
+                if constexpr (sizeof(R) == 4) cut = P.instances[b].lam_cut32;
+                else cut = P.instances[b].lam_cut;
             }
             const uint4 r = philox4x32_10(make_uint4(0u, 0u, id, inst), args.rk);
             const uint2* table = P.src == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit;

@@ -43,7 +43,7 @@ def test_struct_layouts(P):
     for i, cls in enumerate((Bd.MaterialDesc, Bd.GeometryDesc, Bd.RunDesc, Bd.Tallies, Bd.Particle)):
         assert P.lib.le_mc_struct_size(i) == ctypes.sizeof(cls)
     assert Bd.PARTICLE_DTYPE.itemsize == ctypes.sizeof(Bd.Particle)
-    assert P.le_mc_abi_version() == 1
+    assert P.le_mc_abi_version() == 2
 
 
 def test_no_device_is_reported_not_faked(P):
@@ -116,6 +116,9 @@ def test_invalid_descriptors_rejected(P):
         {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.6},
         {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.2, "pore_wall": "black"},
         {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.2, "cells_y": 0},
+        {"kind": "planes", "L": 1.0, "wall_lo": "partial", "spec_lo": 1.5},
+        {"kind": "planes", "L": 1.0, "spec_hi": -0.1},
+        {"kind": "porous", "L": 1.0, "pitch": 1.0, "radius": 0.2, "pore_wall": "partial", "spec_pore": float("nan")},
     ]
     for g in bad_geo:
         with pytest.raises(P.LeMcError) as e:
@@ -123,7 +126,8 @@ def test_invalid_descriptors_rejected(P):
         assert e.value.status == 1, g
     h = P.le_mc_create_geometry(P.geometry_desc({"kind": "planes", "L": 1e-7}))
     P.le_mc_destroy_geometry(h)
-    bad_mat = [dict(W.GRAY_UNIT, tau=0.0), dict(W.SILICON_LIKE, n_bins=5000), dict(W.SILICON_LIKE, T_eq=-1.0)]
+    bad_mat = [dict(W.GRAY_UNIT, tau=0.0), dict(W.SILICON_LIKE, n_bins=5000), dict(W.SILICON_LIKE, T_eq=-1.0),
+               dict(W.GRAY_UNIT, scatter_g=1.0), dict(W.GRAY_UNIT, scatter_g=float("nan"))]
     for m in bad_mat:
         with pytest.raises(P.LeMcError) as e:
             P.le_mc_material_table(P.material_desc(m))

@@ -58,6 +58,22 @@ def _first_path_pin_ok(oracle, analytic, library):
             and r["segments"] == r["particles"])
 
 
+def _aniso_split_pin_ok(oracle, analytic, library):
+    g = 0.6
+    p = W.bulk(n_particles=300_000, material=dict(W.GRAY_UNIT, scatter_g=g), dTdz=-1.0)
+    p["run"]["n_hj"] = 4
+    r = oracle.run(p, library=library)
+    H, se = r["H"], r["H_se"]
+    return all(abs(H[j] / H[0] - g ** j) < 4.0 * abs(H[j] / H[0]) * np.hypot(se[j] / H[j], se[0] / H[0]) + 1e-12
+               for j in (1, 2))
+
+
+def _aniso_bulk_pin_ok(oracle, analytic, library):
+    mat = dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0, scatter_g=0.5)
+    r = oracle.run(W.bulk(n_particles=200_000, material=mat), library=library)
+    return abs(r["kappa"] - 105.0) < 4.0 * r["kappa_se"]
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -85,6 +101,11 @@ MUTATIONS = [
      "if (wall_type == ORC_WALL_SPECULAR) { s.ox = -s.ox; s.oz = -s.oz; }", _specular_pin_ok),
     ("first-free-path cap counts only relaxations", "n_scat + n_wall >= p->max_collisions",
      "n_scat >= p->max_collisions", _first_path_pin_ok),
+    ("anisotropic law about the z axis, not the incoming direction",
+     "hg_direction(p->scatter_g, u[2], u[3], in_x, in_y, in_z,", "hg_direction(p->scatter_g, u[2], u[3], 0.0, 0.0, 1.0,",
+     _aniso_split_pin_ok),
+    ("anisotropic cosine with the wrong sign", "double mu = (1.0 + g * g - q * q) / (2.0 * g);",
+     "double mu = -(1.0 + g * g - q * q) / (2.0 * g);", _aniso_bulk_pin_ok),
     ("density of states missing a factor k", "double dos = k * k / (2.0 * ORC_PI * ORC_PI * vg);",
      "double dos = k / (2.0 * ORC_PI * ORC_PI * vg);", _film_pin_ok),
 ]

@@ -160,12 +160,15 @@ def test_initial_condition_energy_and_modes(oracle, analytic):
     assert stats.chi2.sf(chi2, keep.sum()) > 1e-4
 
 
-@pytest.mark.parametrize("radius", [0.0, 30e-9])
-def test_uniform_initial_excess_stays_uniform(oracle, radius):
+@pytest.mark.parametrize("radius,g", [(0.0, 0.0), (30e-9, 0.0), (30e-9, 0.5)])
+def test_uniform_initial_excess_stays_uniform(oracle, radius, g):
     # A uniform, isotropic excess with mode weights C_b is the linearized
     # equilibrium shape: free flights, Eq. 2 redraws and Lambertian walls must
     # all preserve it, so the counts stay proportional to the solid volume.
-    p = W.porous_initial(n_particles=200_000, precision="fp64", radius=radius)
+    # A direction law that depends only on the angle to the incoming direction
+    # (anisotropic scattering, g != 0) maps an isotropic flux onto itself too.
+    p = W.porous_initial(n_particles=200_000, precision="fp64", radius=radius,
+                         material=dict(W.SILICON_LIKE, scatter_g=g))
     r = oracle.run(p)
     pv = uniform_equilibrium_pvalues(r["grid"], p["geometry"])
     assert min(pv) > 1e-4, pv

@@ -137,6 +137,64 @@ def test_first_collision_truncation(oracle, analytic):
     assert first["kappa"] - full["kappa"] > 5.0 * math.hypot(first["kappa_se"], full["kappa_se"])
 
 
+@pytest.mark.parametrize("g", [0.6, -0.4])
+def test_anisotropic_scattering_direction_law(oracle, g):
+    # Henyey-Greenstein about the incoming direction: unit vectors, cosine
+    # distributed by the law's CDF (mean g), azimuth about the incoming
+    # direction uniform in a frame built here independently
+    from scipy import stats
+    rng = np.random.default_rng(7)
+    n = 4000
+    inc = rng.normal(size=(n, 3))
+    inc /= np.linalg.norm(inc, axis=1)[:, None]
+    inc[0] = (0.0, 0.0, 1.0)
+    inc[1] = (0.0, 0.0, -1.0)
+    u = (rng.integers(0, 2 ** 32, size=(n, 2)).astype(np.float64) + 0.5) / 2.0 ** 32
+    out = np.array([oracle.scatter_direction(g, inc[i], u[i, 0], u[i, 1]) for i in range(n)])
+    assert np.allclose(np.linalg.norm(out, axis=1), 1.0, atol=1e-12)
+    mu = np.sum(out * inc, axis=1)
+    cdf = lambda m: (1 - g * g) / (2 * g) * ((1 + g * g - 2 * g * np.clip(m, -1, 1)) ** -0.5 - 1 / (1 + g))
+    assert stats.kstest(mu, cdf).pvalue > 1e-3
+    e = np.where(np.abs(inc[:, :1]) < 0.9, [[1.0, 0.0, 0.0]], [[0.0, 1.0, 0.0]])
+    t1 = np.cross(inc, e)
+    t1 /= np.linalg.norm(t1, axis=1)[:, None]
+    t2 = np.cross(inc, t1)
+    phi = np.arctan2(np.sum(out * t2, axis=1), np.sum(out * t1, axis=1))
+    assert stats.kstest(phi, stats.uniform(-np.pi, 2 * np.pi).cdf).pvalue > 1e-3
+
+
+def test_isotropic_law_is_g_zero(oracle):
+    # g = 0 keeps the paper's isotropic redraw: mu_z = 2u - 1, whatever the incoming direction
+    out = oracle.scatter_direction(0.0, [1.0, 0.0, 0.0], 0.8, 0.25)
+    assert out[2] == pytest.approx(0.6, abs=1e-15)
+
+
+def test_anisotropic_bulk_conductivity(oracle, analytic):
+    mat = dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0, scatter_g=0.5)
+    r = oracle.run(W.bulk(n_particles=400_000, material=mat))
+    assert _z(r["kappa"], 7.0 * 9.0 * 2.5 / 3.0 / 0.5, r["kappa_se"]) < 4.0
+    assert analytic.kappa_bulk_anisotropic(mat, 0.5) == pytest.approx(7.0 * 9.0 * 2.5 / 3.0 / 0.5, rel=1e-14)
+    si = dict(W.SILICON_LIKE, scatter_g=0.4)
+    pin = analytic.kappa_bulk_anisotropic(si, 0.4)
+    r = oracle.run(W.bulk(n_particles=2_000_000, material=si))
+    assert _z(r["kappa"], pin, r["kappa_se"]) < 4.0, (r["kappa"], pin)
+    assert abs(pin - analytic.kappa_bulk(W.SILICON_LIKE)) > 10 * r["kappa_se"]
+
+
+def test_anisotropic_flux_split_is_geometric(oracle):
+    # gray bulk: the mean flux between relaxation j and j + 1 is g^j times the first flight's
+    g = 0.6
+    mat = dict(W.GRAY_UNIT, scatter_g=g)
+    p = W.bulk(n_particles=1_000_000, material=mat, dTdz=-1.0)
+    p["run"]["n_hj"] = 8
+    r = oracle.run(p)
+    H, se = r["H"], r["H_se"]
+    for j in range(1, 7):
+        ratio = H[j] / H[0]
+        err = abs(ratio) * np.hypot(se[j] / H[j], se[0] / H[0])
+        assert abs(ratio - g ** j) < 4.0 * err + 1e-12, (j, ratio, g ** j, err)
+
+
 def test_bulk_conductivity(oracle, analytic):
     # no boundaries: kappa = (1/3) sum C v^2 tau exactly in expectation
     mat = dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0)
