@@ -268,16 +268,27 @@ LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out
  *   GRID             : int32[n_samples][grid_nz][grid_ny][grid_nx] signed
  *                      particle counts of Eq. 3 (times E_eff = energy per cell)
  *   PARTICLES        : le_mc_particle[n_particles] (record_particles = 1)
+ *   GRID_T           : double[n_samples][grid_nz][grid_ny][grid_nx]  energy
+ *                      temperature T - T_eq of each cell at each sample time
+ *                      (Eq. 3 count times E_eff / (C_tot V_cell), V_cell the
+ *                      whole cell, pores included)
+ *   GRID_TX          : double[n_samples][grid_nx]  T - T_eq averaged over the
+ *                      solid of each x slab (the pores run through the whole
+ *                      thickness, so every slab holds the same solid volume):
+ *                      the temperature history of a layer, as a
+ *                      thermoreflectance-like transient reads it
  * Errors: LE_MC_ERR_INVALID (array not produced by this run, capacity too
  * small), LE_MC_ERR_STATE, LE_MC_ERR_CUDA. */
 enum { LE_MC_ARRAY_T = 0, LE_MC_ARRAY_T_SE = 1, LE_MC_ARRAY_Q = 2, LE_MC_ARRAY_Q_SE = 3,
-       LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7 };
+       LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7,
+       LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9 };
 LE_MC_API le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity,
                               size_t* written);
 
 typedef struct {
     int8_t sign;        /* +1 / -1                                                 */
-    int8_t fate;        /* 0 absorbed, 1 scattering cap, 2 segment cap, 3 t_final   */
+    int8_t fate;        /* 0 absorbed, 1 scattering cap, 2 segment cap, 3 t_final,
+                         * 4 collision cap (max_collisions)                        */
     int16_t pad;
     uint32_t n_seg, n_scat, n_wall, n_periodic;
     uint32_t mode0;     /* emitted mode                                            */

@@ -91,7 +91,7 @@ struct le_mc_run_s {
     size_t off_sums = 0, off_counters = 0, off_queue = 0, off_flags = 0;
     size_t off_prof = 0, off_hj = 0, off_grid = 0, off_records = 0;
     size_t off_long_list = 0, off_long_bits = 0, off_long_count = 0;
-    uint32_t long_cap = 0;
+    uint32_t long_cap = 0, ext_cap = 0;
     size_t prof_len = 0, hj_len = 0, grid_len = 0;
     cudaEvent_t ev_start = nullptr, ev_mid = nullptr, ev_stop = nullptr;
     bool failed = false;
@@ -357,12 +357,13 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
                             (r.schedule == 1 || (r.schedule == 0 && r.n_particles >= 4096));
     if (long_first && r.n_particles > 0) {
         h->long_cap = (uint32_t)(r.n_particles < (1ull << 20) ? r.n_particles : (1ull << 20));
+        h->ext_cap = (uint32_t)(r.n_particles < kExtCap ? r.n_particles : kExtCap);
         off = align_up(off, 256);
-        h->off_long_list = off; off += (size_t)h->long_cap * sizeof(uint32_t);
+        h->off_long_list = off; off += (size_t)(h->ext_cap + h->long_cap) * sizeof(uint32_t);
         off = align_up(off, 256);
         h->off_long_bits = off; off += (size_t)((r.n_particles + 31) / 32) * sizeof(uint32_t);
         off = align_up(off, 256);
-        h->off_long_count = off; off += sizeof(unsigned long long);
+        h->off_long_count = off; off += 4 * sizeof(unsigned int);
     }
     h->dev_bytes = align_up(off, 256);
 
@@ -451,6 +452,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
         P.long_bits = reinterpret_cast<uint32_t*>(h->dev + h->off_long_bits);
         P.long_count = reinterpret_cast<unsigned int*>(h->dev + h->off_long_count);
         P.long_cap = h->long_cap;
+        P.ext_cap = h->ext_cap;
         P.lam_cut = r.long_mfp_cut > 0.0 ? r.long_mfp_cut : 32.0 * G.L;
     }
     fill_consts(P);
@@ -580,6 +582,14 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
         if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
         bytes = h->grid_len * sizeof(int32_t);
         break;
+    case LE_MC_ARRAY_GRID_T:
+        if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
+        bytes = h->grid_len * sizeof(double);
+        break;
+    case LE_MC_ARRAY_GRID_TX:
+        if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
+        bytes = (size_t)r.n_samples * r.grid_nx * sizeof(double);
+        break;
     case LE_MC_ARRAY_PARTICLES:
         if (!r.record_particles) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run kept no records");
         bytes = (size_t)r.n_particles * sizeof(le_mc_particle);
@@ -595,6 +605,18 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
     cudaError_t e = cudaSuccess;
     if (which == LE_MC_ARRAY_GRID) {
         e = cudaMemcpy(dst, h->dev + h->off_grid, bytes, cudaMemcpyDeviceToHost);
+    } else if (which == LE_MC_ARRAY_GRID_T || which == LE_MC_ARRAY_GRID_TX) {
+        std::vector<int32_t> counts(h->grid_len);
+        e = cudaMemcpy(counts.data(), h->dev + h->off_grid, h->grid_len * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            le_mc_tallies t;
+            memset(&t, 0, sizeof(t));
+            normalize(&h->geo->desc, &r, h->mat->sums, h->sums, h->counters, &t);
+            if (which == LE_MC_ARRAY_GRID_T)
+                finalize_grid_t(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), static_cast<double*>(dst));
+            else
+                finalize_grid_tx(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), static_cast<double*>(dst));
+        }
     } else if (which == LE_MC_ARRAY_PARTICLES) {
         e = cudaMemcpy(dst, h->dev + h->off_records, bytes, cudaMemcpyDeviceToHost);
     } else if (which <= LE_MC_ARRAY_Q_SE) {

@@ -48,7 +48,7 @@ struct le_mc_batch_s {
     size_t dev_bytes = 0, zero_off = 0, zero_bytes = 0;
     size_t off_inst = 0, off_offsets = 0, off_queue = 0, off_flags = 0, off_long_count = 0;
     size_t off_sums = 0, off_counters = 0, off_long_bits = 0, off_long_list = 0;
-    uint32_t long_cap = 0;
+    uint32_t long_cap = 0, ext_cap = 0;
     le_mc_launch_config cfg{};
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -124,6 +124,7 @@ KernelArgs make_args(le_mc_batch b)
         P.long_bits = reinterpret_cast<uint32_t*>(b->dev + b->off_long_bits);
         P.long_count = reinterpret_cast<unsigned int*>(b->dev + b->off_long_count);
         P.long_cap = b->long_cap;
+        P.ext_cap = b->ext_cap;
     }
     P.instances = reinterpret_cast<const BatchInstance*>(b->dev + b->off_inst);
     P.offsets = reinterpret_cast<const unsigned long long*>(b->dev + b->off_offsets);
@@ -237,6 +238,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     b->cfg.use_graph = 0;
     b->long_cap = (uint32_t)(total < (1ull << 20) ? total : (1ull << 20));
     if (runs[0].schedule == 2 || total == 0) b->long_cap = 0;
+    b->ext_cap = b->long_cap > 0 ? (uint32_t)(total < kExtCap ? total : kExtCap) : 0;
     size_t off = 0;
     b->off_inst = off; off += (size_t)n * sizeof(BatchInstance);
     off = align_up(off, 256);
@@ -245,7 +247,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     b->zero_off = off;
     b->off_queue = off; off += sizeof(unsigned long long);
     b->off_flags = off; off += sizeof(unsigned long long);
-    b->off_long_count = off; off += sizeof(unsigned long long);
+    b->off_long_count = off; off += 4 * sizeof(unsigned int);
     off = align_up(off, 256);
     b->off_sums = off; off += (size_t)n * 2 * sizeof(double);
     off = align_up(off, 256);
@@ -257,7 +259,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     }
     b->zero_bytes = off - b->zero_off;
     if (b->long_cap > 0) {
-        b->off_long_list = off; off += (size_t)b->long_cap * sizeof(uint32_t);
+        b->off_long_list = off; off += (size_t)(b->ext_cap + b->long_cap) * sizeof(uint32_t);
     }
     b->dev_bytes = align_up(off, 256);
     std::vector<BatchInstance> inst(n);

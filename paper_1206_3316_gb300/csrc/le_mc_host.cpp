@@ -422,6 +422,32 @@ void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, con
     }
 }
 
+void finalize_grid_t(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
+                     const int32_t* grid, double* T)
+{
+    const double Dy = g->pitch * g->cells_y, Dz = g->pitch * g->cells_z;
+    const double V_cell = (g->L / r->grid_nx) * (Dy / r->grid_ny) * (Dz / r->grid_nz);
+    const double f = E_eff / (ms.C_tot * V_cell);
+    const size_t n = (size_t)r->n_samples * r->grid_nz * r->grid_ny * r->grid_nx;
+    for (size_t i = 0; i < n; ++i) T[i] = f * (double)grid[i];
+}
+
+void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
+                      const int32_t* grid, double* Tx)
+{
+    const double pi = 3.141592653589793;
+    const double solid = (g->pitch * g->pitch - pi * g->radius * g->radius) * g->cells_y * g->cells_z;
+    const double f = E_eff / (ms.C_tot * solid * (g->L / r->grid_nx));
+    const size_t plane = (size_t)r->grid_nz * r->grid_ny;
+    for (int k = 0; k < r->n_samples; ++k)
+        for (int ix = 0; ix < r->grid_nx; ++ix) {
+            long long c = 0;
+            const int32_t* base = grid + (size_t)k * plane * r->grid_nx + ix;
+            for (size_t j = 0; j < plane; ++j) c += base[j * r->grid_nx];
+            Tx[(size_t)k * r->grid_nx + ix] = f * (double)c;
+        }
+}
+
 void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, double* H, double* H_se)
 {
     const double N = r->n_particles > 0 ? (double)r->n_particles : 1.0;

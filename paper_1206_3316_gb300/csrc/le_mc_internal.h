@@ -62,6 +62,12 @@ struct Consts {
 
 constexpr int kBatchSmemMax = 512;
 
+// Extreme particles: emission mean free path above kExtremeFactor times the
+// long-first cut (1024 film thicknesses by default), at most kExtCap per
+// launch (the rest join the ordinary long-first list).
+constexpr double kExtremeFactor = 32.0;
+constexpr uint32_t kExtCap = 4096;
+
 // Default launch shape of le_mc_run: 512 threads per block, refill idle
 // lanes once 4 of a warp's 32 are idle, claim queue positions 256 at a time
 // (a GB300 sweep of the 1e7-particle film found this fastest; results do not
@@ -115,10 +121,15 @@ struct TraceParams {
     // long-first schedule: ids of particles whose emission mode has a mean
     // free path above lam_cut, served before the natural order (which then
     // skips the ids flagged in long_bits); long_list == nullptr disables it
-    uint32_t* long_list;           // [long_cap]
+    // The first ext_cap entries of long_list hold the extreme particles
+    // (mean free path above kExtremeFactor lam_cut), each traced by a warp of
+    // its own whose idle lanes compute its random words; the ordinary
+    // long-first list follows.  long_count[0] counts the long-first list,
+    // [1] the extreme list, [2] is the claim counter of the extreme list.
+    uint32_t* long_list;           // [ext_cap + long_cap]
     uint32_t* long_bits;           // [ceil(n_particles / 32)]
-    unsigned int* long_count;      // [1]
-    uint32_t long_cap;
+    unsigned int* long_count;      // [3]
+    uint32_t long_cap, ext_cap;
     double lam_cut;
     // batch mode: queue positions 0 .. offsets[n_instances] - 1 run over the
     // concatenated instances; per-instance sums and counters
@@ -175,6 +186,12 @@ void normalize(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const Mate
 void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
                       const double* raw, double* T, double* T_se, double* q, double* q_se);
 void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, double* H, double* H_se);
+// Transient grids (Eq. 3): per-cell energy temperature, and the average over
+// the solid of each x slab; E_eff is the energy of one particle.
+void finalize_grid_t(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
+                     const int32_t* grid, double* T);
+void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
+                      const int32_t* grid, double* Tx);
 double flux_scale(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
                   double* P_out, double* Vref_out, double* Vsolid_out);
 

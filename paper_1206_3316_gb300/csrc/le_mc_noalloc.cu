@@ -49,11 +49,13 @@ using namespace lemc;
 
 namespace {
 
-// Scratch layout (bytes): [0, 8) queue head, [8, 12) flags, [12, 16) long-
-// first count, then the long-first list and the bitmap of listed particles.
+// Scratch layout (bytes): [0, 8) queue head, [8, 12) flags, [16, 28) the
+// long-first and extreme-list counts and the extreme-list claim counter, then
+// the extreme and long-first lists and the bitmap of listed particles.
 constexpr size_t kHeader = 256;
 constexpr uint32_t kListCap = 1u << 14;
-constexpr size_t kListBytes = (size_t)kListCap * sizeof(uint32_t);
+constexpr uint32_t kNoallocExtCap = 1024;
+constexpr size_t kListBytes = (size_t)(kNoallocExtCap + kListCap) * sizeof(uint32_t);
 constexpr size_t kBitsBytes = (size_t)(LE_MC_NOALLOC_MAX_PARTICLES / 32) * sizeof(uint32_t);
 constexpr size_t kScratchBytes = kHeader + kListBytes + kBitsBytes;
 
@@ -116,7 +118,7 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     // results start at zero; so do the queue head, flags, count and the bitmap words in use
     e = cudaMemsetAsync(d_sums, 0, 2 * sizeof(double), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_counters, 0, CNT_N * sizeof(unsigned long long), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(scratch, 0, 32, st);
     if (e == cudaSuccess && long_first) e = cudaMemsetAsync(scratch + kHeader + kListBytes, 0, (size_t)((N + 31) / 32) * 4, st);
     if (e != cudaSuccess) return set_cuda_error(e, "le_mc_run_noalloc: clear");
 
@@ -157,10 +159,11 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     P.queue = reinterpret_cast<unsigned int*>(scratch);
     P.flags = reinterpret_cast<unsigned int*>(scratch + 8);
     if (long_first) {
-        P.long_count = reinterpret_cast<unsigned int*>(scratch + 12);
+        P.long_count = reinterpret_cast<unsigned int*>(scratch + 16);
         P.long_list = reinterpret_cast<uint32_t*>(scratch + kHeader);
         P.long_bits = reinterpret_cast<uint32_t*>(scratch + kHeader + kListBytes);
         P.long_cap = kListCap;
+        P.ext_cap = kNoallocExtCap;
         P.lam_cut = r.long_mfp_cut > 0.0 ? r.long_mfp_cut : 32.0 * G.L;
     }
     P.refill_min = r.refill_min > 0 ? r.refill_min : 1;

@@ -380,7 +380,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     // (particle ids of the run, or the concatenated instances of a batch)
     // minus those already listed
     const unsigned long long n_pos = BATCH ? P.offsets[P.n_instances] : (unsigned long long)P.n_particles;
-    const uint32_t n_long = P.long_list ? min(*P.long_count, P.long_cap) : 0u;
+    const uint32_t n_long = P.long_list ? min(P.long_count[0], P.long_cap) : 0u;
+    const uint32_t n_ext = (P.long_list && P.ext_cap > 0) ? min(P.long_count[1], P.ext_cap) : 0u;
+    const uint32_t* long_region = P.long_list ? P.long_list + P.ext_cap : nullptr;
     const unsigned long long q_total = (unsigned long long)n_long + n_pos;
     const int refill_min = P.refill_min > 1 ? P.refill_min : 1;
     const Consts<R>& K = consts_of<R>(P);
@@ -422,6 +424,11 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     const unsigned long long chunk = P.chunk >= 32 ? (unsigned long long)P.chunk : 32ull;
     const unsigned long long long_claim = 32ull;
     unsigned long long w_next = 0, w_end = 0;
+    // Extreme particles (emission mean free path above kExtremeFactor times
+    // the long-first cut) can outlast the whole launch at a warp's fair share
+    // of issue slots; each is traced by a warp of its own in assisted rounds
+    // (phase A below), which roughly halves the instructions per segment on
+    // its critical path.
     uint32_t cur_b = 0xFFFFFFFFu;  // batch instance the lane accumulators belong to
 
     // batch mode: move the lane accumulators to instance b's totals
@@ -697,50 +704,172 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (!alive) pending = true;
     };
 
+    // Rounds of precomputed random words, for a warp with few busy lanes
+    // (an extreme particle at the start of the launch, the last particles at
+    // its end): such a warp runs at the latency of one lane, so its idle lanes
+    // compute the busy lanes' next random words (the counters are known in
+    // advance) into the emission buffer's storage, and the busy lanes trace
+    // a round of segments without Philox on their critical path.  Each
+    // segment uses the same words as otherwise.
+    // totals of a finished particle (step V, Eq. 4) into the lane accumulators
+    auto finish = [&]() {
+            if constexpr (BATCH) {
+                if (bidx != cur_b) {
+                    flush_lane(cur_b);
+                    cur_b = bidx;
+                }
+            }
+            const R sL = (R)sign * Lacc;
+            acc_sL.add(sL);
+            acc_sL2.add(sL * sL);
+            c_part += 1;
+            c_seg += n_seg;
+            c_scat += n_scat;
+            c_wall += n_wall;
+            c_per += n_per;
+            c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
+            c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
+            if (P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
+                atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
+                atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
+            }
+            if (P.records) {
+                le_mc_particle rec;
+                rec.sign = (int8_t)sign;
+                rec.fate = (int8_t)fate;
+                rec.pad = 0;
+                rec.n_seg = n_seg;
+                rec.n_scat = n_scat;
+                rec.n_wall = n_wall;
+                rec.n_periodic = n_per;
+                rec.mode0 = mode0;
+                rec.L_axis = (double)Lacc;
+                rec.x0 = (double)x0;
+                rec.t0 = (double)t0;
+                P.records[pid - P.first] = rec;
+            }
+            pending = false;
+    };
+
+    auto assisted = [&]() {
+        uint4* const words = reinterpret_cast<uint4*>(&buf);
+        for (;;) {
+            const unsigned m = __ballot_sync(FULL, alive);
+            if (m == 0) break;
+            const int n_a = __popc(m);
+            const int steps = 32 / n_a;
+            const int a = lane % n_a, s = lane / n_a;
+            unsigned mm = m;
+            for (int i = 0; i < a; ++i) mm &= mm - 1u;
+            const int src = __ffs((int)mm) - 1;
+            const uint32_t seg_a = __shfl_sync(FULL, n_seg, src);
+            const uint32_t pid_a = __shfl_sync(FULL, pid, src);
+            const uint32_t inst_a = __shfl_sync(FULL, instw, src);
+            if (s < steps) words[s * n_a + a] = philox4x32_10(make_uint4(seg_a + 1u + (uint32_t)s, 0u, pid_a, inst_a), rk);
+            __syncwarp();
+            if (alive) {
+                const int my = __popc(m & lanemask_lt);
+                for (int k = 0; k < steps && alive; ++k) segment(words[k * n_a + my]);
+            }
+            __syncwarp();
+            if (pending) finish();
+        }
+    };
+
+    // Phase A: extreme particles, one per otherwise empty warp, claimed first.
+    if (n_ext > 0) {
+        for (;;) {
+            unsigned int e = 0;
+            if (lane == 0) e = atomicAdd(P.long_count + 2, 1u);
+            e = __shfl_sync(FULL, e, 0);
+            if (e >= n_ext) break;
+            if (lane == 0) {
+                const uint32_t epos = P.long_list[e];
+                uint32_t id = epos, eb = 0;
+                EmitCtx<R> ctx;
+                if constexpr (BATCH) {
+                    eb = batch_find(P.offsets, (uint32_t)P.n_instances, epos);
+                    id = (uint32_t)(epos - P.offsets[eb]);
+                    ctx = batch_ctx<R>(P.instances[eb]);
+                } else {
+                    id = P.first + epos;
+                    ctx = run_ctx<R>(P);
+                }
+                R ex, ey, ez, eox, eoy, eoz, et;
+                uint32_t em, ecy, ecz;
+                int es;
+                if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex,
+                                                 ey, ez, eox, eoy, eoz, et, em, es, ecy, ecz))
+                    flags |= FLAG_REJECTION_EXHAUSTED;
+                const int slot = 0;
+                buf.x[slot] = ex;
+                buf.ox[slot] = eox;
+                buf.oy[slot] = eoy;
+                buf.oz[slot] = eoz;
+                buf.pid[slot] = id;
+                buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
+                if constexpr (POROUS) {
+                    buf.y.v[slot] = ey;
+                    buf.z.v[slot] = ez;
+                    buf.cell.v[slot] = ecy | (ecz << 16);
+                }
+                if constexpr (SRC == LE_MC_SRC_PULSE) buf.t.v[slot] = et;
+                if constexpr (BATCH) buf.inst.v[slot] = eb;
+                {  // lane 0 starts it from the buffer entry, as a refill would
+                    x = buf.x[slot];
+                    ox = buf.ox[slot];
+                    oy = buf.oy[slot];
+                    oz = buf.oz[slot];
+                    pid = buf.pid[slot];
+                    const uint32_t ms = buf.mode_sign[slot];
+                    if constexpr (POROUS) {
+                        y = buf.y.v[slot];
+                        z = buf.z.v[slot];
+                        const uint32_t cell = buf.cell.v[slot];
+                        cy = (int)(cell & 0xFFFFu);
+                        cz = (int)(cell >> 16);
+                    }
+                    if constexpr (SRC == LE_MC_SRC_PULSE) t = buf.t.v[slot];
+                    if constexpr (SRC == LE_MC_SRC_INITIAL) t = R(0);
+                    if constexpr (BATCH) {
+                        bidx = buf.inst.v[slot];
+                        const BatchInstance& bi = P.instances[bidx];
+                        if constexpr (sizeof(R) == 4) Lp = bi.L32;
+                        else Lp = bi.L;
+                        instw = bi.inst_id;
+                    }
+                    mode0 = ms & 0x7FFFFFFFu;
+                    sign = (ms >> 31) ? -1 : 1;
+                    if constexpr (FUSED) {
+                        lam = __uint_as_float(s_fused[mode0].z);
+                    } else {
+                        lam = s_props[2 * mode0];
+                        vg = s_props[2 * mode0 + 1];
+                    }
+                    x0 = x;
+                    t0 = t;
+                    Lacc = 0;
+                    hrun = 0;
+                    n_seg = n_scat = n_wall = n_per = 0;
+                    alive = true;
+                }
+
+            }
+            __syncwarp();
+            assisted();
+        }
+    }
+
+    // Phase B: the queue (long-first list, then the natural order).
     for (;;) {
         const unsigned dead = __ballot_sync(FULL, !alive);
         // refill once refill_min lanes are idle (or at once near the end)
         if (dead && (dead == FULL || qdone || __popc(dead) >= refill_min)) {
-            if (pending) {  // totals of the finished particle (step V, Eq. 4)
-                if constexpr (BATCH) {
-                    if (bidx != cur_b) {
-                        flush_lane(cur_b);
-                        cur_b = bidx;
-                    }
-                }
-                const R sL = (R)sign * Lacc;
-                acc_sL.add(sL);
-                acc_sL2.add(sL * sL);
-                c_part += 1;
-                c_seg += n_seg;
-                c_scat += n_scat;
-                c_wall += n_wall;
-                c_per += n_per;
-                c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
-                c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
-                if (P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
-                    atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
-                    atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
-                }
-                if (P.records) {
-                    le_mc_particle rec;
-                    rec.sign = (int8_t)sign;
-                    rec.fate = (int8_t)fate;
-                    rec.pad = 0;
-                    rec.n_seg = n_seg;
-                    rec.n_scat = n_scat;
-                    rec.n_wall = n_wall;
-                    rec.n_periodic = n_per;
-                    rec.mode0 = mode0;
-                    rec.L_axis = (double)Lacc;
-                    rec.x0 = (double)x0;
-                    rec.t0 = (double)t0;
-                    P.records[pid - P.first] = rec;
-                }
-                pending = false;
-            }
+            if (pending) finish();
             const int need = __popc(dead);
             while (cnt < need && !qdone) {
+                uint32_t pos = 0;
+                bool valid = false;
                 // step I for the next 32 claimed queue positions, whole warp
                 if (w_next >= w_end) {
                     unsigned long long base = 0;
@@ -758,12 +887,10 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
                 const unsigned long long q_end = w_end;
                 w_next = min(w_next + 32ull, w_end);
                 if (w_next >= w_end && w_end >= q_total) qdone = true;
-                uint32_t pos = 0;
-                bool valid = false;
                 if (q >= q_end) {
                     valid = false;
                 } else if (q < n_long) {
-                    pos = P.long_list[q];
+                    pos = long_region[q];
                     valid = true;
                 } else {
                     pos = (uint32_t)(q - n_long);
@@ -851,38 +978,14 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             __syncwarp();
             if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
         }
-        // Lifetime tail: with the queue exhausted and the buffer empty, a warp
-        // left with a few long trajectories runs at the latency of one lane.
-        // Its idle lanes then compute the random words of the busy lanes' next
-        // segments (the counters are known in advance) into the emission
-        // buffer's storage, so the busy lanes trace without Philox on their
-        // critical path.  Each segment uses the same words as otherwise.
-        if (qdone && cnt == 0) {
-            const unsigned m = __ballot_sync(FULL, alive);
-            const int n_a = __popc(m);
-            if (n_a > 0 && n_a <= kTailLanes) {
-                const int steps = 32 / n_a;
-                const int a = lane % n_a, s = lane / n_a;
-                unsigned mm = m;
-                for (int i = 0; i < a; ++i) mm &= mm - 1u;
-                const int src = __ffs((int)mm) - 1;
-                const uint32_t seg_a = __shfl_sync(FULL, n_seg, src);
-                const uint32_t pid_a = __shfl_sync(FULL, pid, src);
-                const uint32_t inst_a = __shfl_sync(FULL, instw, src);
-                uint4* words = reinterpret_cast<uint4*>(&buf);
-                if (s < steps) words[s * n_a + a] = philox4x32_10(make_uint4(seg_a + 1u + (uint32_t)s, 0u, pid_a, inst_a), rk);
-                __syncwarp();
-                if (alive) {
-                    const int my_a = __popc(m & lanemask_lt);
-                    for (int k = 0; k < steps && alive; ++k) segment(words[k * n_a + my_a]);
-                }
-                __syncwarp();
-                continue;
-            }
-        }
+        // queue exhausted and buffer empty: a warp down to a few busy lanes
+        // hands them to the assisted rounds (phase C)
+        if (qdone && cnt == 0 && __popc(__ballot_sync(FULL, alive)) <= kTailLanes) break;
         if (!alive) continue;
         segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk));
     }
+    // Phase C: the lifetime tail of this warp.
+    assisted();
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
     if constexpr (BATCH) {
@@ -945,7 +1048,7 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
     const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
     for (uint32_t w0 = first; w0 < N; w0 += stride) {
         const uint32_t pid = w0 + (uint32_t)lane;
-        bool is_long = false;
+        bool is_long = false, is_ext = false;
         if (pid < N) {
             uint32_t id = batch ? pid : P.first + pid, inst = P.inst;
             R cut = consts_of<R>(P).lam_cut;
@@ -962,16 +1065,34 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
             R lam, vg;
             load_props<R>(P.props, mode, lam, vg);
             is_long = lam > cut;
+            is_ext = lam > cut * R(kExtremeFactor);
         }
-        const unsigned m = __ballot_sync(FULL, is_long);
+        // extreme particles first (while the extreme list has room)
+        bool listed = false;
+        const unsigned mx = __ballot_sync(FULL, is_ext);
+        if (mx && P.ext_cap > 0) {
+            unsigned base = 0;
+            if (lane == 0) base = atomicAdd(P.long_count + 1, (unsigned)__popc(mx));
+            base = __shfl_sync(FULL, base, 0);
+            if (is_ext) {
+                const unsigned slot = base + (unsigned)__popc(mx & lanemask_lt);
+                if (slot < P.ext_cap) {
+                    P.long_list[slot] = pid;
+                    atomicOr(&P.long_bits[pid >> 5], 1u << (pid & 31u));
+                    listed = true;
+                }
+            }
+        }
+        const bool to_long = is_long && !listed;
+        const unsigned m = __ballot_sync(FULL, to_long);
         if (m) {
             unsigned base = 0;
             if (lane == 0) base = atomicAdd(P.long_count, (unsigned)__popc(m));
             base = __shfl_sync(FULL, base, 0);
-            if (is_long) {
+            if (to_long) {
                 const unsigned slot = base + (unsigned)__popc(m & lanemask_lt);
                 if (slot < P.long_cap) {
-                    P.long_list[slot] = pid;
+                    P.long_list[P.ext_cap + slot] = pid;
                     atomicOr(&P.long_bits[pid >> 5], 1u << (pid & 31u));
                 }
             }

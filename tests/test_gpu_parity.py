@@ -308,3 +308,46 @@ def test_first_event_truncation_exact_for_film_but_not_for_pores(P, analytic):
           f"first event only {first['kappa']:.3f} +- {first['kappa_se']:.3f} "
           f"({100 * (first['kappa'] / full['kappa'] - 1):+.0f} %)")
     assert abs(first["kappa"] - full["kappa"]) > 5.0 * np.hypot(first["kappa_se"], full["kappa_se"])
+
+
+def test_ttr_like_layer_temperature(P, oracle):
+    # Thermoreflectance-like transient: a 30 nm top layer of a 300 nm film
+    # starts 1 K above T_eq; the solid-slab temperature history T_x(t, x)
+    n = 2_000_000
+    p = W.ttr_film(n_particles=n)
+    g = P.simulate(p)
+    L, nx = 300e-9, 30
+    area = p["geometry"]["pitch"] ** 2
+    f_g = g["E_eff"] / (g["C_tot"] * area * L / nx)
+    Tx = g["T_x"]
+    np.testing.assert_allclose(Tx, g["grid"].reshape(Tx.shape) * f_g, rtol=1e-12)
+    # the layer's energy is conserved at every sample (adiabatic faces)
+    np.testing.assert_allclose(Tx.sum(axis=1) * L / nx, 30e-9, rtol=1e-9)
+    # against the FP64 oracle, slab by slab and time by time (multinomial counts)
+    o = oracle.run(W.ttr_film(n_particles=200_000, precision="fp64"))
+    f_o = o["E_eff"] / (o["C_tot"] * area * L / nx)
+    To = o["grid"].reshape(Tx.shape) * f_o
+    sig = np.sqrt(np.abs(Tx) * f_g + np.abs(To) * f_o)
+    keep = o["grid"].reshape(Tx.shape) >= 20
+    z = np.abs(Tx - To)[keep] / sig[keep]
+    assert z.max() < 5.0, z.max()
+    # the top slab cools and the film tends to dT * 30 nm / 300 nm = 0.1 K
+    assert Tx[0, -1] > 0.5 and Tx[-1, -1] < 0.3 and abs(Tx[-1].mean() - 0.1) < 1e-9
+
+
+def test_grid_temperature_readback(P):
+    p = W.porous_pulse(n_particles=100_000, grid=(4, 6, 6), n_samples=10)
+    mat = P.le_mc_create_material(P.material_desc(p["material"]))
+    geo = P.le_mc_create_geometry(P.geometry_desc(p["geometry"]))
+    h = P.le_mc_run(mat, geo, P.run_desc(p["source"], p["run"]), None)
+    try:
+        t = P.le_mc_read_tallies(h)
+        counts = P.le_mc_read_array(h, "grid")
+        T = P.le_mc_read_array(h, "grid_T")
+        g = p["geometry"]
+        V = (g["L"] / 4) * (g["pitch"] * 6 / 6) * (g["pitch"] * 6 / 6)
+        np.testing.assert_allclose(T, counts * t["E_eff"] / (t["C_tot"] * V), rtol=1e-12)
+    finally:
+        P.le_mc_destroy_run(h)
+        P.le_mc_destroy_geometry(geo)
+        P.le_mc_destroy_material(mat)

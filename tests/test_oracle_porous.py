@@ -172,3 +172,19 @@ def test_uniform_initial_excess_stays_uniform(oracle, radius, g):
     r = oracle.run(p)
     pv = uniform_equilibrium_pvalues(r["grid"], p["geometry"])
     assert min(pv) > 1e-4, pv
+
+
+def test_ttr_layer_energy_is_conserved(oracle):
+    # Thermoreflectance-like transient: the heated layer's energy only spreads
+    # through the film (adiabatic faces), so every sample holds all particles,
+    # and the solid-slab temperatures integrate to dT times the layer thickness.
+    p = W.ttr_film(n_particles=50_000, precision="fp64", n_samples=40)
+    r = oracle.run(p)
+    counts = r["grid"].reshape(40, -1)  # nz = ny = 1: one count per x slab
+    assert np.all(counts.sum(axis=1) == 50_000)
+    L, nx = 300e-9, 30
+    area = p["geometry"]["pitch"] ** 2
+    Tx = counts * r["E_eff"] / (r["C_tot"] * area * L / nx)
+    assert np.allclose(Tx.sum(axis=1) * L / nx, 1.0 * 30e-9, rtol=1e-12)
+    # at the first sample (25 ps) the heat is still mostly in the top 60 nm
+    assert Tx[0, -6:].sum() * L / nx > 0.8 * 30e-9

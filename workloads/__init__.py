@@ -172,6 +172,20 @@ def porous_initial(n_particles=1_000_000, seed=0x5EED_0000_0007, precision="fp32
     }
 
 
+def ttr_film(n_particles=2_000_000, seed=0x5EED_0000_0008, precision="fp32", dT=1.0, thickness=300e-9,
+             heated=30e-9, nx=30, n_samples=100, sample_dt=50e-12, material=None, max_events=1 << 20):
+    """Thermoreflectance-like transient on a single material: a film with
+    adiabatic diffuse faces whose top layer (the last ``heated`` metres below
+    x = thickness) starts dT above T_eq; the temperature of every x slab of
+    the film is sampled at (k + 1/2) sample_dt.  (The paper's Al-on-Si
+    experiment needs material data that is not available; one synthetic
+    material stands in.)  A porous geometry with no pores is a film."""
+    return porous_initial(n_particles=n_particles, seed=seed, precision=precision, dT=dT,
+                          x_range=(thickness - heated, thickness), grid=(nx, 1, 1), n_samples=n_samples,
+                          sample_dt=sample_dt, t_final=(n_samples + 1) * sample_dt, cells=(1, 1),
+                          material=material, thickness=thickness, radius=0.0, max_events=max_events)
+
+
 def batched_films(n_instances=256, seed=2012, n_min=1e4, n_max=1e7, L_min=10e-9, L_max=100e-6,
                   precision="fp32"):
     """Many silicon-like films of uneven size: thickness log-uniform in
