@@ -61,7 +61,7 @@ LANES_PER_SM = 128  # FP32/INT32 lanes issuing one operation per clock
 
 def _sha_kernel_sources():
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "device_math.cuh"):
+    for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h"):
         with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

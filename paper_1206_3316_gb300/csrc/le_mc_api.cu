@@ -357,7 +357,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
                             (r.schedule == 1 || (r.schedule == 0 && r.n_particles >= 4096));
     if (long_first && r.n_particles > 0) {
         h->long_cap = (uint32_t)(r.n_particles < (1ull << 20) ? r.n_particles : (1ull << 20));
-        h->ext_cap = (uint32_t)(r.n_particles < kExtCap ? r.n_particles : kExtCap);
+        h->ext_cap = r.n_particles > kExtMaxParticles ? 0u : (uint32_t)(r.n_particles < kExtCap ? r.n_particles : kExtCap);
         off = align_up(off, 256);
         h->off_long_list = off; off += (size_t)(h->ext_cap + h->long_cap) * sizeof(uint32_t);
         off = align_up(off, 256);

@@ -238,7 +238,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     b->cfg.use_graph = 0;
     b->long_cap = (uint32_t)(total < (1ull << 20) ? total : (1ull << 20));
     if (runs[0].schedule == 2 || total == 0) b->long_cap = 0;
-    b->ext_cap = b->long_cap > 0 ? (uint32_t)(total < kExtCap ? total : kExtCap) : 0;
+    b->ext_cap = (b->long_cap > 0 && total <= kExtMaxParticles) ? (uint32_t)(total < kExtCap ? total : kExtCap) : 0;
     size_t off = 0;
     b->off_inst = off; off += (size_t)n * sizeof(BatchInstance);
     off = align_up(off, 256);

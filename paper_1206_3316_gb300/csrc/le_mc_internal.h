@@ -64,9 +64,14 @@ constexpr int kBatchSmemMax = 512;
 
 // Extreme particles: emission mean free path above kExtremeFactor times the
 // long-first cut (1024 film thicknesses by default), at most kExtCap per
-// launch (the rest join the ordinary long-first list).
+// launch (the rest join the ordinary long-first list).  They only matter in
+// launches short enough for one 4096-segment history to be near-critical
+// (~1e7 particles of ~50 segments take about as long on a GB300), so
+// launches of more than kExtMaxParticles particles keep none: there the
+// dedicated warps would cost lanes and save nothing.
 constexpr double kExtremeFactor = 32.0;
-constexpr uint32_t kExtCap = 4096;
+constexpr uint32_t kExtCap = 512;
+constexpr unsigned long long kExtMaxParticles = 1ull << 25;
 
 // Default launch shape of le_mc_run: 512 threads per block, refill idle
 // lanes once 4 of a warp's 32 are idle, claim queue positions 256 at a time

@@ -54,7 +54,7 @@ namespace {
 // the extreme and long-first lists and the bitmap of listed particles.
 constexpr size_t kHeader = 256;
 constexpr uint32_t kListCap = 1u << 14;
-constexpr uint32_t kNoallocExtCap = 1024;
+constexpr uint32_t kNoallocExtCap = kExtCap;
 constexpr size_t kListBytes = (size_t)(kNoallocExtCap + kListCap) * sizeof(uint32_t);
 constexpr size_t kBitsBytes = (size_t)(LE_MC_NOALLOC_MAX_PARTICLES / 32) * sizeof(uint32_t);
 constexpr size_t kScratchBytes = kHeader + kListBytes + kBitsBytes;

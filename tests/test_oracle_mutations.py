@@ -74,6 +74,13 @@ def _aniso_bulk_pin_ok(oracle, analytic, library):
     return abs(r["kappa"] - 105.0) < 4.0 * r["kappa_se"]
 
 
+def _flight_shape_pin_ok(oracle, analytic, library):
+    lam, n = 7.5, 400_000
+    r = oracle.run(W.bulk(n_particles=n, material=dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0), max_events=1),
+                   library=library)
+    return abs(r["sum_sL2"] / n - lam ** 2) < 4.0 * np.sqrt(7.0 / n) * lam ** 2
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -106,6 +113,8 @@ MUTATIONS = [
      _aniso_split_pin_ok),
     ("anisotropic cosine with the wrong sign", "double mu = (1.0 + g * g - q * q) / (2.0 * g);",
      "double mu = -(1.0 + g * g - q * q) / (2.0 * g);", _aniso_bulk_pin_ok),
+    ("flight length uniform on [0, 2 Lambda] (right mean, wrong law)", "double dist = m->Lambda[s.mode] * -log(u[0]);",
+     "double dist = m->Lambda[s.mode] * 2.0 * u[0];", _flight_shape_pin_ok),
     ("density of states missing a factor k", "double dos = k * k / (2.0 * ORC_PI * ORC_PI * vg);",
      "double dos = k / (2.0 * ORC_PI * ORC_PI * vg);", _film_pin_ok),
 ]

@@ -195,6 +195,17 @@ def test_anisotropic_flux_split_is_geometric(oracle):
         assert abs(ratio - g ** j) < 4.0 * err + 1e-12, (j, ratio, g ** j, err)
 
 
+def test_bulk_first_flight_second_moment(oracle):
+    # First flight only (max_events = 1) in a gray bulk: s L_z = l mu with
+    # l ~ Exp(Lambda) and mu from the |mu| law, so E[(s L_z)^2] = 2 Lambda^2 / 2
+    # = Lambda^2 and Var((s L_z)^2) = E[l^4] E[mu^4] - Lambda^4 = 7 Lambda^4.
+    # The conductivity pins only see the mean flight; this one sees its shape.
+    lam, n = 2.5 * 3.0, 1_000_000
+    r = oracle.run(W.bulk(n_particles=n, material=dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0), max_events=1))
+    m2 = r["sum_sL2"] / n
+    assert abs(m2 - lam ** 2) < 4.0 * math.sqrt(7.0 / n) * lam ** 2, (m2, lam ** 2)
+
+
 def test_bulk_conductivity(oracle, analytic):
     # no boundaries: kappa = (1/3) sum C v^2 tau exactly in expectation
     mat = dict(W.GRAY_UNIT, tau=2.5, v=3.0, C=7.0)
