@@ -174,6 +174,18 @@ void fill_consts(TraceParams& P)
     P.sign_hi = P.dT_hi >= 0.0 ? 1 : -1;
     P.init_sign = P.init_dT >= 0.0 ? 1 : -1;
     P.aniso = P.scatter_g != 0.0 ? 1 : 0;
+    // Without periodic faces (PLANES, BULK) every segment ends in a collision
+    // (a relaxation or a wall hit), so a collision cap is a segment cap: fold
+    // it into max_events and report the collision fate when it is the one
+    // that binds (the kernel then needs no per-segment check for it).
+    P.events_fate = FATE_MAX_EVENTS;
+    if (P.max_collisions > 0u && P.geom != LE_MC_GEOM_POROUS) {
+        if (P.max_collisions <= P.max_events) {
+            P.max_events = P.max_collisions;
+            P.events_fate = FATE_MAX_COLLISIONS;
+        }
+        P.max_collisions = 0u;
+    }
     fill_one<float>(P, P.c32);
     fill_one<double>(P, P.c64);
 }

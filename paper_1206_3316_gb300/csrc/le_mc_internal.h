@@ -101,6 +101,7 @@ struct TraceParams {
     double init_dT, init_x_lo, init_x_hi;
     int32_t sign_lo, sign_hi, init_sign;  // WALLS: sign of dT_lo, dT_hi; INITIAL: of init_dT
     int32_t aniso;                        // scatter_g != 0
+    int32_t events_fate;                  // fate reported when max_events ends a particle
     Consts<float> c32;                    // filled by fill_consts from the doubles
     Consts<double> c64;
     // run

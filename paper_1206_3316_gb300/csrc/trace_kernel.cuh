@@ -61,10 +61,6 @@ struct alignas(16) EmitBuffer {
     Slots<uint32_t, INST ? kBufSlots : 0> inst;
 };
 
-// warps with at most this many busy lanes at the end get their random words
-// precomputed by the idle lanes (see the lifetime-tail branch of trace_kernel)
-constexpr int kTailLanes = 8;
-
 template <typename R, int GEOM, int SRC, bool BATCH = false>
 using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE, BATCH>;
 
@@ -318,7 +314,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     using M = DMath<R>;
     using Buf = BufferOf<R, GEOM, SRC, BATCH>;
     static_assert(sizeof(Buf) >= 32 * sizeof(uint4) && sizeof(Buf) % 16 == 0,
-                  "the lifetime-tail branch keeps 32 random words in a warp's emission buffer");
+                  "assisted rounds keep 32 random words in a warp's emission buffer");
     constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
     constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
@@ -392,6 +388,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
     // anisotropic relaxation-event direction law (kernel-uniform)
     const bool aniso = !DIFF && P.aniso != 0;
     const R hg = K.g;
+    // collision cap (first free path): needs its own check only where periodic
+    // faces end segments too; elsewhere the host folds it into max_events
+    const bool col_cap = POROUS && P.max_collisions > 0u;
     // partially specular walls present (kernel-uniform)
     const bool any_partial = !DIFF && (P.wall_lo == LE_MC_WALL_PARTIAL || P.wall_hi == LE_MC_WALL_PARTIAL ||
                                        (POROUS && P.pore_wall == LE_MC_WALL_PARTIAL));
@@ -699,17 +698,16 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (absorbed) { fate = FATE_ABSORBED; alive = false; }
             else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
             else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
-            else if (P.max_collisions > 0u && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
-            else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
+            else if (col_cap && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
+            else if (n_seg >= P.max_events) { fate = P.events_fate; alive = false; }
             if (!alive) pending = true;
     };
 
-    // Rounds of precomputed random words, for a warp with few busy lanes
-    // (an extreme particle at the start of the launch, the last particles at
-    // its end): such a warp runs at the latency of one lane, so its idle lanes
-    // compute the busy lanes' next random words (the counters are known in
-    // advance) into the emission buffer's storage, and the busy lanes trace
-    // a round of segments without Philox on their critical path.  Each
+    // Rounds of precomputed random words, for a warp tracing one extreme
+    // particle (phase A): such a warp runs at the latency of one lane, so its
+    // idle lanes compute the particle's next random words (the counters are
+    // known in advance) into the emission buffer's storage, and the particle
+    // traces a round of segments without Philox on its critical path.  Each
     // segment uses the same words as otherwise.
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
     auto finish = [&]() {
@@ -978,14 +976,9 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             __syncwarp();
             if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
         }
-        // queue exhausted and buffer empty: a warp down to a few busy lanes
-        // hands them to the assisted rounds (phase C)
-        if (qdone && cnt == 0 && __popc(__ballot_sync(FULL, alive)) <= kTailLanes) break;
         if (!alive) continue;
         segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk));
     }
-    // Phase C: the lifetime tail of this warp.
-    assisted();
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
     if constexpr (BATCH) {

@@ -84,3 +84,21 @@ def test_invalid_specularity_rejected(P):
     prob = W.silicon_film(n_particles=10, specularity=1.5)
     with pytest.raises(Exception):
         P.simulate(prob)
+
+
+def test_collision_cap_per_particle(P, oracle):
+    # the cap is folded into the segment cap for films (every segment ends in a
+    # collision there) and checked per segment in pored films: both report the
+    # collision-cap fate exactly where the oracle does
+    film = W.silicon_film(n_particles=3000, thickness=0.7, material=dict(W.GRAY_UNIT), precision="fp64",
+                          max_scatter=12, max_events=200, dTdz=-1.0)
+    pores = W.porous_film(n_particles=3000, precision="fp64", material=dict(W.GRAY_UNIT, tau=2e-8, v=1.0),
+                          max_events=300, max_scatter=20)
+    for prob, atol in ((film, 1e-12), (pores, 2e-8 * 1e-6)):
+        for cap in (1, 3, 250):
+            p = W.with_run(prob, max_collisions=cap)
+            g = P.simulate(p, record_particles=True)
+            o = oracle.run(p, record_particles=True)
+            _same_particles(g["particles_rec"], o["particles_rec"], atol=atol)
+            if cap < 10:
+                assert 4 in set(np.unique(g["particles_rec"]["fate"]).tolist()), cap
