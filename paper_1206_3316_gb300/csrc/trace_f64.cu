@@ -10,7 +10,7 @@ namespace {
 template <int G, int S, bool PR, bool DF = false>
 cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem, cudaStream_t st)
 {
-    auto k = trace_kernel<double, G, S, PR, false, DF>;
+    auto k = trace_entry<double, G, S, PR, false, DF>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (blocks <= 0) return cudaSuccess;
@@ -21,7 +21,7 @@ cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem
 template <int G, int S, bool PR, bool DF = false>
 cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
 {
-    auto k = trace_kernel<double, G, S, PR, false, DF>;
+    auto k = trace_entry<double, G, S, PR, false, DF>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);

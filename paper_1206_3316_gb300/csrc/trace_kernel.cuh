@@ -308,8 +308,8 @@ __host__ __device__ inline size_t table_bytes(int n_modes)
 // events are isotropic (the paper's base case), so the wall law needs no
 // per-wall lookup and no specular, absorbing or partial branch, and the
 // direction law no anisotropic branch.
-template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
-__global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH, bool DIFF>
+__device__ __forceinline__ void trace_body(const KernelArgs& args)
 {
     using M = DMath<R>;
     using Buf = BufferOf<R, GEOM, SRC, BATCH>;
@@ -699,7 +699,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
             else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
             else if (col_cap && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
-            else if (n_seg >= P.max_events) { fate = P.events_fate; alive = false; }
+            else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
             if (!alive) pending = true;
     };
 
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
             if (P.records) {
                 le_mc_particle rec;
                 rec.sign = (int8_t)sign;
-                rec.fate = (int8_t)fate;
+                rec.fate = (int8_t)(fate == FATE_MAX_EVENTS ? P.events_fate : fate);  // a folded collision cap
                 rec.pad = 0;
                 rec.n_seg = n_seg;
                 rec.n_scat = n_scat;
@@ -1027,6 +1027,33 @@ __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ Kern
 // mean free path above lam_cut (they make the longest trajectories: many
 // wall segments before their first relaxation event) and list them so the
 // trace kernel can serve them first.  Same random words as step I.
+// Kernel entry points.  Pored-film FP32 kernels are held to 64 registers (two
+// 512-thread blocks per SM) although that spills ~250 bytes per thread:
+// measured on GB300, the doubled occupancy outweighs the spills (steady pored
+// film +7 %, surface pulse +17 %).  The others keep the compiler's own
+// register choice (naming a minimum of one block changes it for the worse).
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
+__global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
+{
+    trace_body<R, GEOM, SRC, PROFILE, BATCH, DIFF>(args);
+}
+
+template <typename R, int SRC, bool PROFILE, bool DIFF = false>
+__global__ void __launch_bounds__(512, 2) trace_kernel_porous(const __grid_constant__ KernelArgs args)
+{
+    trace_body<R, LE_MC_GEOM_POROUS, SRC, PROFILE, false, DIFF>(args);
+}
+
+// The entry point of a configuration.
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
+constexpr auto trace_entry()
+{
+    if constexpr (GEOM == LE_MC_GEOM_POROUS && !BATCH && sizeof(R) == 4)
+        return trace_kernel_porous<R, SRC, PROFILE, DIFF>;
+    else
+        return trace_kernel<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ KernelArgs args)
 {
