@@ -165,6 +165,10 @@ static void fill_one(const TraceParams& P, Consts<R>& c)
     c.t_final = (R)P.t_final;
     c.sample_dt = (R)P.sample_dt;
     c.lam_cut = (R)P.lam_cut;
+    c.inv_dt = P.sample_dt > 0.0 ? (R)(1.0 / P.sample_dt) : R(0);
+    c.gsx = P.gx > 0 ? (R)(P.gx / P.L) : R(0);
+    c.gsy = P.gy > 0 ? (R)(P.gy / (P.pitch * P.cells_y)) : R(0);
+    c.gsz = P.gz > 0 ? (R)(P.gz / (P.pitch * P.cells_z)) : R(0);
     c.g = (R)P.scatter_g;
 }
 

@@ -57,6 +57,7 @@ struct Consts {
     R init_lo, init_span;                 // INITIAL: heated layer
     R p_sx, p_st, p_tc, p_y0, p_z0;       // PULSE
     R t_final, sample_dt, lam_cut;
+    R inv_dt, gsx, gsy, gsz;              // 1 / sample_dt; grid cells per metre along x, y, z
     R g;                                  // scattering mean cosine (0 isotropic)
 };
 

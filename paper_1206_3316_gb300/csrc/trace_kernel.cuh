@@ -520,21 +520,32 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 const R t_end = fmin(t_b, K.t_final);
                 // first candidate sample, one early: the rounded quotient may
                 // overshoot by one, and the comparisons below decide exactly
-                int k = (int)ceil(t / dts - R(0.5)) - 1;
+                // (FP32: products with host-computed reciprocals; FP64: the
+                // divisions exactly as the oracle forms them)
+                int k;
+                if constexpr (sizeof(R) == 4) k = (int)ceil(t * K.inv_dt - R(0.5)) - 1;
+                else k = (int)ceil(t / dts - R(0.5)) - 1;
                 k = max(k, 0);
                 const R Dy = K.Dy, Dz = K.Dz;
-                const int wy = cy % P.cells_y, wz = cz % P.cells_z;
-                const R Yc = (R)(wy < 0 ? wy + P.cells_y : wy) * pitch;
-                const R Zc = (R)(wz < 0 ? wz + P.cells_z : wz) * pitch;
+                // cy, cz are kept wrapped into the periodic domain
+                const R Yc = (R)cy * pitch;
+                const R Zc = (R)cz * pitch;
                 for (; k < P.n_samples; ++k) {
                     const R ts = ((R)k + R(0.5)) * dts;
                     if (ts < t) continue;
                     if (ts >= t_b || ts > t_end) break;
                     const R d = vg * (ts - t);
                     const R px = x + ox * d, py = Yc + (y + oy * d), pz = Zc + (z + oz * d);
-                    int ix = (int)M::floor_(px / L * (R)P.gx);
-                    int iy = (int)M::floor_(py / Dy * (R)P.gy);
-                    int iz = (int)M::floor_(pz / Dz * (R)P.gz);
+                    int ix, iy, iz;
+                    if constexpr (sizeof(R) == 4) {
+                        ix = (int)M::floor_(px * K.gsx);
+                        iy = (int)M::floor_(py * K.gsy);
+                        iz = (int)M::floor_(pz * K.gsz);
+                    } else {
+                        ix = (int)M::floor_(px / L * (R)P.gx);
+                        iy = (int)M::floor_(py / Dy * (R)P.gy);
+                        iz = (int)M::floor_(pz / Dz * (R)P.gz);
+                    }
                     ix = min(max(ix, 0), P.gx - 1);
                     iy = min(max(iy, 0), P.gy - 1);
                     iz = min(max(iz, 0), P.gz - 1);
@@ -673,8 +684,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                     const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
                     y = yhi ? R(0) : (ylo ? pitch : y);
                     z = zhi ? R(0) : (zlo ? pitch : z);
-                    cy += (int)yhi - (int)ylo;
-                    cz += (int)zhi - (int)zlo;
+                    // unit-cell indices wrapped into the periodic domain
+                    cy = yhi ? (cy + 1 == P.cells_y ? 0 : cy + 1) : (ylo ? (cy == 0 ? P.cells_y - 1 : cy - 1) : cy);
+                    cz = zhi ? (cz + 1 == P.cells_z ? 0 : cz + 1) : (zlo ? (cz == 0 ? P.cells_z - 1 : cz - 1) : cz);
                 } else {
                     nox = scat ? sx : wox;
                     noy = scat ? sy : woy;
