@@ -61,6 +61,18 @@ struct alignas(16) EmitBuffer {
     Slots<uint32_t, INST ? kBufSlots : 0> inst;
 };
 
+// Transient kernels defer the Eq. 3 samples of a segment: each lane leaves
+// its segment's start point, direction, start time, speed, sign and first
+// sample index here, and the whole warp then places the samples of all its
+// lanes together at a point where every lane is converged (see flush_jobs in
+// trace_kernel), so a lane whose segment spans many sample times no longer
+// holds the other 31 lanes in a divergent loop.
+template <typename R>
+struct SampleJobs {
+    R x[32], y[32], z[32], ox[32], oy[32], oz[32], t[32], v[32];
+    int k0[32], sign[32], cell[32];  // cell: unit cell cy | cz << 16
+};
+
 template <typename R, int GEOM, int SRC, bool BATCH = false>
 using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE, BATCH>;
 
@@ -334,6 +346,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     Buf* s_buf = reinterpret_cast<Buf*>(smem + off);
     const int n_warps = blockDim.x >> 5;
     off += (size_t)n_warps * sizeof(Buf);
+    SampleJobs<R>* s_jobs = reinterpret_cast<SampleJobs<R>*>(smem + off);
+    if constexpr (TRANSIENT) off += (size_t)n_warps * sizeof(SampleJobs<R>);
     off = (off + 7) & ~(size_t)7;
     double* s_prof = reinterpret_cast<double*>(smem + off);
     const int prof_len = PROFILE ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
@@ -451,9 +465,64 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         c_part = c_seg = c_scat = c_wall = c_per = c_trunc = c_abs = 0;
     };
 
+    // Eq. 3 tally of one sample: the particle's cell at t'_k adds its sign.
+    // (FP32: products with host-computed reciprocals; FP64: the divisions
+    // exactly as the oracle forms them.)
+    auto place_sample = [&](int k, R x0, R y0, R z0, R dx, R dy, R dz, R t0, R v, int s, int ccy, int ccz) {
+        const R d = v * (((R)k + R(0.5)) * K.sample_dt - t0);
+        const R px = x0 + dx * d, py = (R)ccy * pitch + (y0 + dy * d), pz = (R)ccz * pitch + (z0 + dz * d);
+        int ix, iy, iz;
+        if constexpr (sizeof(R) == 4) {
+            ix = (int)M::floor_(px * K.gsx);
+            iy = (int)M::floor_(py * K.gsy);
+            iz = (int)M::floor_(pz * K.gsz);
+        } else {
+            ix = (int)M::floor_(px / L * (R)P.gx);
+            iy = (int)M::floor_(py / K.Dy * (R)P.gy);
+            iz = (int)M::floor_(pz / K.Dz * (R)P.gz);
+        }
+        ix = min(max(ix, 0), P.gx - 1);
+        iy = min(max(iy, 0), P.gy - 1);
+        iz = min(max(iz, 0), P.gz - 1);
+        const size_t cell = (((size_t)k * P.gz + iz) * P.gy + iy) * P.gx + ix;
+        atomicAdd(&P.grid[cell], s);
+    };
+    // Place every deferred sample of the warp (all 32 lanes converged): item j
+    // of the warp's total belongs to the first lane whose inclusive prefix
+    // count exceeds j (binary search over the lanes by shuffles).
+    int job_n = 0;
+    auto flush_jobs = [&]() {
+        const int total = __reduce_add_sync(FULL, (unsigned)job_n);
+        if (total == 0) return;
+        int inc = job_n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int excl = inc - job_n;
+        const SampleJobs<R>& J = s_jobs[threadIdx.x >> 5];
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int j = base + lane;
+            int own = 0;
+#pragma unroll
+            for (int bit = 16; bit > 0; bit >>= 1) {
+                const int v = __shfl_sync(FULL, inc, own + bit - 1);
+                if (v <= j) own += bit;
+            }
+            const int own_excl = __shfl_sync(FULL, excl, own);
+            if (j < total)
+                place_sample(J.k0[own] + (j - own_excl), J.x[own], J.y[own], J.z[own], J.ox[own], J.oy[own], J.oz[own],
+                             J.t[own], J.v[own], J.sign[own], J.cell[own] & 0xFFFF, J.cell[own] >> 16);
+        }
+        __syncwarp();
+        job_n = 0;
+    };
+
     // ---- one segment: steps II-VI, from the segment's four random words r
     // (counter (n_seg + 1, 0, pid, instance): known before the segment runs)
-    auto segment = [&](const uint4 r) {
+    auto segment = [&](const uint4 r, const bool coop) {
             // step II: flight to the next relaxation event (as a length)
             const R ell = lam * M::neg_log(M::uniform(r.x));
             // step III: first boundary along the ray
@@ -516,41 +585,45 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             if constexpr (TRANSIENT) t_b = t + seg / vg;
             // step V: contribution of the segment
             if constexpr (TRANSIENT) {
+                // Eq. 3: the sample times t'_k in [t, t_b), up to t_final: a
+                // contiguous index range [k_lo, k_end), found exactly from
+                // rounded estimates with the same comparisons a scan would make
                 const R dts = K.sample_dt;
                 const R t_end = fmin(t_b, K.t_final);
-                // first candidate sample, one early: the rounded quotient may
-                // overshoot by one, and the comparisons below decide exactly
-                // (FP32: products with host-computed reciprocals; FP64: the
-                // divisions exactly as the oracle forms them)
-                int k;
-                if constexpr (sizeof(R) == 4) k = (int)ceil(t * K.inv_dt - R(0.5)) - 1;
-                else k = (int)ceil(t / dts - R(0.5)) - 1;
-                k = max(k, 0);
-                const R Dy = K.Dy, Dz = K.Dz;
-                // cy, cz are kept wrapped into the periodic domain
-                const R Yc = (R)cy * pitch;
-                const R Zc = (R)cz * pitch;
-                for (; k < P.n_samples; ++k) {
-                    const R ts = ((R)k + R(0.5)) * dts;
-                    if (ts < t) continue;
-                    if (ts >= t_b || ts > t_end) break;
-                    const R d = vg * (ts - t);
-                    const R px = x + ox * d, py = Yc + (y + oy * d), pz = Zc + (z + oz * d);
-                    int ix, iy, iz;
-                    if constexpr (sizeof(R) == 4) {
-                        ix = (int)M::floor_(px * K.gsx);
-                        iy = (int)M::floor_(py * K.gsy);
-                        iz = (int)M::floor_(pz * K.gsz);
-                    } else {
-                        ix = (int)M::floor_(px / L * (R)P.gx);
-                        iy = (int)M::floor_(py / Dy * (R)P.gy);
-                        iz = (int)M::floor_(pz / Dz * (R)P.gz);
+                const int ns = P.n_samples;
+                auto ts_of = [&](int k) { return ((R)k + R(0.5)) * dts; };
+                int k_lo, k_end;
+                if constexpr (sizeof(R) == 4) {
+                    k_lo = (int)ceil(t * K.inv_dt - R(0.5)) - 1;
+                    k_end = (int)ceil(t_end * K.inv_dt - R(0.5)) - 1;
+                } else {
+                    k_lo = (int)ceil(t / dts - R(0.5)) - 1;
+                    k_end = (int)ceil(t_end / dts - R(0.5)) - 1;
+                }
+                k_lo = max(k_lo, 0);
+                while (k_lo < ns && ts_of(k_lo) < t) ++k_lo;
+                k_end = max(k_end, k_lo);
+                while (k_end < ns && ts_of(k_end) < t_b && ts_of(k_end) <= t_end) ++k_end;
+                const int n_s = k_end - k_lo;
+                // (cy, cz are kept wrapped into the periodic domain)
+                if (coop) {
+                    job_n = n_s;
+                    if (n_s > 0) {
+                        SampleJobs<R>& J = s_jobs[threadIdx.x >> 5];
+                        J.x[lane] = x;
+                        J.y[lane] = y;
+                        J.z[lane] = z;
+                        J.cell[lane] = cy | (cz << 16);
+                        J.ox[lane] = ox;
+                        J.oy[lane] = oy;
+                        J.oz[lane] = oz;
+                        J.t[lane] = t;
+                        J.v[lane] = vg;
+                        J.k0[lane] = k_lo;
+                        J.sign[lane] = sign;
                     }
-                    ix = min(max(ix, 0), P.gx - 1);
-                    iy = min(max(iy, 0), P.gy - 1);
-                    iz = min(max(iz, 0), P.gz - 1);
-                    const size_t cell = (((size_t)k * P.gz + iz) * P.gy + iy) * P.gx + ix;
-                    atomicAdd(&P.grid[cell], sign);
+                } else {
+                    for (int k = k_lo; k < k_end; ++k) place_sample(k, x, y, z, ox, oy, oz, t, vg, sign, cy, cz);
                 }
             }
             if constexpr (PROFILE) {
@@ -779,7 +852,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             __syncwarp();
             if (alive) {
                 const int my = __popc(m & lanemask_lt);
-                for (int k = 0; k < steps && alive; ++k) segment(words[k * n_a + my]);
+                for (int k = 0; k < steps && alive; ++k) segment(words[k * n_a + my], false);
             }
             __syncwarp();
             if (pending) finish();
@@ -872,6 +945,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
 
     // Phase B: the queue (long-first list, then the natural order).
     for (;;) {
+        if constexpr (TRANSIENT) flush_jobs();
         const unsigned dead = __ballot_sync(FULL, !alive);
         // refill once refill_min lanes are idle (or at once near the end)
         if (dead && (dead == FULL || qdone || __popc(dead) >= refill_min)) {
@@ -989,8 +1063,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
         }
         if (!alive) continue;
-        segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk));
+        segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk), true);
     }
+    if constexpr (TRANSIENT) flush_jobs();
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
     if constexpr (BATCH) {
@@ -1138,6 +1213,7 @@ inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_le
 {
     size_t off = table_bytes<R, SRC, PROFILE>(n_modes);
     off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC, BATCH>);
+    if (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL) off += (size_t)(threads / 32) * sizeof(SampleJobs<R>);
     off = (off + 7) & ~(size_t)7;
     off += (size_t)prof_len * sizeof(double);
     off += (size_t)hj_len * sizeof(double);
