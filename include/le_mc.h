@@ -204,7 +204,10 @@ typedef struct {
                                      * summation order).                       */
     int32_t refill_min;             /* a warp refills idle lanes once this many
                                      * are idle (0 = library default, 4)         */
-    double long_mfp_cut;            /* [m]; 0 = 32 L (PLANES, POROUS)            */
+    double long_mfp_cut;            /* [m]; 0 = 32 L (PLANES, POROUS).  Runs of
+                                     * at most 2^25 particles also trace those
+                                     * above 32 times this first, each by a warp
+                                     * of its own (at most 512)                */
     int32_t chunk;                  /* queue positions a warp claims per atomic,
                                      * multiple of 32 (0 = library default, 256) */
     uint32_t first_particle;        /* particle ids traced are first_particle ..
