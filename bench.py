@@ -480,8 +480,12 @@ def main():
     }
     if not args.no_batched:
         line["batched"] = batched_measurement(P, torch, dev, stream, args.steps, launch)
+        # whole-launch rate (the dominant kernel is the same trace kernel)
+        line["batched"]["roofline_frac"] = line["batched"]["value"] * OPS_PER_SEGMENT / peak_ops
     if args.served_seconds > 0:
         line["served"] = served_measurement(P, args.served_seconds)
+        # arrival-limited: the stream offers far less work than the GPU can trace
+        line["served"]["roofline_frac"] = line["served"]["aggregate_segments_per_s"] * OPS_PER_SEGMENT / peak_ops
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(problem)
     print(json.dumps(line), flush=True)

@@ -118,3 +118,24 @@ def test_batch_rejects_mixed_families(P):
     d = W.porous_film(n_particles=10)
     with pytest.raises(P.LeMcError):
         P.Batch([d])
+
+
+def test_batched_films_each_instance_against_its_pin(P, oracle, analytic):
+    # config 3: 256 films of uneven thickness and size in one launch; every
+    # instance matches the Fuchs-Sondheimer value for its thickness, and the
+    # small instances match the FP64 oracle
+    probs = W.batched_films(256)
+    with P.Batch(probs) as b:
+        b.launch()
+        got = b.results()
+    zs = []
+    for p, g in zip(probs, got):
+        pin = analytic.kappa_film(W.SILICON_LIKE, p["geometry"]["L"])
+        zs.append(abs(g["kappa"] - pin) / g["kappa_se"])
+        assert g["particles"] == p["run"]["n_particles"] and g["device_flags"] == 0
+    assert max(zs) < 4.5, max(zs)
+    small = [i for i, p in enumerate(probs) if p["run"]["n_particles"] <= 100_000][:24]
+    for i in small:
+        o = oracle.run(W.with_run(probs[i], precision="fp64"))
+        z = abs(got[i]["kappa"] - o["kappa"]) / np.hypot(got[i]["kappa_se"], o["kappa_se"])
+        assert z < 4.5, (i, z)

@@ -351,3 +351,27 @@ def test_grid_temperature_readback(P):
         P.le_mc_destroy_run(h)
         P.le_mc_destroy_geometry(geo)
         P.le_mc_destroy_material(mat)
+
+
+def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
+    # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
+    # picks): below the pore-free film times the solid fraction, and the same
+    # conductivity as the FP64 oracle on a smaller sample
+    g = P.simulate(W.porous_film(n_particles=100_000_000), arrays=False)
+    film = analytic.kappa_film(W.SILICON_LIKE, 300e-9)
+    assert 0.0 < g["kappa"] < film * (1.0 - np.pi * 0.3 ** 2)
+    assert g["device_flags"] == 0 and g["particles"] == 100_000_000
+    o = oracle.run(W.porous_film(n_particles=400_000, precision="fp64"))
+    assert _z(g, o, "kappa") < 3.0
+
+
+def test_pulse_full_size_conserves_every_particle(P):
+    # config-2 transient at full size: with adiabatic walls every particle is
+    # counted exactly once at every sample after the pulse has been emitted
+    # (emission times beyond 17 sigma of the 300 ps pulse do not occur)
+    n = 100_000_000
+    g = P.simulate(W.porous_pulse(n_particles=n))
+    sums = g["grid"].reshape(g["grid"].shape[0], -1).sum(axis=1, dtype=np.int64)
+    assert sums[-1] == n
+    assert np.all(np.diff(sums[:60]) >= 0)  # the count only grows while the pulse emits
+    assert g["device_flags"] == 0
