@@ -144,3 +144,52 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def truncation_study(H, H_se, resolved=3.0, first=2):
+    """Choose the scattering cap K_s from the flux split by scattering index
+    (the ``H`` / ``H_se`` arrays of a run with ``n_hj`` > 0), as the paper does
+    empirically after its Fig. 2: <H_j> is the flux carried between the j-th
+    and (j+1)-th relaxation of a history (j = 0: emission to the first).
+
+    Returns a dict with
+      k_s      the first j at which |<H_j>| falls to its own standard error
+               (collecting later terms adds noise, not information);
+      ratio    the geometric decay ratio of |<H_j>| fitted, by weighted least
+               squares on log |<H_j>|, over the contiguous run of indices from
+               ``first`` on that are resolved to ``resolved`` standard errors
+               (None if fewer than two are);
+      tail(K)  a function: the flux the cap K drops, sum_{j >= K} <H_j>,
+               extrapolated from that fit (0 when the split is not decaying).
+    Host-side arithmetic on the tallies; the tracing itself is unchanged."""
+    import numpy as np
+
+    H = np.asarray(H, dtype=np.float64)
+    se = np.asarray(H_se, dtype=np.float64)
+    n = H.size
+    below = np.nonzero(np.abs(H) <= se)[0]
+    k_s = int(below[0]) if below.size else n
+    # the decaying range: the contiguous run of resolved terms from `first` on
+    # (isolated noise excursions further out must not enter the fit)
+    idx = np.arange(n)
+    ok = np.zeros(n, dtype=bool)
+    for j in range(first, n):
+        if not (se[j] > 0 and np.abs(H[j]) > resolved * se[j]):
+            break
+        ok[j] = True
+    ratio, amp, sgn = None, 0.0, 0.0
+    if ok.sum() >= 2:
+        j, y = idx[ok], np.log(np.abs(H[ok]))
+        w = (np.abs(H[ok]) / se[ok]) ** 2  # 1 / var(log|H|)
+        A = np.vstack([np.ones_like(j, dtype=np.float64), j]).T
+        coef = np.linalg.lstsq(A * np.sqrt(w)[:, None], y * np.sqrt(w), rcond=None)[0]
+        ratio = float(np.exp(coef[1]))
+        amp = float(np.exp(coef[0]))
+        sgn = float(np.sign(np.sum(H[ok])))
+
+    def tail(K):
+        if ratio is None or not (0.0 < ratio < 1.0):
+            return 0.0
+        return sgn * amp * ratio ** K / (1.0 - ratio)
+
+    return {"k_s": k_s, "ratio": ratio, "tail": tail}

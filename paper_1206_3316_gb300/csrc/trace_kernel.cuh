@@ -390,9 +390,16 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // (particle ids of the run, or the concatenated instances of a batch)
     // minus those already listed
     const unsigned long long n_pos = BATCH ? P.offsets[P.n_instances] : (unsigned long long)P.n_particles;
-    const uint32_t n_long = P.long_list ? min(P.long_count[0], P.long_cap) : 0u;
-    const uint32_t n_ext = (P.long_list && P.ext_cap > 0) ? min(P.long_count[1], P.ext_cap) : 0u;
-    const uint32_t* long_region = P.long_list ? P.long_list + P.ext_cap : nullptr;
+    // The extreme list is used all or nothing: if classification found more
+    // extreme particles than it holds, which ones fit depended on the order
+    // of atomics, so none is traced apart and the (full, contiguous) extreme
+    // region joins the long-first list instead.
+    const uint32_t raw_ext = (P.long_list && P.ext_cap > 0) ? P.long_count[1] : 0u;
+    const bool ext_overflow = raw_ext > P.ext_cap;
+    const uint32_t n_ext = ext_overflow ? 0u : raw_ext;
+    const uint32_t n_long0 = P.long_list ? min(P.long_count[0], P.long_cap) : 0u;
+    const uint32_t n_long = ext_overflow ? P.ext_cap + n_long0 : n_long0;
+    const uint32_t* long_region = P.long_list ? (ext_overflow ? P.long_list : P.long_list + P.ext_cap) : nullptr;
     const unsigned long long q_total = (unsigned long long)n_long + n_pos;
     const int refill_min = P.refill_min > 1 ? P.refill_min : 1;
     const Consts<R>& K = consts_of<R>(P);
@@ -794,6 +801,15 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // known in advance) into the emission buffer's storage, and the particle
     // traces a round of segments without Philox on its critical path.  Each
     // segment uses the same words as otherwise.
+    //
+    // Reproducibility: the rounds inline a second copy of the segment code,
+    // whose FP32 operations the compiler may contract differently from the
+    // main loop's copy, so a particle must always be traced by the same copy.
+    // The set of extreme particles is fixed by their emission modes (and is
+    // used all or nothing, see n_ext), so which copy traces a particle never
+    // depends on timing, and results are bit-identical across runs and
+    // launch shapes.  (Assisting whichever lanes happen to be last at the end
+    // of the queue broke that and is not done.)
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
     auto finish = [&]() {
             if constexpr (BATCH) {

@@ -375,3 +375,40 @@ def test_pulse_full_size_conserves_every_particle(P):
     assert sums[-1] == n
     assert np.all(np.diff(sums[:60]) >= 0)  # the count only grows while the pulse emits
     assert g["device_flags"] == 0
+
+
+def test_scattering_cap_drops_exactly_the_later_flux_split(P):
+    # The same histories cut at K relaxations lose exactly the flux carried
+    # after the K-th one: kappa(64) - kappa(K) = -(sum_{j >= K} <H_j>) / (dT/dz),
+    # up to summation order; the truncation study predicts that loss.
+    from tests.test_oracle_transport import _truncation_study
+    full = P.simulate(W.porous_film(n_particles=20_000_000, max_scatter=64, n_hj=64))
+    H, se = full["H"], full["H_se"]
+    dTdz = -1.0 / 100e-9
+    st = _truncation_study()(H, se)
+    for K in (2, 4, 8):
+        cut = P.simulate(W.porous_film(n_particles=20_000_000, max_scatter=K), arrays=False)
+        lost = full["kappa"] - cut["kappa"]
+        expect = -H[K:].sum() / dTdz
+        assert lost == pytest.approx(expect, rel=1e-4, abs=1e-6 * abs(full["kappa"])), (K, lost, expect)
+        err = np.sqrt((se[K:] ** 2).sum()) / abs(dTdz)
+        assert abs(-st["tail"](K) / dTdz - lost) < 3.0 * err, (K, lost, -st["tail"](K) / dTdz, err)
+
+
+@pytest.mark.parametrize("case", ["pored film", "10 nm film (extreme list overflows)"])
+def test_fp32_histories_bit_identical_across_runs_and_shapes(P, case):
+    # Every particle is traced by the same compiled code whatever the timing
+    # (extreme particles, traced apart, are a set fixed by their emission
+    # modes, used all or nothing), so FP32 histories repeat bit for bit.
+    if case == "pored film":
+        p = W.porous_film(n_particles=1_000_000, pitch=150e-9, radius=40e-9)
+    else:
+        p = W.silicon_film(n_particles=2_000_000, thickness=10e-9)
+    runs = [P.simulate(p, record_particles=True),
+            P.simulate(p, record_particles=True),
+            P.simulate(p, record_particles=True, launch={"threads_per_block": 256, "blocks_per_sm": 1})]
+    for r in runs[1:]:
+        for f in ("sign", "fate", "n_seg", "n_scat", "n_wall", "n_periodic", "mode0"):
+            assert np.array_equal(r["particles_rec"][f], runs[0]["particles_rec"][f]), (case, f)
+        assert np.array_equal(r["particles_rec"]["L_axis"], runs[0]["particles_rec"]["L_axis"]), case
+        assert r["segments"] == runs[0]["segments"]

@@ -271,3 +271,33 @@ def test_two_slab_solvers_agree(analytic):
     assert abs(analytic.slab_solution(t, M=200)["psi"] - (0.5 + float(analytic.En(3, t)))) < 1e-3
     # thick limit approaches the diffusion result with jump conditions, 4/(3 tau_L + 4)
     assert abs(analytic.slab_solution(50.0, M=400)["psi"] / (4.0 / (3 * 50.0 + 4.0)) - 1) < 0.01
+
+
+def _truncation_study():
+    # the package's host-side helper, loaded without the CUDA library
+    import os
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_1206_3316_gb300", "__init__.py")).read()
+    ns = {}
+    exec(src[src.index("def truncation_study"):], ns)
+    return ns["truncation_study"]
+
+
+def test_truncation_study_predicts_dropped_flux(oracle):
+    # Pored film, flux split by scattering index up to 64 relaxations: the
+    # geometric extrapolation of the resolved, decaying <H_j> predicts the flux
+    # a cap K drops (measured directly as the sum of the later <H_j>) within
+    # the statistical error of that sum; the paper's noise criterion gives K_s.
+    study = _truncation_study()
+    p = W.porous_film(n_particles=2_000_000, precision="fp64", max_scatter=64, n_hj=64)
+    r = oracle.run(p)
+    H, se = r["H"], r["H_se"]
+    st = study(H, se)
+    assert 3 <= st["k_s"] < 64 and 0.0 < st["ratio"] < 1.0
+    for K in (2, 4, 6):
+        dropped, err = H[K:].sum(), np.sqrt((se[K:] ** 2).sum())
+        assert abs(st["tail"](K) - dropped) < 3.0 * err, (K, st["tail"](K), dropped, err)
+    # diffuse film: nothing after the first event survives in expectation
+    f = oracle.run(W.silicon_film(n_particles=400_000, precision="fp64", n_hj=16))
+    sf = study(f["H"], f["H_se"])
+    assert sf["k_s"] <= 3 and np.all(np.abs(f["H"][1:]) < 4.0 * f["H_se"][1:])
