@@ -78,7 +78,7 @@ bool fp32(const le_mc_batch b) { return b->run0.precision == LE_MC_PREC_FP32; }
 bool all_diffuse(const le_mc_batch b)
 {
     return b->run0.source == LE_MC_SRC_GRADIENT && b->geo0.wall_lo == LE_MC_WALL_DIFFUSE &&
-           b->geo0.wall_hi == LE_MC_WALL_DIFFUSE && b->mv.scatter_g == 0.0;
+           b->geo0.wall_hi == LE_MC_WALL_DIFFUSE && b->mv.scatter_g == 0.0 && b->run0.n_hj <= 0;
 }
 
 // Kernel arguments for the whole batch.

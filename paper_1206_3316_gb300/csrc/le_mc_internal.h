@@ -69,7 +69,7 @@ constexpr int kBatchSmemMax = 512;
 // launches short enough for one 4096-segment history to be near-critical
 // (~1e7 particles of ~50 segments take about as long on a GB300), so
 // launches of more than kExtMaxParticles particles keep none: there the
-// dedicated warps would cost lanes and save nothing.
+// warps tracing them apart would cost lanes and save nothing.
 constexpr double kExtremeFactor = 32.0;
 constexpr uint32_t kExtCap = 512;
 constexpr unsigned long long kExtMaxParticles = 1ull << 25;

@@ -60,7 +60,7 @@ static bool all_diffuse(const TraceParams& p)
 {
     return p.src == LE_MC_SRC_GRADIENT && (p.geom == LE_MC_GEOM_PLANES || p.geom == LE_MC_GEOM_POROUS) &&
            p.wall_lo == LE_MC_WALL_DIFFUSE && p.wall_hi == LE_MC_WALL_DIFFUSE &&
-           (p.geom != LE_MC_GEOM_POROUS || p.pore_wall == LE_MC_WALL_DIFFUSE) && p.aniso == 0;
+           (p.geom != LE_MC_GEOM_POROUS || p.pore_wall == LE_MC_WALL_DIFFUSE) && p.aniso == 0 && p.n_hj == 0;
 }
 
 cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
