@@ -189,7 +189,8 @@ typedef struct {
     int32_t n_samples;              /* PULSE: sample times (k + 1/2) sample_dt    */
     double t_final;                 /* PULSE: end of the simulation [s]          */
     double sample_dt;               /* PULSE: sample spacing [s]                 */
-    int32_t n_hj;                   /* flux split by scattering index j (0 = off) */
+    int32_t n_hj;                   /* flux split by scattering index j (0 = off;
+                                     * steady sources only)                     */
     int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
     int32_t blocks_per_sm;          /* launch shape (0 = library default)        */
     int32_t threads_per_block;      /* 0 = default: 512, or 256 when that keeps more

@@ -286,6 +286,10 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
         if (r->n_batch < 1 || r->n_batch > LE_MC_MAX_BATCH) { *why = "n_batch out of 1..64"; return LE_MC_ERR_INVALID; }
     }
     if (r->n_hj < 0 || r->n_hj > LE_MC_MAX_HJ) { *why = "n_hj out of range"; return LE_MC_ERR_INVALID; }
+    if (r->n_hj > 0 && (r->source == LE_MC_SRC_PULSE || r->source == LE_MC_SRC_INITIAL)) {
+        *why = "the flux split by scattering index (n_hj) is a steady estimator";
+        return LE_MC_ERR_INVALID;
+    }
     if (r->n_samples < 0) { *why = "n_samples < 0"; return LE_MC_ERR_INVALID; }
     if (r->n_samples > 0) {
         if (r->source != LE_MC_SRC_PULSE && r->source != LE_MC_SRC_INITIAL) {

@@ -332,6 +332,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     constexpr bool POROUS = (GEOM == LE_MC_GEOM_POROUS);
     constexpr bool TRANSIENT = (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL);
     constexpr bool AXIS_X = (SRC == LE_MC_SRC_WALLS);
+    // the flux split by scattering index (a steady estimator): not in DIFF
+    // kernels (runs that ask for it use the general kernel) nor transient ones
+    constexpr bool HJ = !DIFF && !TRANSIENT;
     // Kernels whose estimators never need the group velocity (steady path
     // integrals) keep one 16-byte word per mode: (threshold, alias,
     // Lambda_j, Lambda_alias), so an Eq. 2 redraw is a single shared load.
@@ -677,7 +680,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             }
             const R dL = AXIS_X ? (x_new - x) : oz * seg;
             Lacc += dL;
-            if constexpr (!DIFF) hrun += dL;
+            if constexpr (HJ) hrun += dL;
 
             // steps IVa / IVb.  Every lane evaluates the same straight-line code
             // and keeps its own outcome through selects, so walls and relaxation
@@ -781,7 +784,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             n_scat += scat ? 1u : 0u;
             n_wall += on_wall ? 1u : 0u;
             n_per += periodic ? 1u : 0u;
-            if constexpr (!DIFF) {  // flux split by scattering index (never in DIFF kernels)
+            if constexpr (HJ) {  // flux split by scattering index
                 if (P.n_hj > 0 && scat) {
                     if (n_scat - 1u < (uint32_t)P.n_hj) {
                         atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
@@ -832,7 +835,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             c_per += n_per;
             c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
             c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
-            if (!DIFF && P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
+            if (HJ && P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
                 atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
                 atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
             }

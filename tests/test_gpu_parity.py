@@ -412,3 +412,12 @@ def test_fp32_histories_bit_identical_across_runs_and_shapes(P, case):
             assert np.array_equal(r["particles_rec"][f], runs[0]["particles_rec"][f]), (case, f)
         assert np.array_equal(r["particles_rec"]["L_axis"], runs[0]["particles_rec"]["L_axis"]), case
         assert r["segments"] == runs[0]["segments"]
+
+
+def test_flux_split_rejected_for_transient_sources(P):
+    for prob in (W.porous_pulse(n_particles=100, grid=(2, 2, 2), n_samples=4),
+                 W.porous_initial(n_particles=100, grid=(2, 2, 2), n_samples=4)):
+        prob["run"]["n_hj"] = 8
+        with pytest.raises(P.LeMcError) as e:
+            P.simulate(prob)
+        assert e.value.status == 1
