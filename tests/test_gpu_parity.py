@@ -421,3 +421,21 @@ def test_flux_split_rejected_for_transient_sources(P):
         with pytest.raises(P.LeMcError) as e:
             P.simulate(prob)
         assert e.value.status == 1
+
+
+@pytest.mark.parametrize("material", ["gray", "silicon-like"])
+def test_slab_profiles_fp32_chi2_against_oracle(P, oracle, material):
+    # FP32 GPU profiles T(x), q(x) (batch-mean errors) against the FP64 oracle
+    # on the same seeded problem: chi^2 over the 50 bins below its p = 1e-3
+    # quantile, for each profile
+    from scipy import stats
+    prob = W.gray_slab(n_particles=4_000_000, n_bins=50, precision="fp32")
+    if material != "gray":
+        prob["material"] = dict(W.SILICON_LIKE, n_bins=10)
+        prob["geometry"]["L"] = 100e-9
+    g = P.simulate(prob)
+    o = oracle.run(W.with_run(prob, n_particles=1_000_000, precision="fp64"))
+    for key in ("T", "q"):
+        z = (g[key] - o[key]) / np.hypot(g[key + "_se"], o[key + "_se"])
+        chi2 = float(np.sum(z ** 2))
+        assert stats.chi2.sf(chi2, z.size) > 1e-3, (material, key, chi2)
