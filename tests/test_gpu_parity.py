@@ -439,3 +439,25 @@ def test_slab_profiles_fp32_chi2_against_oracle(P, oracle, material):
         z = (g[key] - o[key]) / np.hypot(g[key + "_se"], o[key + "_se"])
         chi2 = float(np.sum(z ** 2))
         assert stats.chi2.sf(chi2, z.size) > 1e-3, (material, key, chi2)
+
+
+def test_more_than_2_31_particles_in_one_run(P, analytic):
+    # the largest runs the ABI allows are ~2^32 particles: 64-bit queue
+    # positions, 32-bit particle ids near their limit, a 268 MB long-first
+    # bitmap; the gray slab (3 segments a particle) keeps it to ~0.1 s
+    n = (1 << 31) + 5
+    g = P.simulate(W.gray_slab(n_particles=n, n_bins=0, precision="fp32"), arrays=False)
+    assert g["particles"] == n and g["device_flags"] == 0
+    pin = analytic.slab_solution(1.0, n_bins=50, M=200)["psi"]
+    assert abs(g["psi"] - pin) < 3.0 * g["psi_se"], (g["psi"], pin, g["psi_se"])
+
+
+@pytest.mark.parametrize("n", [1, 31, 33, 4095, 4097])
+def test_ragged_sizes_per_particle(P, oracle, n):
+    # sizes around a warp and around the long-first threshold (4096)
+    prob = W.silicon_film(n_particles=n, thickness=0.7, material=dict(W.GRAY_UNIT), precision="fp64",
+                          max_scatter=12, max_events=200, dTdz=-1.0)
+    g = P.simulate(prob, record_particles=True)
+    o = oracle.run(prob, record_particles=True)
+    _same_particles(g["particles_rec"], o["particles_rec"])
+    assert g["particles"] == n
