@@ -60,10 +60,15 @@ LANES_PER_SM = 128  # FP32/INT32 lanes issuing one operation per clock
 
 
 def _sha_kernel_sources():
+    """Hash of the kernel sources with comments and whitespace removed, so
+    that only edits which can change the compiled code invalidate a capture."""
     h = hashlib.sha256()
     for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h"):
-        with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f)) as fh:
+            txt = fh.read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        h.update(re.sub(r"\s+", "", txt).encode())
     return h.hexdigest()[:16]
 
 

@@ -449,11 +449,6 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     const unsigned long long chunk = P.chunk >= 32 ? (unsigned long long)P.chunk : 32ull;
     const unsigned long long long_claim = 32ull;
     unsigned long long w_next = 0, w_end = 0;
-    // Extreme particles (emission mean free path above kExtremeFactor times
-    // the long-first cut) can outlast the whole launch at a warp's fair share
-    // of issue slots; each is traced by a warp of its own in assisted rounds
-    // (phase A below), which roughly halves the instructions per segment on
-    // its critical path.
     uint32_t cur_b = 0xFFFFFFFFu;  // batch instance the lane accumulators belong to
 
     // batch mode: move the lane accumulators to instance b's totals
@@ -535,271 +530,271 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // ---- one segment: steps II-VI, from the segment's four random words r
     // (counter (n_seg + 1, 0, pid, instance): known before the segment runs)
     auto segment = [&](const uint4 r, const bool coop) {
-            // step II: flight to the next relaxation event (as a length)
-            const R ell = lam * M::neg_log(M::uniform(r.x));
-            // step III: first boundary along the ray
-            R d_b = big;
-            int kind = HIT_NONE;
-            if constexpr (GEOM != LE_MC_GEOM_BULK) {
-                // distance to the wall ahead; a flight parallel to the walls gets
-                // an infinite (or NaN, never <= ell) distance and no hit
-                const bool up = ox > R(0);
-                d_b = M::div(up ? (Lp - x) : x, fabs(ox));
-                kind = up ? HIT_XHI : HIT_XLO;
-            }
-            if constexpr (POROUS) {
-                if (rad > R(0)) {
-                    const R ry = y - half, rz = z - half;
-                    const R a = oy * oy + oz * oz;
-                    const R b = ry * oy + rz * oz;
-                    const R c = ry * ry + rz * rz - rad2;
-                    if (a > R(0) && b < R(0)) {
-                        const R disc = b * b - a * c;
-                        if (disc >= R(0)) {
-                            R tc = M::div(c, M::sqrt_(disc) - b);
-                            tc = fmax(tc, R(0));
-                            if (tc < d_b) { d_b = tc; kind = HIT_CYL; }
-                        }
+        // step II: flight to the next relaxation event (as a length)
+        const R ell = lam * M::neg_log(M::uniform(r.x));
+        // step III: first boundary along the ray
+        R d_b = big;
+        int kind = HIT_NONE;
+        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            // distance to the wall ahead; a flight parallel to the walls gets
+            // an infinite (or NaN, never <= ell) distance and no hit
+            const bool up = ox > R(0);
+            d_b = M::div(up ? (Lp - x) : x, fabs(ox));
+            kind = up ? HIT_XHI : HIT_XLO;
+        }
+        if constexpr (POROUS) {
+            if (rad > R(0)) {
+                const R ry = y - half, rz = z - half;
+                const R a = oy * oy + oz * oz;
+                const R b = ry * oy + rz * oz;
+                const R c = ry * ry + rz * rz - rad2;
+                if (a > R(0) && b < R(0)) {
+                    const R disc = b * b - a * c;
+                    if (disc >= R(0)) {
+                        R tc = M::div(c, M::sqrt_(disc) - b);
+                        tc = fmax(tc, R(0));
+                        if (tc < d_b) { d_b = tc; kind = HIT_CYL; }
                     }
                 }
-                if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
-                else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
-                if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
-                else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
             }
-            bool hit = (kind != HIT_NONE) && (d_b <= ell);
-            if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
-                // Absorbing walls decide a particle's fate: when the FP32 flight
-                // and wall distances are within a few ulp of each other (grazing
-                // flights make the wall distance large and its rounding
-                // relatively coarse), redo the comparison in FP64 from the same
-                // inputs.
-                const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
-                if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
-                    const double u = (double)M::uniform(r.x);
-                    const double ell64 = (double)lam * -log(u);
-                    const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
-                    hit = d64 <= ell64;
-                }
+            if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
+            else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
+            if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
+            else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
+        }
+        bool hit = (kind != HIT_NONE) && (d_b <= ell);
+        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+            // Absorbing walls decide a particle's fate: when the FP32 flight
+            // and wall distances are within a few ulp of each other (grazing
+            // flights make the wall distance large and its rounding
+            // relatively coarse), redo the comparison in FP64 from the same
+            // inputs.
+            const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
+            if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
+                const double u = (double)M::uniform(r.x);
+                const double ell64 = (double)lam * -log(u);
+                const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
+                hit = d64 <= ell64;
             }
-            R seg = hit ? d_b : ell;
-            if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
-                seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
-            }
-            R x_new = x + ox * seg;
-            if (hit && kind == HIT_XLO) x_new = R(0);
-            if (hit && kind == HIT_XHI) x_new = Lp;
+        }
+        R seg = hit ? d_b : ell;
+        if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
+            seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
+        }
+        R x_new = x + ox * seg;
+        if (hit && kind == HIT_XLO) x_new = R(0);
+        if (hit && kind == HIT_XHI) x_new = Lp;
 
-            // end time of the segment, computed once: the sample windows [t, t_b)
-            // of consecutive segments must tile time exactly (no sample lost or
-            // counted twice), so the particle's next start is this same value
-            R t_b = t;
-            if constexpr (TRANSIENT) t_b = t + seg / vg;
-            // step V: contribution of the segment
-            if constexpr (TRANSIENT) {
-                // Eq. 3: the sample times t'_k in [t, t_b), up to t_final: a
-                // contiguous index range [k_lo, k_end), found exactly from
-                // rounded estimates with the same comparisons a scan would make
-                const R dts = K.sample_dt;
-                const R t_end = fmin(t_b, K.t_final);
-                const int ns = P.n_samples;
-                auto ts_of = [&](int k) { return ((R)k + R(0.5)) * dts; };
-                int k_lo, k_end;
-                if constexpr (sizeof(R) == 4) {
-                    k_lo = (int)ceil(t * K.inv_dt - R(0.5)) - 1;
-                    k_end = (int)ceil(t_end * K.inv_dt - R(0.5)) - 1;
-                } else {
-                    k_lo = (int)ceil(t / dts - R(0.5)) - 1;
-                    k_end = (int)ceil(t_end / dts - R(0.5)) - 1;
-                }
-                k_lo = max(k_lo, 0);
-                while (k_lo < ns && ts_of(k_lo) < t) ++k_lo;
-                k_end = max(k_end, k_lo);
-                while (k_end < ns && ts_of(k_end) < t_b && ts_of(k_end) <= t_end) ++k_end;
-                const int n_s = k_end - k_lo;
-                // (cy, cz are kept wrapped into the periodic domain)
-                if (coop) {
-                    job_n = n_s;
-                    if (n_s > 0) {
-                        SampleJobs<R>& J = s_jobs[threadIdx.x >> 5];
-                        J.x[lane] = x;
-                        J.y[lane] = y;
-                        J.z[lane] = z;
-                        J.cell[lane] = cy | (cz << 16);
-                        J.ox[lane] = ox;
-                        J.oy[lane] = oy;
-                        J.oz[lane] = oz;
-                        J.t[lane] = t;
-                        J.v[lane] = vg;
-                        J.k0[lane] = k_lo;
-                        J.sign[lane] = sign;
-                    }
-                } else {
-                    for (int k = k_lo; k < k_end; ++k) place_sample(k, x, y, z, ox, oy, oz, t, vg, sign, cy, cz);
-                }
-            }
-            if constexpr (PROFILE) {
-                // time and x-displacement spent in each bin along x (slab)
-                const int nb = P.n_bins_x;
-                const R dx = L / (R)nb;
-                const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
-                const size_t stride = (size_t)nb + 1;
-                double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
-                double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
-                double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
-                double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
-                const R lo = fmin(x, x_new), hi = fmax(x, x_new);
-                int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
-                k0 = min(max(k0, 0), nb - 1);
-                k1 = min(max(k1, 0), nb - 1);
-                const double s = (double)sign;
-                if (ox == R(0)) {
-                    atomicAdd(&Td[k0], s * (double)(seg / vg));
-                } else {
-                    const R w = R(1) / (vg * fabs(ox));  // time per unit x
-                    const R qs = ox > R(0) ? R(1) : R(-1);
-                    if (k0 == k1) {
-                        const R len = hi - lo;
-                        atomicAdd(&Td[k0], s * (double)(len * w));
-                        atomicAdd(&qd[k0], s * (double)(len * qs));
-                    } else {
-                        const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
-                        const R lb = hi - (R)k1 * dx;        // partial last bin
-                        atomicAdd(&Td[k0], s * (double)(la * w));
-                        atomicAdd(&qd[k0], s * (double)(la * qs));
-                        atomicAdd(&Td[k1], s * (double)(lb * w));
-                        atomicAdd(&qd[k1], s * (double)(lb * qs));
-                        if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
-                            atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
-                            atomicAdd(&Tr[k1], -s * (double)(dx * w));
-                            atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
-                            atomicAdd(&qr[k1], -s * (double)(dx * qs));
-                        }
-                    }
-                }
-            }
-            const R dL = AXIS_X ? (x_new - x) : oz * seg;
-            Lacc += dL;
-            if constexpr (HJ) hrun += dL;
-
-            // steps IVa / IVb.  Every lane evaluates the same straight-line code
-            // and keeps its own outcome through selects, so walls and relaxation
-            // events do not split the warp.
-            x = x_new;
-            if constexpr (POROUS) {
-                y += oy * seg;
-                z += oz * seg;
-            }
-            if constexpr (TRANSIENT) t = t_b;
-            ++n_seg;
-            const bool scat = !hit;
-            int wall = -1;
-            if constexpr (DIFF) {
-                wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
-            } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
-                wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
-                if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
-                wall = hit ? wall : -1;
-                // partially specular wall: specular with probability p, decided by
-                // the flight's second uniform (a relaxation's mode draw otherwise)
-                if (any_partial && wall == LE_MC_WALL_PARTIAL) {
-                    const R p = (kind == HIT_XLO) ? K.spec_lo : ((kind == HIT_XHI) ? K.spec_hi : K.spec_pore);
-                    wall = (M::uniform(r.y) < p) ? (int)LE_MC_WALL_SPECULAR : (int)LE_MC_WALL_DIFFUSE;
-                }
-            }
-            const bool on_wall = wall >= 0;
-            const bool absorbed = wall == LE_MC_WALL_BLACK;
-            const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
-            const bool periodic = hit && !on_wall;
-            // Eq. 2 redraw (kept only on a relaxation event)
-            if constexpr (FUSED) {
-                const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
-                const uint4 e = s_fused[(uint32_t)(mm >> 32)];
-                const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
-                lam = scat ? lam_new : lam;
+        // end time of the segment, computed once: the sample windows [t, t_b)
+        // of consecutive segments must tile time exactly (no sample lost or
+        // counted twice), so the particle's next start is this same value
+        R t_b = t;
+        if constexpr (TRANSIENT) t_b = t + seg / vg;
+        // step V: contribution of the segment
+        if constexpr (TRANSIENT) {
+            // Eq. 3: the sample times t'_k in [t, t_b), up to t_final: a
+            // contiguous index range [k_lo, k_end), found exactly from
+            // rounded estimates with the same comparisons a scan would make
+            const R dts = K.sample_dt;
+            const R t_end = fmin(t_b, K.t_final);
+            const int ns = P.n_samples;
+            auto ts_of = [&](int k) { return ((R)k + R(0.5)) * dts; };
+            int k_lo, k_end;
+            if constexpr (sizeof(R) == 4) {
+                k_lo = (int)ceil(t * K.inv_dt - R(0.5)) - 1;
+                k_end = (int)ceil(t_end * K.inv_dt - R(0.5)) - 1;
             } else {
-                const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
-                const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
-                lam = scat ? lam_new : lam;
-                vg = scat ? vg_new : vg;
+                k_lo = (int)ceil(t / dts - R(0.5)) - 1;
+                k_end = (int)ceil(t_end / dts - R(0.5)) - 1;
             }
-            // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
-            const R u2 = M::uniform(r.z);
-            R sn, cs;
-            M::sincos_2pi(M::uniform(r.w), &sn, &cs);
-            const R mu = scat ? (R(2) * u2 - R(1)) : M::sqrt_(u2);
-            const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
-            const R a = st * cs, b = st * sn;
-            // direction after a relaxation: isotropic (a, b, mu) about z, or the
-            // Henyey-Greenstein law of mean cosine g about the incoming direction,
-            // its cosine from the inverted CDF and its azimuth in the
-            // orthonormal frame of Duff et al. (JCGT 2017) built on (ox, oy, oz)
-            R sx = a, sy = b, sz = mu;
-            if (aniso && scat) {
-                const R q = M::div(R(1) - hg * hg, R(1) - hg + R(2) * hg * u2);
-                R mh = M::div(R(1) + hg * hg - q * q, R(2) * hg);
-                mh = fmin(fmax(mh, R(-1)), R(1));
-                const R sh = M::sqrt_(fmax(R(0), R(1) - mh * mh));
-                const R sg = oz >= R(0) ? R(1) : R(-1);
-                const R fa = M::div(R(-1), sg + oz);
-                const R fb = ox * oy * fa;
-                sx = mh * ox + sh * (cs * (R(1) + sg * ox * ox * fa) + sn * fb);
-                sy = mh * oy + sh * (cs * (sg * fb) + sn * (sg + oy * oy * fa));
-                sz = mh * oz + sh * (cs * (-sg * ox) + sn * (-oy));
+            k_lo = max(k_lo, 0);
+            while (k_lo < ns && ts_of(k_lo) < t) ++k_lo;
+            k_end = max(k_end, k_lo);
+            while (k_end < ns && ts_of(k_end) < t_b && ts_of(k_end) <= t_end) ++k_end;
+            const int n_s = k_end - k_lo;
+            // (cy, cz are kept wrapped into the periodic domain)
+            if (coop) {
+                job_n = n_s;
+                if (n_s > 0) {
+                    SampleJobs<R>& J = s_jobs[threadIdx.x >> 5];
+                    J.x[lane] = x;
+                    J.y[lane] = y;
+                    J.z[lane] = z;
+                    J.cell[lane] = cy | (cz << 16);
+                    J.ox[lane] = ox;
+                    J.oy[lane] = oy;
+                    J.oz[lane] = oz;
+                    J.t[lane] = t;
+                    J.v[lane] = vg;
+                    J.k0[lane] = k_lo;
+                    J.sign[lane] = sign;
+                }
+            } else {
+                for (int k = k_lo; k < k_end; ++k) place_sample(k, x, y, z, ox, oy, oz, t, vg, sign, cy, cz);
             }
-            R nox = sx, noy = sy, noz = sz;
-            if constexpr (GEOM != LE_MC_GEOM_BULK) {
-                // x walls: Lambertian about +-x, or mirror
-                const R wox = diffuse ? ((kind == HIT_XLO) ? mu : -mu) : -ox;
-                const R woy = diffuse ? a : oy;
-                const R woz = diffuse ? b : oz;
-                if constexpr (POROUS) {
-                    // pore wall: normal from the axis to the hit point
-                    const R ny = (y - half) / rad, nz = (z - half) / rad;
-                    const R dn = oy * ny + oz * nz;
-                    const R cox = diffuse ? a : ox;
-                    const R coy = diffuse ? (mu * ny - b * nz) : (oy - R(2) * dn * ny);
-                    const R coz = diffuse ? (mu * nz + b * ny) : (oz - R(2) * dn * nz);
-                    const bool cyl = kind == HIT_CYL;
-                    nox = scat ? sx : (periodic ? ox : (cyl ? cox : wox));
-                    noy = scat ? sy : (periodic ? oy : (cyl ? coy : woy));
-                    noz = scat ? sz : (periodic ? oz : (cyl ? coz : woz));
-                    // periodic unit-cell face: re-insert on the opposite face
-                    const bool yhi = periodic && kind == HIT_YHI, ylo = periodic && kind == HIT_YLO;
-                    const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
-                    y = yhi ? R(0) : (ylo ? pitch : y);
-                    z = zhi ? R(0) : (zlo ? pitch : z);
-                    // unit-cell indices wrapped into the periodic domain
-                    cy = yhi ? (cy + 1 == P.cells_y ? 0 : cy + 1) : (ylo ? (cy == 0 ? P.cells_y - 1 : cy - 1) : cy);
-                    cz = zhi ? (cz + 1 == P.cells_z ? 0 : cz + 1) : (zlo ? (cz == 0 ? P.cells_z - 1 : cz - 1) : cz);
+        }
+        if constexpr (PROFILE) {
+            // time and x-displacement spent in each bin along x (slab)
+            const int nb = P.n_bins_x;
+            const R dx = L / (R)nb;
+            const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
+            const size_t stride = (size_t)nb + 1;
+            double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
+            double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
+            double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
+            double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
+            const R lo = fmin(x, x_new), hi = fmax(x, x_new);
+            int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
+            k0 = min(max(k0, 0), nb - 1);
+            k1 = min(max(k1, 0), nb - 1);
+            const double s = (double)sign;
+            if (ox == R(0)) {
+                atomicAdd(&Td[k0], s * (double)(seg / vg));
+            } else {
+                const R w = R(1) / (vg * fabs(ox));  // time per unit x
+                const R qs = ox > R(0) ? R(1) : R(-1);
+                if (k0 == k1) {
+                    const R len = hi - lo;
+                    atomicAdd(&Td[k0], s * (double)(len * w));
+                    atomicAdd(&qd[k0], s * (double)(len * qs));
                 } else {
-                    nox = scat ? sx : wox;
-                    noy = scat ? sy : woy;
-                    noz = scat ? sz : woz;
-                }
-            }
-            ox = nox;
-            oy = noy;
-            oz = noz;
-            n_scat += scat ? 1u : 0u;
-            n_wall += on_wall ? 1u : 0u;
-            n_per += periodic ? 1u : 0u;
-            if constexpr (HJ) {  // flux split by scattering index
-                if (P.n_hj > 0 && scat) {
-                    if (n_scat - 1u < (uint32_t)P.n_hj) {
-                        atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
-                        atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
+                    const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
+                    const R lb = hi - (R)k1 * dx;        // partial last bin
+                    atomicAdd(&Td[k0], s * (double)(la * w));
+                    atomicAdd(&qd[k0], s * (double)(la * qs));
+                    atomicAdd(&Td[k1], s * (double)(lb * w));
+                    atomicAdd(&qd[k1], s * (double)(lb * qs));
+                    if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
+                        atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
+                        atomicAdd(&Tr[k1], -s * (double)(dx * w));
+                        atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
+                        atomicAdd(&qr[k1], -s * (double)(dx * qs));
                     }
-                    hrun = R(0);
                 }
             }
-            // step VI and truncation
-            if (absorbed) { fate = FATE_ABSORBED; alive = false; }
-            else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
-            else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
-            else if (col_cap && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
-            else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
-            if (!alive) pending = true;
+        }
+        const R dL = AXIS_X ? (x_new - x) : oz * seg;
+        Lacc += dL;
+        if constexpr (HJ) hrun += dL;
+
+        // steps IVa / IVb.  Every lane evaluates the same straight-line code
+        // and keeps its own outcome through selects, so walls and relaxation
+        // events do not split the warp.
+        x = x_new;
+        if constexpr (POROUS) {
+            y += oy * seg;
+            z += oz * seg;
+        }
+        if constexpr (TRANSIENT) t = t_b;
+        ++n_seg;
+        const bool scat = !hit;
+        int wall = -1;
+        if constexpr (DIFF) {
+            wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
+        } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
+            if constexpr (POROUS) wall = (kind == HIT_CYL) ? P.pore_wall : wall;
+            wall = hit ? wall : -1;
+            // partially specular wall: specular with probability p, decided by
+            // the flight's second uniform (a relaxation's mode draw otherwise)
+            if (any_partial && wall == LE_MC_WALL_PARTIAL) {
+                const R p = (kind == HIT_XLO) ? K.spec_lo : ((kind == HIT_XHI) ? K.spec_hi : K.spec_pore);
+                wall = (M::uniform(r.y) < p) ? (int)LE_MC_WALL_SPECULAR : (int)LE_MC_WALL_DIFFUSE;
+            }
+        }
+        const bool on_wall = wall >= 0;
+        const bool absorbed = wall == LE_MC_WALL_BLACK;
+        const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
+        const bool periodic = hit && !on_wall;
+        // Eq. 2 redraw (kept only on a relaxation event)
+        if constexpr (FUSED) {
+            const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
+            const uint4 e = s_fused[(uint32_t)(mm >> 32)];
+            const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
+            lam = scat ? lam_new : lam;
+        } else {
+            const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+            const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
+            lam = scat ? lam_new : lam;
+            vg = scat ? vg_new : vg;
+        }
+        // fresh direction: isotropic (relaxation) or Lambertian (diffuse wall)
+        const R u2 = M::uniform(r.z);
+        R sn, cs;
+        M::sincos_2pi(M::uniform(r.w), &sn, &cs);
+        const R mu = scat ? (R(2) * u2 - R(1)) : M::sqrt_(u2);
+        const R st = M::sqrt_(fmax(R(0), R(1) - mu * mu));
+        const R a = st * cs, b = st * sn;
+        // direction after a relaxation: isotropic (a, b, mu) about z, or the
+        // Henyey-Greenstein law of mean cosine g about the incoming direction,
+        // its cosine from the inverted CDF and its azimuth in the
+        // orthonormal frame of Duff et al. (JCGT 2017) built on (ox, oy, oz)
+        R sx = a, sy = b, sz = mu;
+        if (aniso && scat) {
+            const R q = M::div(R(1) - hg * hg, R(1) - hg + R(2) * hg * u2);
+            R mh = M::div(R(1) + hg * hg - q * q, R(2) * hg);
+            mh = fmin(fmax(mh, R(-1)), R(1));
+            const R sh = M::sqrt_(fmax(R(0), R(1) - mh * mh));
+            const R sg = oz >= R(0) ? R(1) : R(-1);
+            const R fa = M::div(R(-1), sg + oz);
+            const R fb = ox * oy * fa;
+            sx = mh * ox + sh * (cs * (R(1) + sg * ox * ox * fa) + sn * fb);
+            sy = mh * oy + sh * (cs * (sg * fb) + sn * (sg + oy * oy * fa));
+            sz = mh * oz + sh * (cs * (-sg * ox) + sn * (-oy));
+        }
+        R nox = sx, noy = sy, noz = sz;
+        if constexpr (GEOM != LE_MC_GEOM_BULK) {
+            // x walls: Lambertian about +-x, or mirror
+            const R wox = diffuse ? ((kind == HIT_XLO) ? mu : -mu) : -ox;
+            const R woy = diffuse ? a : oy;
+            const R woz = diffuse ? b : oz;
+            if constexpr (POROUS) {
+                // pore wall: normal from the axis to the hit point
+                const R ny = (y - half) / rad, nz = (z - half) / rad;
+                const R dn = oy * ny + oz * nz;
+                const R cox = diffuse ? a : ox;
+                const R coy = diffuse ? (mu * ny - b * nz) : (oy - R(2) * dn * ny);
+                const R coz = diffuse ? (mu * nz + b * ny) : (oz - R(2) * dn * nz);
+                const bool cyl = kind == HIT_CYL;
+                nox = scat ? sx : (periodic ? ox : (cyl ? cox : wox));
+                noy = scat ? sy : (periodic ? oy : (cyl ? coy : woy));
+                noz = scat ? sz : (periodic ? oz : (cyl ? coz : woz));
+                // periodic unit-cell face: re-insert on the opposite face
+                const bool yhi = periodic && kind == HIT_YHI, ylo = periodic && kind == HIT_YLO;
+                const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
+                y = yhi ? R(0) : (ylo ? pitch : y);
+                z = zhi ? R(0) : (zlo ? pitch : z);
+                // unit-cell indices wrapped into the periodic domain
+                cy = yhi ? (cy + 1 == P.cells_y ? 0 : cy + 1) : (ylo ? (cy == 0 ? P.cells_y - 1 : cy - 1) : cy);
+                cz = zhi ? (cz + 1 == P.cells_z ? 0 : cz + 1) : (zlo ? (cz == 0 ? P.cells_z - 1 : cz - 1) : cz);
+            } else {
+                nox = scat ? sx : wox;
+                noy = scat ? sy : woy;
+                noz = scat ? sz : woz;
+            }
+        }
+        ox = nox;
+        oy = noy;
+        oz = noz;
+        n_scat += scat ? 1u : 0u;
+        n_wall += on_wall ? 1u : 0u;
+        n_per += periodic ? 1u : 0u;
+        if constexpr (HJ) {  // flux split by scattering index
+            if (P.n_hj > 0 && scat) {
+                if (n_scat - 1u < (uint32_t)P.n_hj) {
+                    atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
+                    atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
+                }
+                hrun = R(0);
+            }
+        }
+        // step VI and truncation
+        if (absorbed) { fate = FATE_ABSORBED; alive = false; }
+        else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
+        else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
+        else if (col_cap && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
+        else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
+        if (!alive) pending = true;
     };
 
     // Rounds of precomputed random words, for a warp tracing one extreme
@@ -819,42 +814,42 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // of the queue broke that and is not done.)
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
     auto finish = [&]() {
-            if constexpr (BATCH) {
-                if (bidx != cur_b) {
-                    flush_lane(cur_b);
-                    cur_b = bidx;
-                }
+        if constexpr (BATCH) {
+            if (bidx != cur_b) {
+                flush_lane(cur_b);
+                cur_b = bidx;
             }
-            const R sL = (R)sign * Lacc;
-            acc_sL.add(sL);
-            acc_sL2.add(sL * sL);
-            c_part += 1;
-            c_seg += n_seg;
-            c_scat += n_scat;
-            c_wall += n_wall;
-            c_per += n_per;
-            c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
-            c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
-            if (HJ && P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
-                atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
-                atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
-            }
-            if (P.records) {
-                le_mc_particle rec;
-                rec.sign = (int8_t)sign;
-                rec.fate = (int8_t)(fate == FATE_MAX_EVENTS ? P.events_fate : fate);  // a folded collision cap
-                rec.pad = 0;
-                rec.n_seg = n_seg;
-                rec.n_scat = n_scat;
-                rec.n_wall = n_wall;
-                rec.n_periodic = n_per;
-                rec.mode0 = mode0;
-                rec.L_axis = (double)Lacc;
-                rec.x0 = (double)x0;
-                rec.t0 = (double)t0;
-                P.records[pid - P.first] = rec;
-            }
-            pending = false;
+        }
+        const R sL = (R)sign * Lacc;
+        acc_sL.add(sL);
+        acc_sL2.add(sL * sL);
+        c_part += 1;
+        c_seg += n_seg;
+        c_scat += n_scat;
+        c_wall += n_wall;
+        c_per += n_per;
+        c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
+        c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
+        if (HJ && P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
+            atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
+            atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
+        }
+        if (P.records) {
+            le_mc_particle rec;
+            rec.sign = (int8_t)sign;
+            rec.fate = (int8_t)(fate == FATE_MAX_EVENTS ? P.events_fate : fate);  // a folded collision cap
+            rec.pad = 0;
+            rec.n_seg = n_seg;
+            rec.n_scat = n_scat;
+            rec.n_wall = n_wall;
+            rec.n_periodic = n_per;
+            rec.mode0 = mode0;
+            rec.L_axis = (double)Lacc;
+            rec.x0 = (double)x0;
+            rec.t0 = (double)t0;
+            P.records[pid - P.first] = rec;
+        }
+        pending = false;
     };
 
     auto assisted = [&]() {
