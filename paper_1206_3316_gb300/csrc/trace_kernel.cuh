@@ -797,21 +797,6 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         if (!alive) pending = true;
     };
 
-    // Rounds of precomputed random words, for a warp tracing one extreme
-    // particle (phase A): such a warp runs at the latency of one lane, so its
-    // idle lanes compute the particle's next random words (the counters are
-    // known in advance) into the emission buffer's storage, and the particle
-    // traces a round of segments without Philox on its critical path.  Each
-    // segment uses the same words as otherwise.
-    //
-    // Reproducibility: the rounds inline a second copy of the segment code,
-    // whose FP32 operations the compiler may contract differently from the
-    // main loop's copy, so a particle must always be traced by the same copy.
-    // The set of extreme particles is fixed by their emission modes (and is
-    // used all or nothing, see n_ext), so which copy traces a particle never
-    // depends on timing, and results are bit-identical across runs and
-    // launch shapes.  (Assisting whichever lanes happen to be last at the end
-    // of the queue broke that and is not done.)
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
     auto finish = [&]() {
         if constexpr (BATCH) {
@@ -852,6 +837,21 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         pending = false;
     };
 
+    // Rounds of precomputed random words, for a warp tracing one extreme
+    // particle (phase A): such a warp runs at the latency of one lane, so its
+    // idle lanes compute the particle's next random words (the counters are
+    // known in advance) into the emission buffer's storage, and the particle
+    // traces a round of segments without Philox on its critical path.  Each
+    // segment uses the same words as otherwise.
+    //
+    // Reproducibility: the rounds inline a second copy of the segment code,
+    // whose FP32 operations the compiler may contract differently from the
+    // main loop's copy, so a particle must always be traced by the same copy.
+    // The set of extreme particles is fixed by their emission modes (and is
+    // used all or nothing, see n_ext), so which copy traces a particle never
+    // depends on timing, and results are bit-identical across runs and
+    // launch shapes.  (Assisting whichever lanes happen to be last at the end
+    // of the queue broke that and is not done.)
     auto assisted = [&]() {
         uint4* const words = reinterpret_cast<uint4*>(&buf);
         for (;;) {
@@ -877,6 +877,83 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         }
     };
 
+    // step I for queue position `pos` (a particle id of the run, or a position
+    // in the concatenated instances of a batch) into emission-buffer slot
+    // base + popc(before): the slot is formed after the emission, which keeps
+    // it out of the registers live across emit_particle
+    auto emit_to = [&](uint32_t pos, int base, unsigned before) {
+        uint32_t id = pos, eb = 0;
+        EmitCtx<R> ctx;
+        if constexpr (BATCH) {
+            eb = batch_find(P.offsets, (uint32_t)P.n_instances, pos);
+            id = (uint32_t)(pos - P.offsets[eb]);
+            ctx = batch_ctx<R>(P.instances[eb]);
+        } else {
+            id = P.first + pos;
+            ctx = run_ctx<R>(P);
+        }
+        R ex, ey, ez, eox, eoy, eoz, et;
+        uint32_t em, ecy, ecz;
+        int es;
+        if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex, ey,
+                                         ez, eox, eoy, eoz, et, em, es, ecy, ecz))
+            flags |= FLAG_REJECTION_EXHAUSTED;
+        const int slot = base + __popc(before);
+        buf.x[slot] = ex;
+        buf.ox[slot] = eox;
+        buf.oy[slot] = eoy;
+        buf.oz[slot] = eoz;
+        buf.pid[slot] = id;
+        buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
+        if constexpr (POROUS) {
+            buf.y.v[slot] = ey;
+            buf.z.v[slot] = ez;
+            buf.cell.v[slot] = ecy | (ecz << 16);
+        }
+        if constexpr (SRC == LE_MC_SRC_PULSE) buf.t.v[slot] = et;
+        if constexpr (BATCH) buf.inst.v[slot] = eb;
+    };
+
+    // start this lane's next particle from emission-buffer slot `slot`
+    auto take = [&](int slot) {
+        x = buf.x[slot];
+        ox = buf.ox[slot];
+        oy = buf.oy[slot];
+        oz = buf.oz[slot];
+        pid = buf.pid[slot];
+        const uint32_t ms = buf.mode_sign[slot];
+        if constexpr (POROUS) {
+            y = buf.y.v[slot];
+            z = buf.z.v[slot];
+            const uint32_t cell = buf.cell.v[slot];
+            cy = (int)(cell & 0xFFFFu);
+            cz = (int)(cell >> 16);
+        }
+        if constexpr (SRC == LE_MC_SRC_PULSE) t = buf.t.v[slot];
+        if constexpr (SRC == LE_MC_SRC_INITIAL) t = R(0);
+        if constexpr (BATCH) {
+            bidx = buf.inst.v[slot];
+            const BatchInstance& bi = P.instances[bidx];
+            if constexpr (sizeof(R) == 4) Lp = bi.L32;
+            else Lp = bi.L;
+            instw = bi.inst_id;
+        }
+        mode0 = ms & 0x7FFFFFFFu;
+        sign = (ms >> 31) ? -1 : 1;
+        if constexpr (FUSED) {
+            lam = __uint_as_float(s_fused[mode0].z);
+        } else {
+            lam = s_props[2 * mode0];
+            vg = s_props[2 * mode0 + 1];
+        }
+        x0 = x;
+        t0 = t;
+        Lacc = 0;
+        hrun = 0;
+        n_seg = n_scat = n_wall = n_per = 0;
+        alive = true;
+    };
+
     // Phase A: extreme particles, one per otherwise empty warp, claimed first.
     if (n_ext > 0) {
         for (;;) {
@@ -884,77 +961,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             if (lane == 0) e = atomicAdd(P.long_count + 2, 1u);
             e = __shfl_sync(FULL, e, 0);
             if (e >= n_ext) break;
-            if (lane == 0) {
-                const uint32_t epos = P.long_list[e];
-                uint32_t id = epos, eb = 0;
-                EmitCtx<R> ctx;
-                if constexpr (BATCH) {
-                    eb = batch_find(P.offsets, (uint32_t)P.n_instances, epos);
-                    id = (uint32_t)(epos - P.offsets[eb]);
-                    ctx = batch_ctx<R>(P.instances[eb]);
-                } else {
-                    id = P.first + epos;
-                    ctx = run_ctx<R>(P);
-                }
-                R ex, ey, ez, eox, eoy, eoz, et;
-                uint32_t em, ecy, ecz;
-                int es;
-                if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex,
-                                                 ey, ez, eox, eoy, eoz, et, em, es, ecy, ecz))
-                    flags |= FLAG_REJECTION_EXHAUSTED;
-                const int slot = 0;
-                buf.x[slot] = ex;
-                buf.ox[slot] = eox;
-                buf.oy[slot] = eoy;
-                buf.oz[slot] = eoz;
-                buf.pid[slot] = id;
-                buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
-                if constexpr (POROUS) {
-                    buf.y.v[slot] = ey;
-                    buf.z.v[slot] = ez;
-                    buf.cell.v[slot] = ecy | (ecz << 16);
-                }
-                if constexpr (SRC == LE_MC_SRC_PULSE) buf.t.v[slot] = et;
-                if constexpr (BATCH) buf.inst.v[slot] = eb;
-                {  // lane 0 starts it from the buffer entry, as a refill would
-                    x = buf.x[slot];
-                    ox = buf.ox[slot];
-                    oy = buf.oy[slot];
-                    oz = buf.oz[slot];
-                    pid = buf.pid[slot];
-                    const uint32_t ms = buf.mode_sign[slot];
-                    if constexpr (POROUS) {
-                        y = buf.y.v[slot];
-                        z = buf.z.v[slot];
-                        const uint32_t cell = buf.cell.v[slot];
-                        cy = (int)(cell & 0xFFFFu);
-                        cz = (int)(cell >> 16);
-                    }
-                    if constexpr (SRC == LE_MC_SRC_PULSE) t = buf.t.v[slot];
-                    if constexpr (SRC == LE_MC_SRC_INITIAL) t = R(0);
-                    if constexpr (BATCH) {
-                        bidx = buf.inst.v[slot];
-                        const BatchInstance& bi = P.instances[bidx];
-                        if constexpr (sizeof(R) == 4) Lp = bi.L32;
-                        else Lp = bi.L;
-                        instw = bi.inst_id;
-                    }
-                    mode0 = ms & 0x7FFFFFFFu;
-                    sign = (ms >> 31) ? -1 : 1;
-                    if constexpr (FUSED) {
-                        lam = __uint_as_float(s_fused[mode0].z);
-                    } else {
-                        lam = s_props[2 * mode0];
-                        vg = s_props[2 * mode0 + 1];
-                    }
-                    x0 = x;
-                    t0 = t;
-                    Lacc = 0;
-                    hrun = 0;
-                    n_seg = n_scat = n_wall = n_per = 0;
-                    alive = true;
-                }
-
+            if (lane == 0) {  // lane 0 starts it from the buffer, as a refill would
+                emit_to(P.long_list[e], 0, 0u);
+                take(0);
             }
             __syncwarp();
             assisted();
@@ -999,82 +1008,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                     valid = !(P.long_list && ((P.long_bits[pos >> 5] >> (pos & 31u)) & 1u));
                 }
                 const unsigned vmask = __ballot_sync(FULL, valid);
-                if (valid) {
-                    uint32_t id = pos, eb = 0;
-                    EmitCtx<R> ctx;
-                    if constexpr (BATCH) {
-                        eb = batch_find(P.offsets, (uint32_t)P.n_instances, pos);
-                        id = (uint32_t)(pos - P.offsets[eb]);
-                        ctx = batch_ctx<R>(P.instances[eb]);
-                    } else {
-                        id = P.first + pos;
-                        ctx = run_ctx<R>(P);
-                    }
-                    R ex, ey, ez, eox, eoy, eoz, et;
-                    uint32_t em, ecy, ecz;
-                    int es;
-                    if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex, ey, ez, eox, eoy, eoz, et, em, es,
-                                                     ecy, ecz))
-                        flags |= FLAG_REJECTION_EXHAUSTED;
-                    const int slot = cnt + __popc(vmask & lanemask_lt);
-                    buf.x[slot] = ex;
-                    buf.ox[slot] = eox;
-                    buf.oy[slot] = eoy;
-                    buf.oz[slot] = eoz;
-                    buf.pid[slot] = id;
-                    buf.mode_sign[slot] = em | (es < 0 ? 0x80000000u : 0u);
-                    if constexpr (POROUS) {
-                        buf.y.v[slot] = ey;
-                        buf.z.v[slot] = ez;
-                        buf.cell.v[slot] = ecy | (ecz << 16);
-                    }
-                    if constexpr (SRC == LE_MC_SRC_PULSE) buf.t.v[slot] = et;
-                    if constexpr (BATCH) buf.inst.v[slot] = eb;
-                }
+                if (valid) emit_to(pos, cnt, vmask & lanemask_lt);
                 cnt += __popc(vmask);
                 __syncwarp();
             }
             if (!alive) {
                 const int rank = __popc(dead & lanemask_lt);
-                if (rank < cnt) {
-                    const int slot = cnt - 1 - rank;
-                    x = buf.x[slot];
-                    ox = buf.ox[slot];
-                    oy = buf.oy[slot];
-                    oz = buf.oz[slot];
-                    pid = buf.pid[slot];
-                    const uint32_t ms = buf.mode_sign[slot];
-                    if constexpr (POROUS) {
-                        y = buf.y.v[slot];
-                        z = buf.z.v[slot];
-                        const uint32_t cell = buf.cell.v[slot];
-                        cy = (int)(cell & 0xFFFFu);
-                        cz = (int)(cell >> 16);
-                    }
-                    if constexpr (SRC == LE_MC_SRC_PULSE) t = buf.t.v[slot];
-                    if constexpr (SRC == LE_MC_SRC_INITIAL) t = R(0);
-                    if constexpr (BATCH) {
-                        bidx = buf.inst.v[slot];
-                        const BatchInstance& bi = P.instances[bidx];
-                        if constexpr (sizeof(R) == 4) Lp = bi.L32;
-                        else Lp = bi.L;
-                        instw = bi.inst_id;
-                    }
-                    mode0 = ms & 0x7FFFFFFFu;
-                    sign = (ms >> 31) ? -1 : 1;
-                    if constexpr (FUSED) {
-                        lam = __uint_as_float(s_fused[mode0].z);
-                    } else {
-                        lam = s_props[2 * mode0];
-                        vg = s_props[2 * mode0 + 1];
-                    }
-                    x0 = x;
-                    t0 = t;
-                    Lacc = 0;
-                    hrun = 0;
-                    n_seg = n_scat = n_wall = n_per = 0;
-                    alive = true;
-                }
+                if (rank < cnt) take(cnt - 1 - rank);
             }
             cnt -= min(cnt, need);
             __syncwarp();
@@ -1128,10 +1068,6 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     }
 }
 
-// Long-first schedule, pass 1: flag the particles whose emission mode has a
-// mean free path above lam_cut (they make the longest trajectories: many
-// wall segments before their first relaxation event) and list them so the
-// trace kernel can serve them first.  Same random words as step I.
 // Kernel entry points.  Pored-film FP32 kernels are held to 64 registers (two
 // 512-thread blocks per SM) although that spills ~250 bytes per thread:
 // measured on GB300, the doubled occupancy outweighs the spills (steady pored
@@ -1159,6 +1095,12 @@ constexpr auto trace_entry()
         return trace_kernel<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
 }
 
+// Long-first schedule, pass 1: flag the particles whose emission mode has a
+// mean free path above lam_cut (they make the longest trajectories: many
+// wall segments before their first relaxation event) and list them so the
+// trace kernel can serve them first; those above kExtremeFactor x lam_cut go
+// to the extreme list (traced one per warp in phase A) while it has room.
+// Same random words as step I.
 template <typename R>
 __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ KernelArgs args)
 {
