@@ -281,11 +281,17 @@ LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out
  *                      thickness, so every slab holds the same solid volume):
  *                      the temperature history of a layer, as a
  *                      thermoreflectance-like transient reads it
+ *   GRID_T_SE, GRID_TX_SE : double, shaped as GRID_T and GRID_TX: standard
+ *                      errors of those values.  A particle is in at most one
+ *                      cell (one slab) at a sample time and all particles of
+ *                      the transient sources carry one sign, so a count n of
+ *                      N particles has the estimated variance
+ *                      N/(N-1) |n| (1 - |n|/N)
  * Errors: LE_MC_ERR_INVALID (array not produced by this run, capacity too
  * small), LE_MC_ERR_STATE, LE_MC_ERR_CUDA. */
 enum { LE_MC_ARRAY_T = 0, LE_MC_ARRAY_T_SE = 1, LE_MC_ARRAY_Q = 2, LE_MC_ARRAY_Q_SE = 3,
        LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7,
-       LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9 };
+       LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9, LE_MC_ARRAY_GRID_T_SE = 10, LE_MC_ARRAY_GRID_TX_SE = 11 };
 LE_MC_API le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity,
                               size_t* written);
 

@@ -47,6 +47,7 @@ def simulate(problem, stream=None, arrays=True, record_particles=False, launch=N
                         gx, gy, gz = run["grid"]
                         out["grid"] = le_mc_read_array(h, "grid").reshape(run["n_samples"], gz, gy, gx)
                         out["T_x"] = le_mc_read_array(h, "grid_Tx").reshape(run["n_samples"], gx)
+                        out["T_x_se"] = le_mc_read_array(h, "grid_Tx_se").reshape(run["n_samples"], gx)
                 if record_particles:
                     out["particles_rec"] = le_mc_read_array(h, "particles")
                 return out

@@ -583,10 +583,12 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
         bytes = h->grid_len * sizeof(int32_t);
         break;
     case LE_MC_ARRAY_GRID_T:
+    case LE_MC_ARRAY_GRID_T_SE:
         if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
         bytes = h->grid_len * sizeof(double);
         break;
     case LE_MC_ARRAY_GRID_TX:
+    case LE_MC_ARRAY_GRID_TX_SE:
         if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
         bytes = (size_t)r.n_samples * r.grid_nx * sizeof(double);
         break;
@@ -605,17 +607,22 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
     cudaError_t e = cudaSuccess;
     if (which == LE_MC_ARRAY_GRID) {
         e = cudaMemcpy(dst, h->dev + h->off_grid, bytes, cudaMemcpyDeviceToHost);
-    } else if (which == LE_MC_ARRAY_GRID_T || which == LE_MC_ARRAY_GRID_TX) {
+    } else if (which == LE_MC_ARRAY_GRID_T || which == LE_MC_ARRAY_GRID_TX || which == LE_MC_ARRAY_GRID_T_SE ||
+               which == LE_MC_ARRAY_GRID_TX_SE) {
         std::vector<int32_t> counts(h->grid_len);
         e = cudaMemcpy(counts.data(), h->dev + h->off_grid, h->grid_len * sizeof(int32_t), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) {
             le_mc_tallies t;
             memset(&t, 0, sizeof(t));
             normalize(&h->geo->desc, &r, h->mat->sums, h->sums, h->counters, &t);
-            if (which == LE_MC_ARRAY_GRID_T)
-                finalize_grid_t(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), static_cast<double*>(dst));
+            double* out = static_cast<double*>(dst);
+            const bool se = which == LE_MC_ARRAY_GRID_T_SE || which == LE_MC_ARRAY_GRID_TX_SE;
+            if (which == LE_MC_ARRAY_GRID_T || which == LE_MC_ARRAY_GRID_T_SE)
+                finalize_grid_t(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), se ? nullptr : out,
+                                se ? out : nullptr);
             else
-                finalize_grid_tx(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), static_cast<double*>(dst));
+                finalize_grid_tx(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), se ? nullptr : out,
+                                 se ? out : nullptr);
         }
     } else if (which == LE_MC_ARRAY_PARTICLES) {
         e = cudaMemcpy(dst, h->dev + h->off_records, bytes, cudaMemcpyDeviceToHost);

@@ -442,29 +442,48 @@ void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, con
     }
 }
 
+// Standard error of an Eq. 3 count n of N particles.  At a sample time a
+// particle is in at most one cell (and one x slab), and every particle of the
+// transient sources carries the same sign, so each particle adds 0 or its
+// sign to n: the unbiased estimate of the variance of that per-particle term,
+// times N, is N/(N-1) |n| (1 - |n|/N).
+static double count_se(double n, double N)
+{
+    if (N <= 1.0) return 0.0;
+    const double a = fabs(n);
+    const double v = a * (1.0 - a / N) * (N / (N - 1.0));
+    return v > 0.0 ? sqrt(v) : 0.0;
+}
+
 void finalize_grid_t(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
-                     const int32_t* grid, double* T)
+                     const int32_t* grid, double* T, double* T_se)
 {
     const double Dy = g->pitch * g->cells_y, Dz = g->pitch * g->cells_z;
     const double V_cell = (g->L / r->grid_nx) * (Dy / r->grid_ny) * (Dz / r->grid_nz);
     const double f = E_eff / (ms.C_tot * V_cell);
+    const double N = (double)r->n_particles;
     const size_t n = (size_t)r->n_samples * r->grid_nz * r->grid_ny * r->grid_nx;
-    for (size_t i = 0; i < n; ++i) T[i] = f * (double)grid[i];
+    for (size_t i = 0; i < n; ++i) {
+        if (T) T[i] = f * (double)grid[i];
+        if (T_se) T_se[i] = f * count_se((double)grid[i], N);
+    }
 }
 
 void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
-                      const int32_t* grid, double* Tx)
+                      const int32_t* grid, double* Tx, double* Tx_se)
 {
     const double pi = 3.141592653589793;
     const double solid = (g->pitch * g->pitch - pi * g->radius * g->radius) * g->cells_y * g->cells_z;
     const double f = E_eff / (ms.C_tot * solid * (g->L / r->grid_nx));
+    const double N = (double)r->n_particles;
     const size_t plane = (size_t)r->grid_nz * r->grid_ny;
     for (int k = 0; k < r->n_samples; ++k)
         for (int ix = 0; ix < r->grid_nx; ++ix) {
             long long c = 0;
             const int32_t* base = grid + (size_t)k * plane * r->grid_nx + ix;
             for (size_t j = 0; j < plane; ++j) c += base[j * r->grid_nx];
-            Tx[(size_t)k * r->grid_nx + ix] = f * (double)c;
+            if (Tx) Tx[(size_t)k * r->grid_nx + ix] = f * (double)c;
+            if (Tx_se) Tx_se[(size_t)k * r->grid_nx + ix] = f * count_se((double)c, N);
         }
 }
 

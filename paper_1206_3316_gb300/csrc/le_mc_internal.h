@@ -194,11 +194,12 @@ void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, con
                       const double* raw, double* T, double* T_se, double* q, double* q_se);
 void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, double* H, double* H_se);
 // Transient grids (Eq. 3): per-cell energy temperature, and the average over
-// the solid of each x slab; E_eff is the energy of one particle.
+// the solid of each x slab, with their standard errors (either output may be
+// null); E_eff is the energy of one particle.
 void finalize_grid_t(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
-                     const int32_t* grid, double* T);
+                     const int32_t* grid, double* T, double* T_se);
 void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
-                      const int32_t* grid, double* Tx);
+                      const int32_t* grid, double* Tx, double* Tx_se);
 double flux_scale(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
                   double* P_out, double* Vref_out, double* Vsolid_out);
 

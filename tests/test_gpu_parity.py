@@ -347,10 +347,46 @@ def test_grid_temperature_readback(P):
         g = p["geometry"]
         V = (g["L"] / 4) * (g["pitch"] * 6 / 6) * (g["pitch"] * 6 / 6)
         np.testing.assert_allclose(T, counts * t["E_eff"] / (t["C_tot"] * V), rtol=1e-12)
+        # standard errors: binomial variance of a single-sign count of N particles
+        N = p["run"]["n_particles"]
+        T_se = P.le_mc_read_array(h, "grid_T_se")
+        a = np.abs(counts.astype(np.float64))
+        np.testing.assert_allclose(T_se, np.sqrt(a * (1 - a / N) * N / (N - 1)) * t["E_eff"] / (t["C_tot"] * V),
+                                   rtol=1e-12)
+        Tx = P.le_mc_read_array(h, "grid_Tx").reshape(10, 4)
+        Tx_se = P.le_mc_read_array(h, "grid_Tx_se").reshape(10, 4)
+        slab = np.abs(counts.reshape(10, 6 * 6, 4).sum(axis=1).astype(np.float64))
+        hit = slab > 0
+        assert hit.sum() > 10 and np.all(Tx_se[~hit] == 0) and np.all(Tx_se[hit] > 0)
+        np.testing.assert_allclose(Tx_se[hit] / np.abs(Tx[hit]),
+                                   np.sqrt((1 - slab[hit] / N) * N / (N - 1) / slab[hit]), rtol=1e-12)
     finally:
         P.le_mc_destroy_run(h)
         P.le_mc_destroy_geometry(geo)
         P.le_mc_destroy_material(mat)
+
+
+def test_transient_standard_errors_match_seed_scatter(P):
+    # The reported standard error of a slab temperature is the scatter of that
+    # value over independent runs.  Three 100 nm slabs of the TTR-like film:
+    # the heated slab starts with every particle and the slabs trade them, so
+    # occupancies run between ~1/3 and ~1, where a binomial count variance
+    # N p (1 - p) and a Poisson one (N p) differ by up to tenfold.
+    R, n = 128, 100_000
+    runs = [P.simulate(W.ttr_film(n_particles=n, seed=0x7700 + s, nx=3, n_samples=20)) for s in range(R)]
+    Tx = np.stack([r["T_x"] for r in runs])
+    se = np.stack([r["T_x_se"] for r in runs])
+    counts = np.stack([r["grid"].reshape(20, 3) for r in runs]).astype(np.float64)
+    emp = Tx.var(axis=0, ddof=1)
+    rep = (se ** 2).mean(axis=0)
+    f = Tx[0][counts[0] != 0] / counts[0][counts[0] != 0]
+    poisson = (np.abs(counts).mean(axis=0)) * f.mean() ** 2
+    keep = rep > 0
+    ratio = emp[keep].sum() / rep[keep].sum()
+    print(f"\nseed scatter / reported variance {ratio:.3f}; / Poisson variance {emp[keep].sum() / poisson[keep].sum():.3f}")
+    # pooled over 60 cells of 127 degrees of freedom each: about 2 % (1 sigma)
+    assert abs(ratio - 1.0) < 0.1, ratio
+    assert emp[keep].sum() / poisson[keep].sum() < 0.8
 
 
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
