@@ -42,12 +42,13 @@ extern "C" {
 #define LE_MC_API
 #endif
 
-#define LE_MC_ABI_VERSION 2
+#define LE_MC_ABI_VERSION 3
 #define LE_MC_MAX_BRANCHES 4
 #define LE_MC_MAX_MODES 4096        /* mode tables live in shared memory       */
 #define LE_MC_MAX_BINS_X 256        /* slab profile bins                       */
 #define LE_MC_MAX_BATCH 64          /* batch groups for profile error bars     */
 #define LE_MC_MAX_HJ 128            /* per-scattering-index flux tallies       */
+#define LE_MC_MAX_MAP 64            /* steady map cells per axis               */
 
 typedef enum {
     LE_MC_OK = 0,
@@ -148,6 +149,13 @@ typedef struct le_mc_geometry_s* le_mc_geometry;
 
 /* Validates and stores the geometry.  Errors: LE_MC_ERR_INVALID. */
 LE_MC_API le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le_mc_geometry* out);
+
+/* Host-only: solid fraction of each cell of a map_ny x map_nz map over the
+ * (y, z) unit cell of a POROUS geometry (the cell minus its overlap with the
+ * pore's circle, exact), written to fraction[map_nz][map_ny].  These are the
+ * fractions that normalise the steady maps (LE_MC_ARRAY_MAP_SOLID).
+ * Errors: LE_MC_ERR_INVALID (not POROUS, sizes out of 1..LE_MC_MAX_MAP). */
+LE_MC_API le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32_t map_nz, double* fraction);
 LE_MC_API le_mc_status le_mc_destroy_geometry(le_mc_geometry g);
 
 /* ---- run: sources (step I), termination (step VI), estimators (step V) ---- */
@@ -184,7 +192,8 @@ typedef struct {
     uint32_t max_scatter;           /* terminate at this scattering event (0 = none) */
     uint32_t max_events;            /* terminate after this many segments (>= 1) */
     int32_t n_bins_x;               /* WALLS: T(x), q(x) profile bins (0 = off)   */
-    int32_t n_batch;                /* profile batch groups (particle id mod n_batch) */
+    int32_t n_batch;                /* profile and map batch groups (particle id
+                                     * mod n_batch)                              */
     int32_t grid_nx, grid_ny, grid_nz; /* PULSE: counting grid over L x domain   */
     int32_t n_samples;              /* PULSE: sample times (k + 1/2) sample_dt    */
     double t_final;                 /* PULSE: end of the simulation [s]          */
@@ -221,6 +230,12 @@ typedef struct {
                                      * faces not counted (0 = none); 1 follows
                                      * each particle over its first free path
                                      * only (the first-free-path estimate)     */
+    int32_t map_ny, map_nz;         /* POROUS + GRADIENT: steady maps over the
+                                     * (y, z) unit cell, integrated through the
+                                     * thickness (Eq. 4 per map cell), on
+                                     * map_ny x map_nz equal cells (0 = off;
+                                     * 1..LE_MC_MAX_MAP each); error bars from
+                                     * the n_batch groups                      */
 } le_mc_run_desc;
 
 typedef struct le_mc_run_s* le_mc_run_handle;
@@ -287,11 +302,24 @@ LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out
  *                      the transient sources carry one sign, so a count n of
  *                      N particles has the estimated variance
  *                      N/(N-1) |n| (1 - |n|/N)
+ *   MAP_T, MAP_T_SE   : double[map_nz][map_ny]  steady T - T_eq(z) over the
+ *                      solid of each map cell (time-integrated deviational
+ *                      energy over C_tot x solid volume; add the imposed
+ *                      linear T_eq(z) for the local temperature), and its
+ *                      batch-means standard error; NaN where a cell holds
+ *                      no solid
+ *   MAP_Q, MAP_Q_SE   : double[map_nz][map_ny]  local heat flux along z over
+ *                      the solid of each map cell [W/m^2] and its standard
+ *                      error; NaN where a cell holds no solid
+ *   MAP_SOLID         : double[map_nz][map_ny]  solid fraction of each map
+ *                      cell (exact, from the pore's circle)
  * Errors: LE_MC_ERR_INVALID (array not produced by this run, capacity too
  * small), LE_MC_ERR_STATE, LE_MC_ERR_CUDA. */
 enum { LE_MC_ARRAY_T = 0, LE_MC_ARRAY_T_SE = 1, LE_MC_ARRAY_Q = 2, LE_MC_ARRAY_Q_SE = 3,
        LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7,
-       LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9, LE_MC_ARRAY_GRID_T_SE = 10, LE_MC_ARRAY_GRID_TX_SE = 11 };
+       LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9, LE_MC_ARRAY_GRID_T_SE = 10, LE_MC_ARRAY_GRID_TX_SE = 11,
+       LE_MC_ARRAY_MAP_T = 12, LE_MC_ARRAY_MAP_T_SE = 13, LE_MC_ARRAY_MAP_Q = 14, LE_MC_ARRAY_MAP_Q_SE = 15,
+       LE_MC_ARRAY_MAP_SOLID = 16 };
 LE_MC_API le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity,
                               size_t* written);
 

@@ -90,6 +90,10 @@ typedef struct {
     double sample_dt;     /* transient sample spacing                      */
     int32_t n_threads;
     int32_t record_particles;
+    /* POROUS, GRADIENT: steady maps over the (y, z) unit cell, integrated
+     * through the thickness, map_ny x map_nz cells (0 = off); their error
+     * bars come from the n_batch groups */
+    int32_t map_ny, map_nz;
 } orc_problem;
 
 typedef struct {
@@ -324,17 +328,25 @@ typedef struct {
     double* h_sum;   /* [n_hj] */
     double* h_sum2;  /* [n_hj] */
     int64_t* grid;   /* [n_samples][nz][ny][nx] signed counts                */
+    double* mT_sum;  /* [n_batch][map_nz][map_ny] sum of s * time over the cell */
+    double* mq_sum;  /* [n_batch][map_nz][map_ny] sum of s * z-displacement    */
 } orc_tally;
 
 static void tally_free(orc_tally* t)
 {
     free(t->T_sum); free(t->q_sum); free(t->h_sum); free(t->h_sum2); free(t->grid);
+    free(t->mT_sum); free(t->mq_sum);
     memset(t, 0, sizeof(*t));
 }
 
 static size_t grid_cells(const orc_problem* p)
 {
     return (size_t)p->n_samples * p->grid_nz * p->grid_ny * p->grid_nx;
+}
+
+static size_t map_cells(const orc_problem* p)
+{
+    return (p->map_ny > 0 && p->map_nz > 0) ? (size_t)p->map_ny * p->map_nz : 0;
 }
 
 static int tally_alloc(const orc_problem* p, orc_tally* t)
@@ -354,6 +366,12 @@ static int tally_alloc(const orc_problem* p, orc_tally* t)
     if (p->n_samples > 0) {
         t->grid = calloc(grid_cells(p), sizeof(int64_t));
         if (!t->grid) return -1;
+    }
+    if (map_cells(p) > 0) {
+        size_t nm = map_cells(p) * (size_t)(p->n_batch > 0 ? p->n_batch : 1);
+        t->mT_sum = calloc(nm, sizeof(double));
+        t->mq_sum = calloc(nm, sizeof(double));
+        if (!t->mT_sum || !t->mq_sum) return -1;
     }
     return 0;
 }
@@ -547,6 +565,135 @@ static void tally_slab_bins(const orc_problem* p, const orc_mat* m, orc_tally* t
     }
 }
 
+/* Clip the parameter interval [*a, *b] of the line x0 + d t to lo <= x < hi
+ * (lo <= x <= hi when `last`, the top cell of the range). */
+static void clip_axis(double x0, double d, double lo, double hi, int last, double* a, double* b)
+{
+    if (d == 0.0) {
+        int inside = x0 >= lo && (last ? x0 <= hi : x0 < hi);
+        if (!inside) *b = *a - 1.0;
+        return;
+    }
+    double t1 = (lo - x0) / d, t2 = (hi - x0) / d;
+    if (t1 > t2) { double tmp = t1; t1 = t2; t2 = tmp; }
+    if (t1 > *a) *a = t1;
+    if (t2 < *b) *b = t2;
+}
+
+/* Steady maps (Eq. 4 per map cell): over the (y, z) unit cell, integrated
+ * through the thickness, a segment adds s * (the time it spends over the
+ * cell) to the cell's temperature sum and s * (its z displacement over the
+ * cell) to its flux sum.  The segment [0, seg] of the ray (y, z) + (oy, oz) t
+ * is clipped to each cell's y and z extents in turn; cells outside the
+ * segment's bounding box cannot meet it and are skipped. */
+static void tally_map(const orc_problem* p, const orc_mat* m, orc_tally* tl, uint64_t pid, const orc_state* s,
+                      double seg)
+{
+    const int ny = p->map_ny, nz = p->map_nz;
+    const double dy = p->pitch / ny, dz = p->pitch / nz;
+    const size_t cells = (size_t)ny * nz;
+    /* batch group of the particle pair (2i, 2i + 1): the gradient source
+     * gives even ids one sign and odd ids the other, so a group must hold
+     * pairs for its estimate to see both signs */
+    const int g = (int)((pid >> 1) % (uint64_t)(p->n_batch > 0 ? p->n_batch : 1));
+    double* T = tl->mT_sum + (size_t)g * cells;
+    double* q = tl->mq_sum + (size_t)g * cells;
+    const double y1 = s->y + s->oy * seg, z1 = s->z + s->oz * seg;
+    int j0 = (int)floor(fmin(s->y, y1) / dy), j1 = (int)floor(fmax(s->y, y1) / dy);
+    int k0 = (int)floor(fmin(s->z, z1) / dz), k1 = (int)floor(fmax(s->z, z1) / dz);
+    if (j0 < 0) j0 = 0;
+    if (k0 < 0) k0 = 0;
+    if (j1 > ny - 1) j1 = ny - 1;
+    if (k1 > nz - 1) k1 = nz - 1;
+    const double vg = m->v[s->mode];
+    for (int k = k0; k <= k1; ++k)
+        for (int j = j0; j <= j1; ++j) {
+            double a = 0.0, b = seg;
+            clip_axis(s->y, s->oy, j * dy, (j + 1) * dy, j == ny - 1, &a, &b);
+            clip_axis(s->z, s->oz, k * dz, (k + 1) * dz, k == nz - 1, &a, &b);
+            if (b <= a) continue;
+            T[(size_t)k * ny + j] += s->sign * ((b - a) / vg);
+            q[(size_t)k * ny + j] += s->sign * (s->oz * (b - a));
+        }
+}
+
+/* Solid area of the map cell [ya, yb] x [za, zb] of the unit cell: the cell
+ * minus its overlap with the pore disk (centre (c, c), radius r).  The overlap
+ * is the integral over y of the z-length shared by [za, zb] and the disk's
+ * chord; with y = c + r sin(theta) the chord half-length is r cos(theta) and
+ * the integrand is smooth between the angles where the chord's ends cross za
+ * or zb, so each such piece is integrated by 20-point Gauss-Legendre. */
+static double chord_overlap(double c, double r, double za, double zb, double th)
+{
+    const double h = r * cos(th);
+    double lo = fmax(za, c - h), hi = fmin(zb, c + h);
+    return hi > lo ? (hi - lo) * r * cos(th) : 0.0;
+}
+
+/* Positive nodes and weights of 20-point Gauss-Legendre quadrature on
+ * [-1, 1]: Newton's method on the Legendre polynomial P_20 (three-term
+ * recurrence), started from the Chebyshev-like guess cos(pi (i - 1/4) / 20.5). */
+static void gauss_legendre20(double* x, double* w)
+{
+    const int n = 20;
+    for (int i = 1; i <= n / 2; ++i) {
+        double z = cos(ORC_PI * (i - 0.25) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-16) break;
+        }
+        x[i - 1] = z;
+        w[i - 1] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static double map_cell_solid(double c, double r, double ya, double yb, double za, double zb)
+{
+    const double full = (yb - ya) * (zb - za);
+    if (r <= 0.0) return full;
+    double lo = fmax(ya, c - r), hi = fmin(yb, c + r);
+    if (hi <= lo) return full;
+    double t_lo = asin(fmax(-1.0, fmin(1.0, (lo - c) / r)));
+    double t_hi = asin(fmax(-1.0, fmin(1.0, (hi - c) / r)));
+    /* breakpoints: c + r cos(th) = zb or za, c - r cos(th) = za or zb */
+    double brk[10];
+    int nb = 0;
+    brk[nb++] = t_lo;
+    const double zs[2] = {za, zb};
+    for (int i = 0; i < 2; ++i) {
+        double w = fabs(zs[i] - c) / r;
+        if (w < 1.0) {
+            double a = acos(w);
+            if (a > t_lo && a < t_hi) brk[nb++] = a;
+            if (-a > t_lo && -a < t_hi) brk[nb++] = -a;
+        }
+    }
+    brk[nb++] = t_hi;
+    for (int i = 1; i < nb; ++i) /* insertion sort */
+        for (int j = i; j > 0 && brk[j] < brk[j - 1]; --j) { double t = brk[j]; brk[j] = brk[j - 1]; brk[j - 1] = t; }
+    double x20[10], w20[10];
+    gauss_legendre20(x20, w20);
+    double overlap = 0.0;
+    for (int i = 0; i + 1 < nb; ++i) {
+        double a = brk[i], b = brk[i + 1], mid = 0.5 * (a + b), half = 0.5 * (b - a);
+        if (half <= 0.0) continue;
+        double sum = 0.0;
+        for (int k = 0; k < 10; ++k)
+            sum += w20[k] * (chord_overlap(c, r, za, zb, mid - half * x20[k]) +
+                             chord_overlap(c, r, za, zb, mid + half * x20[k]));
+        overlap += half * sum;
+    }
+    return full - overlap;
+}
+
 static int grid_index(double v, double extent, int n)
 {
     int i = (int)floor(v / extent * n);
@@ -625,6 +772,7 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
         if (hit && kind == HIT_XLO) x_new = 0.0;
         if (hit && kind == HIT_XHI) x_new = p->L;
         if (p->n_bins_x > 0) tally_slab_bins(p, m, tl, pid, s.sign, xa, x_new, s.ox, dt_seg, s.mode);
+        if (map_cells(p) > 0) tally_map(p, m, tl, pid, &s, seg);
         double dL = axis_x ? (x_new - xa) : dz;
         L_axis += dL;
         h_run += dL;
@@ -766,6 +914,9 @@ static int validate(const orc_problem* p)
         (!(p->pitch > 0.0) || p->radius < 0.0 || 2.0 * p->radius >= p->pitch || p->cells_y < 1 || p->cells_z < 1))
         return -1;
     if (p->n_bins_x > 0 && p->geom_kind != ORC_GEOM_PLANES) return -1;
+    if (p->map_ny < 0 || p->map_nz < 0) return -1;
+    if (map_cells(p) > 0 && (p->geom_kind != ORC_GEOM_POROUS || p->src_kind != ORC_SRC_GRADIENT || p->n_batch < 1))
+        return -1;
     if (p->n_samples > 0 && (p->geom_kind != ORC_GEOM_POROUS || !(p->t_final > 0.0) || !(p->sample_dt > 0.0) ||
                              p->grid_nx < 1 || p->grid_ny < 1 || p->grid_nz < 1))
         return -1;
@@ -784,9 +935,15 @@ static int validate(const orc_problem* p)
  *   q_mean/q_se [n_bins_x]   slab heat flux per bin
  *   h_mean/h_se [n_hj]       flux contribution between scattering j and j+1
  *   grid_counts  [n_samples*nz*ny*nx] signed particle counts (Eq. 3)
- *   records [n_particles]    per-particle records                          */
+ *   records [n_particles]    per-particle records
+ *   maps [5][map_nz][map_ny] steady maps over the unit cell: T - T_eq(z)
+ *                            over the solid of each map cell, its standard
+ *                            error, the local z flux over that solid, its
+ *                            standard error, and the cell's solid fraction
+ *                            (NaN values where a cell holds no solid)     */
 int orc_run(const orc_problem* p, orc_result* res, double* T_mean, double* T_se, double* q_mean,
-            double* q_se, double* h_mean, double* h_se, int64_t* grid_counts, orc_particle* records)
+            double* q_se, double* h_mean, double* h_se, int64_t* grid_counts, orc_particle* records,
+            double* maps)
 {
     if (validate(p)) return -1;
     orc_mat m;
@@ -833,6 +990,10 @@ int orc_run(const orc_problem* p, orc_result* res, double* T_mean, double* T_se,
             for (int j = 0; j < p->n_hj; ++j) { tot.h_sum[j] += t->h_sum[j]; tot.h_sum2[j] += t->h_sum2[j]; }
             if (p->n_samples > 0)
                 for (size_t c = 0; c < grid_cells(p); ++c) tot.grid[c] += t->grid[c];
+            for (size_t c = 0; c < map_cells(p) * (size_t)(p->n_batch > 0 ? p->n_batch : 1); ++c) {
+                tot.mT_sum[c] += t->mT_sum[c];
+                tot.mq_sum[c] += t->mq_sum[c];
+            }
         }
     }
     if (rc == 0) {
@@ -929,6 +1090,44 @@ int orc_run(const orc_problem* p, orc_result* res, double* T_mean, double* T_se,
         }
         if (p->n_samples > 0 && grid_counts)
             memcpy(grid_counts, tot.grid, grid_cells(p) * sizeof(int64_t));
+        /* steady maps: batch means over the n_batch groups; a cell's values
+         * are per unit solid volume (solid area of the cell x thickness x
+         * number of unit cells) */
+        if (map_cells(p) > 0 && maps) {
+            const int ny = p->map_ny, nz = p->map_nz, B = p->n_batch;
+            const size_t cells = map_cells(p);
+            const double dy = p->pitch / ny, dz = p->pitch / nz, c0 = 0.5 * p->pitch;
+            for (int k = 0; k < nz; ++k)
+                for (int j = 0; j < ny; ++j) {
+                    const size_t i = (size_t)k * ny + j;
+                    const double area = map_cell_solid(c0, p->radius, j * dy, (j + 1) * dy, k * dz, (k + 1) * dz);
+                    const double V = area * p->L * p->cells_y * p->cells_z;
+                    double sT = 0, sT2 = 0, sq = 0, sq2 = 0, Tt = 0, qt = 0;
+                    for (int g = 0; g < B; ++g) {
+                        /* particles 2q + e (e = 0, 1) below N with q = g mod B */
+                        double ng = 0.0;
+                        for (uint64_t e = 0; e < 2; ++e) {
+                            uint64_t Q = N > e ? (N - e + 1) / 2 : 0;
+                            ng += (double)(Q / B + ((uint64_t)g < Q % B ? 1 : 0));
+                        }
+                        if (ng <= 0) ng = 1;
+                        double Tg = P / ng * tot.mT_sum[(size_t)g * cells + i] / (m.C_tot * V);
+                        double qg = P / ng * tot.mq_sum[(size_t)g * cells + i] / V;
+                        sT += Tg; sT2 += Tg * Tg; sq += qg; sq2 += qg * qg;
+                        Tt += tot.mT_sum[(size_t)g * cells + i];
+                        qt += tot.mq_sum[(size_t)g * cells + i];
+                    }
+                    double vT = B > 1 ? (sT2 - sT * sT / B) / (B - 1.0) : 0.0;
+                    double vq = B > 1 ? (sq2 - sq * sq / B) / (B - 1.0) : 0.0;
+                    /* a cell whose solid is below 1e-12 of its area counts as empty */
+                    const int solid = area > 1e-12 * dy * dz;
+                    maps[0 * cells + i] = solid ? P / Nd * Tt / (m.C_tot * V) : NAN;
+                    maps[1 * cells + i] = solid ? sqrt(fmax(vT, 0.0) / B) : NAN;
+                    maps[2 * cells + i] = solid ? P / Nd * qt / V : NAN;
+                    maps[3 * cells + i] = solid ? sqrt(fmax(vq, 0.0) / B) : NAN;
+                    maps[4 * cells + i] = solid ? area / (dy * dz) : 0.0;
+                }
+        }
     }
     for (int i = 0; i < nt; ++i) tally_free(&jobs[i].tally);
     tally_free(&tot);

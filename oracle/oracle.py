@@ -67,6 +67,7 @@ class Problem(C.Structure):
         ("n_hj", C.c_int32),
         ("t_final", C.c_double), ("sample_dt", C.c_double),
         ("n_threads", C.c_int32), ("record_particles", C.c_int32),
+        ("map_ny", C.c_int32), ("map_nz", C.c_int32),
     ]
 
 
@@ -111,7 +112,7 @@ _lib = None
 
 def _bind(handle):
     handle.orc_run.restype = C.c_int
-    handle.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 8
+    handle.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 9
     return handle
 
 
@@ -140,7 +141,7 @@ def lib():
     if _lib is None:
         _lib = C.CDLL(build())
         _lib.orc_run.restype = C.c_int
-        _lib.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 8
+        _lib.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 9
         _lib.orc_philox4x32_10.argtypes = [C.POINTER(C.c_uint32), C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         _lib.orc_material.restype = C.c_int
         _lib.orc_material.argtypes = [C.POINTER(Problem)] + [C.c_void_p] * 4 + [C.c_int]
@@ -200,6 +201,8 @@ def to_problem(prob, n_threads=None, record_particles=False):
     p.t_final, p.sample_dt = r.get("t_final", 0.0), r.get("sample_dt", 0.0)
     p.n_threads = n_threads if n_threads else (os.cpu_count() or 1)
     p.record_particles = 1 if record_particles else 0
+    my, mz = r.get("map", (0, 0))
+    p.map_ny, p.map_nz = int(my), int(mz)
     return p
 
 
@@ -216,12 +219,14 @@ def run(prob, n_threads=None, record_particles=False, library=None):
     ncell = p.n_samples * p.grid_nx * p.grid_ny * p.grid_nz if p.n_samples > 0 else 0
     grid = np.zeros(ncell, dtype=np.int64)
     recs = np.zeros(p.n_particles if record_particles else 0, dtype=PARTICLE_DTYPE)
+    nmap = p.map_ny * p.map_nz if p.map_ny > 0 and p.map_nz > 0 else 0
+    maps = np.zeros(5 * nmap)
 
     def ptr(a):
         return a.ctypes.data if a.size else None
 
     rc = L.orc_run(C.byref(p), C.byref(res), ptr(T_mean), ptr(T_se), ptr(q_mean), ptr(q_se),
-                   ptr(h_mean), ptr(h_se), ptr(grid), ptr(recs))
+                   ptr(h_mean), ptr(h_se), ptr(grid), ptr(recs), ptr(maps))
     if rc != 0:
         raise ValueError(f"oracle rejected the problem (rc={rc})")
     out = {f[0]: getattr(res, f[0]) for f in Result._fields_}
@@ -231,6 +236,9 @@ def run(prob, n_threads=None, record_particles=False, library=None):
         out.update(H=h_mean, H_se=h_se)
     if ncell:
         out["grid"] = grid.reshape(p.n_samples, p.grid_nz, p.grid_ny, p.grid_nx)
+    if nmap:
+        m = maps.reshape(5, p.map_nz, p.map_ny)
+        out.update(map_T=m[0], map_T_se=m[1], map_q=m[2], map_q_se=m[3], map_solid=m[4])
     if record_particles:
         out["particles_rec"] = recs
     return out

@@ -16,7 +16,7 @@ from ._binding import (  # noqa: F401
     le_mc_material_table, le_mc_philox, le_mc_read_array, le_mc_read_tallies, le_mc_run, le_mc_sample_modes,
     le_mc_wait, lib, material_desc, run_desc, LIB_PATH, le_mc_server_cancel, le_mc_server_create,
     le_mc_server_destroy, le_mc_server_poll, le_mc_server_stats, le_mc_server_submit, le_mc_server_wait_all,
-    le_mc_run_noalloc, NOALLOC_MAX_PARTICLES,
+    le_mc_run_noalloc, NOALLOC_MAX_PARTICLES, le_mc_map_solid,
 )
 
 
@@ -48,6 +48,10 @@ def simulate(problem, stream=None, arrays=True, record_particles=False, launch=N
                         out["grid"] = le_mc_read_array(h, "grid").reshape(run["n_samples"], gz, gy, gx)
                         out["T_x"] = le_mc_read_array(h, "grid_Tx").reshape(run["n_samples"], gx)
                         out["T_x_se"] = le_mc_read_array(h, "grid_Tx_se").reshape(run["n_samples"], gx)
+                    if tuple(run.get("map", (0, 0))) != (0, 0):
+                        my, mz = run["map"]
+                        for k in ("map_T", "map_T_se", "map_q", "map_q_se", "map_solid"):
+                            out[k] = le_mc_read_array(h, k).reshape(mz, my)
                 if record_particles:
                     out["particles_rec"] = le_mc_read_array(h, "particles")
                 return out

@@ -26,7 +26,8 @@ WALL = {"black": 0, "diffuse": 1, "specular": 2, "partial": 3}
 SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
 PREC = {"fp64": 0, "fp32": 1}
 ARRAY = {"T": 0, "T_se": 1, "q": 2, "q_se": 3, "H": 4, "H_se": 5, "grid": 6, "particles": 7,
-         "grid_T": 8, "grid_Tx": 9, "grid_T_se": 10, "grid_Tx_se": 11}
+         "grid_T": 8, "grid_Tx": 9, "grid_T_se": 10, "grid_Tx_se": 11,
+         "map_T": 12, "map_T_se": 13, "map_q": 14, "map_q_se": 15, "map_solid": 16}
 MAX_BRANCHES = 4
 
 
@@ -68,7 +69,7 @@ class RunDesc(C.Structure):
                 ("schedule", C.c_int32), ("refill_min", C.c_int32), ("long_mfp_cut", C.c_double),
                 ("chunk", C.c_int32), ("first_particle", C.c_uint32),
                 ("init_dT", C.c_double), ("init_x_lo", C.c_double), ("init_x_hi", C.c_double),
-                ("max_collisions", C.c_uint32)]
+                ("max_collisions", C.c_uint32), ("map_ny", C.c_int32), ("map_nz", C.c_int32)]
 
 
 class Tallies(C.Structure):
@@ -125,6 +126,7 @@ SIGNATURES = {
     "le_mc_material_table": (_STATUS, [C.POINTER(MaterialDesc), C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "le_mc_alias_table": (_STATUS, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "le_mc_map_solid": (_STATUS, [C.POINTER(GeometryDesc), C.c_int32, C.c_int32, C.c_void_p]),
     "le_mc_create_geometry": (_STATUS, [C.POINTER(GeometryDesc), C.POINTER(_H)]),
     "le_mc_destroy_geometry": (_STATUS, [_H]),
     "le_mc_run": (_STATUS, [_H, _H, C.POINTER(RunDesc), C.c_void_p, C.POINTER(_H)]),
@@ -255,6 +257,8 @@ def run_desc(src, run, launch=None):
     r.max_collisions = int(run.get("max_collisions", 0))
     r.init_dT = float(src.get("dT", 0.0)) if src["kind"] == "initial" else 0.0
     r.init_x_lo, r.init_x_hi = float(src.get("x_lo", 0.0)), float(src.get("x_hi", 0.0))
+    my, mz = run.get("map", (0, 0))
+    r.map_ny, r.map_nz = int(my), int(mz)
     return r
 
 
@@ -284,6 +288,12 @@ def le_mc_alias_table(weights):
     al = np.zeros(w.size, dtype=np.uint32)
     _check(lib.le_mc_alias_table(w.ctypes.data, w.size, thr.ctypes.data, al.ctypes.data), "le_mc_alias_table")
     return thr, al
+
+
+def le_mc_map_solid(desc, map_ny, map_nz):
+    out = np.zeros((int(map_nz), int(map_ny)))
+    _check(lib.le_mc_map_solid(C.byref(desc), int(map_ny), int(map_nz), out.ctypes.data), "le_mc_map_solid")
+    return out
 
 
 def le_mc_create_geometry(desc):

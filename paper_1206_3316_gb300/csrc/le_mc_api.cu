@@ -226,6 +226,18 @@ le_mc_status le_mc_alias_table(const double* weights, int32_t n, uint32_t* thres
     return LE_MC_OK;
 }
 
+le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32_t map_nz, double* fraction)
+{
+    const char* why = nullptr;
+    if (!g || !fraction) return fail(LE_MC_ERR_INVALID, "le_mc_map_solid: null pointer");
+    if (check_geometry(g, &why) != LE_MC_OK) return fail(LE_MC_ERR_INVALID, "le_mc_map_solid", why);
+    if (g->kind != LE_MC_GEOM_POROUS) return fail(LE_MC_ERR_INVALID, "le_mc_map_solid: needs the POROUS geometry");
+    if (map_ny < 1 || map_nz < 1 || map_ny > LE_MC_MAX_MAP || map_nz > LE_MC_MAX_MAP)
+        return fail(LE_MC_ERR_INVALID, "le_mc_map_solid: map_ny, map_nz out of 1..LE_MC_MAX_MAP");
+    map_solid_fractions(g->pitch, g->radius, map_ny, map_nz, fraction);
+    return LE_MC_OK;
+}
+
 le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_material* out)
 {
     if (!out) return fail(LE_MC_ERR_INVALID, "le_mc_create_material: out is null");
@@ -334,8 +346,11 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     h->stream = (cudaStream_t)stream;
     h->device = dev;
     const le_mc_run_desc& r = h->desc;
-    const bool profile = r.n_bins_x > 0;
-    h->prof_len = profile ? (size_t)4 * r.n_batch * (r.n_bins_x + 1) : 0;
+    // the PROFILE kernels tally slab profiles (PLANES) or steady maps (POROUS)
+    const bool has_map = r.map_ny > 0 && r.map_nz > 0;
+    const bool profile = r.n_bins_x > 0 || has_map;
+    h->prof_len = has_map ? (size_t)2 * r.n_batch * r.map_ny * r.map_nz
+                : profile ? (size_t)4 * r.n_batch * (r.n_bins_x + 1) : 0;
     h->hj_len = (size_t)2 * r.n_hj;
     h->grid_len = r.n_samples > 0 ? (size_t)r.n_samples * r.grid_nx * r.grid_ny * r.grid_nz : 0;
     size_t off = 0;
@@ -425,6 +440,8 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.max_collisions = r.max_collisions;
     P.n_bins_x = r.n_bins_x;
     P.n_batch = profile ? r.n_batch : 1;
+    P.map_ny = has_map ? r.map_ny : 0;
+    P.map_nz = has_map ? r.map_nz : 0;
     P.prof = reinterpret_cast<double*>(h->dev + h->off_prof);
     P.n_hj = r.n_hj;
     P.hj = reinterpret_cast<double*>(h->dev + h->off_hj);
@@ -461,10 +478,13 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     // 512 threads per block, or 256 when that keeps more warps resident (a
     // kernel instance whose registers leave room for only one 512-thread
     // block per SM)
+    // (the steady maps live in global memory only; slab profiles also have a
+    // shared-memory copy per block)
+    const int smem_prof = has_map ? 0 : (int)h->prof_len;
     auto shape_for = [&](int t, size_t* sm_bytes, int* resident) {
-        cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, (int)h->prof_len,
+        cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, smem_prof,
                                                 (int)h->hj_len, sm_bytes)
-                               : smem_trace_f64(G.kind, r.source, profile, m->n_modes, t, (int)h->prof_len,
+                               : smem_trace_f64(G.kind, r.source, profile, m->n_modes, t, smem_prof,
                                                 (int)h->hj_len, sm_bytes);
         if (err == cudaSuccess)
             err = fp32 ? occupancy_trace_for_f32(P, profile, t, *sm_bytes, resident)
@@ -592,6 +612,11 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
         if (h->grid_len == 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no grid");
         bytes = (size_t)r.n_samples * r.grid_nx * sizeof(double);
         break;
+    case LE_MC_ARRAY_MAP_T: case LE_MC_ARRAY_MAP_T_SE: case LE_MC_ARRAY_MAP_Q: case LE_MC_ARRAY_MAP_Q_SE:
+    case LE_MC_ARRAY_MAP_SOLID:
+        if (r.map_ny <= 0 || r.map_nz <= 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no maps");
+        bytes = (size_t)r.map_ny * r.map_nz * sizeof(double);
+        break;
     case LE_MC_ARRAY_PARTICLES:
         if (!r.record_particles) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run kept no records");
         bytes = (size_t)r.n_particles * sizeof(le_mc_particle);
@@ -623,6 +648,15 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
             else
                 finalize_grid_tx(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), se ? nullptr : out,
                                  se ? out : nullptr);
+        }
+    } else if (which >= LE_MC_ARRAY_MAP_T && which <= LE_MC_ARRAY_MAP_SOLID) {
+        const size_t cells = (size_t)r.map_ny * r.map_nz;
+        std::vector<double> raw(h->prof_len), out(5 * cells);
+        e = cudaMemcpy(raw.data(), h->dev + h->off_prof, raw.size() * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) {
+            finalize_map(&h->geo->desc, &r, h->mat->sums, raw.data(), out.data(), out.data() + cells,
+                         out.data() + 2 * cells, out.data() + 3 * cells, out.data() + 4 * cells);
+            memcpy(dst, out.data() + (size_t)(which - LE_MC_ARRAY_MAP_T) * cells, bytes);
         }
     } else if (which == LE_MC_ARRAY_PARTICLES) {
         e = cudaMemcpy(dst, h->dev + h->off_records, bytes, cudaMemcpyDeviceToHost);

@@ -206,8 +206,9 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "batches take WALLS or GRADIENT sources");
         if (runs[i].first_particle != 0)
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "batch instances start at particle 0");
-        if (runs[i].n_bins_x > 0 || runs[i].n_hj > 0 || runs[i].n_samples > 0 || runs[i].record_particles)
-            return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "profiles, H_j, grids and records are not batched");
+        if (runs[i].n_bins_x > 0 || runs[i].n_hj > 0 || runs[i].n_samples > 0 || runs[i].record_particles ||
+            runs[i].map_ny > 0)
+            return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "profiles, maps, H_j, grids and records are not batched");
         if (!same_family(geoms[i], geoms[0], runs[i], runs[0]))
             return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create",
                              "instances must share walls, source kind, precision, seed and caps");

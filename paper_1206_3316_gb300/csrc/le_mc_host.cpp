@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <limits>
 #include <vector>
 
 #include "le_mc_internal.h"
@@ -170,6 +171,10 @@ static void fill_one(const TraceParams& P, Consts<R>& c)
     c.gsy = P.gy > 0 ? (R)(P.gy / (P.pitch * P.cells_y)) : R(0);
     c.gsz = P.gz > 0 ? (R)(P.gz / (P.pitch * P.cells_z)) : R(0);
     c.g = (R)P.scatter_g;
+    c.map_dy = P.map_ny > 0 ? (R)(P.pitch / P.map_ny) : R(0);
+    c.map_dz = P.map_nz > 0 ? (R)(P.pitch / P.map_nz) : R(0);
+    c.map_iy = P.map_ny > 0 ? (R)(P.map_ny / P.pitch) : R(0);
+    c.map_iz = P.map_nz > 0 ? (R)(P.map_nz / P.pitch) : R(0);
 }
 
 void fill_consts(TraceParams& P)
@@ -283,6 +288,18 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
     if (r->n_bins_x < 0 || r->n_bins_x > LE_MC_MAX_BINS_X) { *why = "n_bins_x out of range"; return LE_MC_ERR_INVALID; }
     if (r->n_bins_x > 0) {
         if (r->source != LE_MC_SRC_WALLS) { *why = "profiles need the WALLS source"; return LE_MC_ERR_INVALID; }
+        if (r->n_batch < 1 || r->n_batch > LE_MC_MAX_BATCH) { *why = "n_batch out of 1..64"; return LE_MC_ERR_INVALID; }
+    }
+    if (r->map_ny < 0 || r->map_nz < 0 || r->map_ny > LE_MC_MAX_MAP || r->map_nz > LE_MC_MAX_MAP ||
+        (r->map_ny > 0) != (r->map_nz > 0)) {
+        *why = "map_ny, map_nz must both be 0, or both in 1..LE_MC_MAX_MAP";
+        return LE_MC_ERR_INVALID;
+    }
+    if (r->map_ny > 0) {
+        if (g->kind != LE_MC_GEOM_POROUS || r->source != LE_MC_SRC_GRADIENT) {
+            *why = "steady maps need the POROUS geometry and the GRADIENT source";
+            return LE_MC_ERR_INVALID;
+        }
         if (r->n_batch < 1 || r->n_batch > LE_MC_MAX_BATCH) { *why = "n_batch out of 1..64"; return LE_MC_ERR_INVALID; }
     }
     if (r->n_hj < 0 || r->n_hj > LE_MC_MAX_HJ) { *why = "n_hj out of range"; return LE_MC_ERR_INVALID; }
@@ -485,6 +502,94 @@ void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, con
             if (Tx) Tx[(size_t)k * r->grid_nx + ix] = f * (double)c;
             if (Tx_se) Tx_se[(size_t)k * r->grid_nx + ix] = f * count_se((double)c, N);
         }
+}
+
+// Area of the disk of radius r about the origin below y = a and z = b, from
+// the antiderivative of the chord half-length h(y) = sqrt(r^2 - y^2):
+// H(y) = (y h(y) + r^2 asin(y / r)) / 2.  Along y the z-extent below b is
+// 2h where h <= b, b + h where -h < b < h, and 0 where b <= -h.
+static double disk_corner_area(double a, double b, double r)
+{
+    if (a <= -r || b <= -r) return 0.0;
+    if (a > r) a = r;
+    auto H = [r](double y) {
+        y = y < -r ? -r : (y > r ? r : y);
+        const double h = sqrt(fmax(0.0, r * r - y * y));
+        return 0.5 * (y * h + r * r * asin(y / r));
+    };
+    auto piece = [&](double lo, double hi, bool full) {
+        lo = fmax(lo, -r);
+        hi = fmin(hi, a);
+        if (hi <= lo) return 0.0;
+        return full ? 2.0 * (H(hi) - H(lo)) : b * (hi - lo) + (H(hi) - H(lo));
+    };
+    if (b >= r) return piece(-r, r, true);
+    const double yb = sqrt(r * r - b * b);
+    if (b >= 0.0) return piece(-r, -yb, true) + piece(-yb, yb, false) + piece(yb, r, true);
+    return piece(-yb, yb, false);
+}
+
+// Solid area of the map cell [ya, yb] x [za, zb] of a unit cell whose pore
+// (radius r) is centred at (c, c): the cell minus its overlap with the disk,
+// by inclusion-exclusion of four corner areas.
+static double cell_solid_area(double c, double r, double ya, double yb, double za, double zb)
+{
+    const double full = (yb - ya) * (zb - za);
+    if (r <= 0.0) return full;
+    const double overlap = disk_corner_area(yb - c, zb - c, r) - disk_corner_area(ya - c, zb - c, r) -
+                           disk_corner_area(yb - c, za - c, r) + disk_corner_area(ya - c, za - c, r);
+    const double a = full - overlap;
+    // a cell whose solid is below 1e-12 of its area counts as empty
+    return a > 1e-12 * full ? a : 0.0;
+}
+
+void map_solid_fractions(double pitch, double radius, int ny, int nz, double* frac)
+{
+    const double dy = pitch / ny, dz = pitch / nz, c = 0.5 * pitch;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            frac[(size_t)k * ny + j] = cell_solid_area(c, radius, j * dy, (j + 1) * dy, k * dz, (k + 1) * dz) / (dy * dz);
+}
+
+void finalize_map(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, const double* raw,
+                  double* T, double* T_se, double* q, double* q_se, double* solid)
+{
+    const int ny = r->map_ny, nz = r->map_nz, B = r->n_batch;
+    const size_t cells = (size_t)ny * nz;
+    double P = 0.0;
+    flux_scale(g, r, ms, &P, nullptr, nullptr);
+    const unsigned long long N = r->n_particles;
+    const double Nd = N > 0 ? (double)N : 1.0;
+    std::vector<double> frac(cells);
+    map_solid_fractions(g->pitch, g->radius, ny, nz, frac.data());
+    const double cell_volume = (g->pitch / ny) * (g->pitch / nz) * g->L * g->cells_y * g->cells_z;
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (size_t i = 0; i < cells; ++i) {
+        const double V = frac[i] * cell_volume;  // solid volume over the map cell
+        double sT = 0, sT2 = 0, sq = 0, sq2 = 0, Tt = 0, qt = 0;
+        for (int b = 0; b < B; ++b) {
+            // group b holds the particle pairs (2q, 2q + 1) with q = b mod B
+            double ng = 0.0;
+            for (unsigned long long e = 0; e < 2; ++e) {
+                const unsigned long long Q = N > e ? (N - e + 1) / 2 : 0;
+                ng += (double)(Q / B + ((unsigned long long)b < Q % B ? 1 : 0));
+            }
+            if (ng <= 0) ng = 1;
+            const double rT = raw[(size_t)b * cells + i], rq = raw[((size_t)B + b) * cells + i];
+            const double Tb = P / ng * rT / (ms.C_tot * V), qb = P / ng * rq / V;
+            sT += Tb; sT2 += Tb * Tb; sq += qb; sq2 += qb * qb;
+            Tt += rT;
+            qt += rq;
+        }
+        const double vT = B > 1 ? (sT2 - sT * sT / B) / (B - 1.0) : 0.0;
+        const double vq = B > 1 ? (sq2 - sq * sq / B) / (B - 1.0) : 0.0;
+        const bool has = frac[i] > 0.0;
+        if (T) T[i] = has ? P / Nd * Tt / (ms.C_tot * V) : nan;
+        if (T_se) T_se[i] = has ? sqrt(fmax(vT, 0.0) / B) : nan;
+        if (q) q[i] = has ? P / Nd * qt / V : nan;
+        if (q_se) q_se[i] = has ? sqrt(fmax(vq, 0.0) / B) : nan;
+        if (solid) solid[i] = frac[i];
+    }
 }
 
 void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, double* H, double* H_se)

@@ -59,6 +59,7 @@ struct Consts {
     R t_final, sample_dt, lam_cut;
     R inv_dt, gsx, gsy, gsz;              // 1 / sample_dt; grid cells per metre along x, y, z
     R g;                                  // scattering mean cosine (0 isotropic)
+    R map_dy, map_dz, map_iy, map_iz;     // steady map cell sizes and cells per metre
 };
 
 constexpr int kBatchSmemMax = 512;
@@ -108,8 +109,11 @@ struct TraceParams {
     // run
     uint32_t n_particles, key0, key1, inst, max_scatter, max_events, max_collisions;
     // slab profile: [4][n_batch][n_bins_x + 1] (T direct, T difference,
-    // q direct, q difference), FP64
+    // q direct, q difference), FP64; or, in pored films, the steady maps
+    // [2][n_batch][map_nz][map_ny] (sum of s x time, sum of s x z
+    // displacement over each map cell)
     int32_t n_bins_x, n_batch;
+    int32_t map_ny, map_nz;
     double* prof;
     // flux by scattering index: [2][n_hj] (sum s h, sum h^2)
     int32_t n_hj;
@@ -200,6 +204,14 @@ void finalize_grid_t(const le_mc_geometry_desc* g, const le_mc_run_desc* r, cons
                      const int32_t* grid, double* T, double* T_se);
 void finalize_grid_tx(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, double E_eff,
                       const int32_t* grid, double* Tx, double* Tx_se);
+// Steady maps of a pored film from the raw [2][n_batch][map_nz][map_ny]
+// sums: T - T_eq(z) and the local z flux over the solid of each map cell,
+// batch-means standard errors, and the solid fraction (any output may be
+// null).
+void finalize_map(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms, const double* raw,
+                  double* T, double* T_se, double* q, double* q_se, double* solid);
+// Solid fraction of each of the ny x nz map cells of a unit cell ([nz][ny]).
+void map_solid_fractions(double pitch, double radius, int ny, int nz, double* frac);
 double flux_scale(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
                   double* P_out, double* Vref_out, double* Vsolid_out);
 

@@ -100,7 +100,8 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
         return set_error(LE_MC_ERR_INVALID, "le_mc_run_noalloc",
                          "n_particles above LE_MC_NOALLOC_MAX_PARTICLES (trace larger problems in pieces with "
                          "first_particle)");
-    if (r.source == LE_MC_SRC_PULSE || r.source == LE_MC_SRC_INITIAL || r.n_bins_x > 0 || r.n_hj > 0 || r.record_particles)
+    if (r.source == LE_MC_SRC_PULSE || r.source == LE_MC_SRC_INITIAL || r.n_bins_x > 0 || r.n_hj > 0 || r.record_particles ||
+        r.map_ny > 0)
         return set_error(LE_MC_ERR_INVALID, "le_mc_run_noalloc",
                          "only the scalar sums and counters are produced (no grid, profile, H_j or records)");
     int dev = 0;

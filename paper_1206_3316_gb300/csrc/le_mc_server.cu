@@ -306,7 +306,8 @@ le_mc_status le_mc_server_submit(le_mc_server s, const le_mc_material_desc* m, c
         return set_error(LE_MC_ERR_INVALID, "le_mc_server_submit", why);
     if (check_geometry(g, &why) != LE_MC_OK) return set_error(LE_MC_ERR_INVALID, "le_mc_server_submit", why);
     if (check_run(g, r, n_modes, &why) != LE_MC_OK) return set_error(LE_MC_ERR_INVALID, "le_mc_server_submit", why);
-    if (r->source == LE_MC_SRC_PULSE || r->source == LE_MC_SRC_INITIAL || r->n_bins_x > 0 || r->n_hj > 0 || r->record_particles || r->first_particle)
+    if (r->source == LE_MC_SRC_PULSE || r->source == LE_MC_SRC_INITIAL || r->n_bins_x > 0 || r->n_hj > 0 || r->record_particles || r->first_particle ||
+        r->map_ny > 0)
         return set_error(LE_MC_ERR_INVALID, "le_mc_server_submit",
                          "served requests are steady WALLS / GRADIENT runs without arrays");
     if (!(target_rel_err > 0.0)) return set_error(LE_MC_ERR_INVALID, "le_mc_server_submit", "target_rel_err must be > 0");

@@ -355,7 +355,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     if constexpr (TRANSIENT) off += (size_t)n_warps * sizeof(SampleJobs<R>);
     off = (off + 7) & ~(size_t)7;
     double* s_prof = reinterpret_cast<double*>(smem + off);
-    const int prof_len = PROFILE ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
+    // slab profile in shared memory (PLANES; the steady maps of POROUS
+    // kernels are added to global memory directly)
+    const int prof_len = (PROFILE && !POROUS) ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
     off += (size_t)prof_len * sizeof(double);
     double* s_hj = reinterpret_cast<double*>(smem + off);
     const int hj_len = 2 * P.n_hj;
@@ -633,7 +635,51 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 for (int k = k_lo; k < k_end; ++k) place_sample(k, x, y, z, ox, oy, oz, t, vg, sign, cy, cz);
             }
         }
-        if constexpr (PROFILE) {
+        if constexpr (PROFILE && POROUS) {
+            // steady maps (Eq. 4 per map cell): walk the cells of the (y, z)
+            // map that the segment crosses, adding s x (time over the cell)
+            // and s x (z displacement over the cell) to the run's FP64 map
+            // sums.  A segment crosses several cells, and reductions into
+            // global memory measured faster here than FP64 (or fixed-point
+            // integer) atomics on shared-memory copies.  Each crossing
+            // parameter comes from its own cell boundary, so the walk
+            // accumulates no drift.
+            const int ny = P.map_ny, nz = P.map_nz;
+            const size_t cells = (size_t)ny * nz;
+            // batch group of the particle pair (2i, 2i + 1), so that every
+            // group holds both signs of the gradient source
+            const int g = (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
+            double* mT = P.prof + (size_t)g * cells;
+            double* mQ = P.prof + ((size_t)P.n_batch + g) * cells;
+            int j = min(max((int)M::floor_(y * K.map_iy), 0), ny - 1);
+            int k = min(max((int)M::floor_(z * K.map_iz), 0), nz - 1);
+            const bool up_y = oy > R(0), up_z = oz > R(0);
+            const R ry = oy != R(0) ? M::div(R(1), oy) : R(0);
+            const R rz = oz != R(0) ? M::div(R(1), oz) : R(0);
+            const R wT = M::div((R)sign, vg), wQ = (R)sign * oz;
+            R t_in = R(0);
+            for (int it = 0; it <= ny + nz; ++it) {
+                const R ty = oy != R(0) ? ((R)(j + (up_y ? 1 : 0)) * K.map_dy - y) * ry : big;
+                const R tz = oz != R(0) ? ((R)(k + (up_z ? 1 : 0)) * K.map_dz - z) * rz : big;
+                const R t_out = fmin(fmin(ty, tz), seg);
+                const R d = t_out - t_in;
+                if (d > R(0)) {
+                    const size_t c = (size_t)k * ny + j;
+                    atomicAdd(&mT[c], (double)(d * wT));
+                    atomicAdd(&mQ[c], (double)(d * wQ));
+                }
+                if (t_out >= seg) break;
+                if (ty <= tz) {
+                    j += up_y ? 1 : -1;
+                    if (j < 0 || j >= ny) break;
+                } else {
+                    k += up_z ? 1 : -1;
+                    if (k < 0 || k >= nz) break;
+                }
+                t_in = t_out;
+            }
+        }
+        if constexpr (PROFILE && !POROUS) {
             // time and x-displacement spent in each bin along x (slab)
             const int nb = P.n_bins_x;
             const R dx = L / (R)nb;

@@ -43,7 +43,7 @@ def test_struct_layouts(P):
     for i, cls in enumerate((Bd.MaterialDesc, Bd.GeometryDesc, Bd.RunDesc, Bd.Tallies, Bd.Particle)):
         assert P.lib.le_mc_struct_size(i) == ctypes.sizeof(cls)
     assert Bd.PARTICLE_DTYPE.itemsize == ctypes.sizeof(Bd.Particle)
-    assert P.le_mc_abi_version() == 2
+    assert P.le_mc_abi_version() == 3
 
 
 def test_no_device_is_reported_not_faked(P):
@@ -136,3 +136,19 @@ def test_invalid_descriptors_rejected(P):
         P.le_mc_alias_table(np.zeros(4))
     with pytest.raises(P.LeMcError):
         P.le_mc_alias_table(np.array([1.0, -1.0]))
+
+
+def test_map_solid_fractions_match_oracle(P, oracle):
+    # two independent computations of each map cell's solid: the library's
+    # closed form (inclusion-exclusion of disk-corner areas) and the oracle's
+    # Gauss-Legendre quadrature of the pore's chords
+    for ny, nz, r in ((8, 8, 30e-9), (16, 16, 30e-9), (7, 5, 45e-9), (64, 64, 10e-9), (3, 1, 0.0)):
+        prob = W.porous_film(n_particles=64, precision="fp64", map=(ny, nz), radius=r)
+        lib = P.le_mc_map_solid(P.geometry_desc(prob["geometry"]), ny, nz)
+        np.testing.assert_allclose(lib, oracle.run(prob)["map_solid"], rtol=0, atol=1e-12)
+    g = P.geometry_desc(W.porous_film(n_particles=1)["geometry"])
+    for ny, nz in ((0, 4), (4, 65)):
+        with pytest.raises(P.LeMcError):
+            P.le_mc_map_solid(g, ny, nz)
+    with pytest.raises(P.LeMcError):
+        P.le_mc_map_solid(P.geometry_desc({"kind": "planes", "L": 1e-7}), 4, 4)

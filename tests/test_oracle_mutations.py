@@ -81,6 +81,12 @@ def _flight_shape_pin_ok(oracle, analytic, library):
     return abs(r["sum_sL2"] / n - lam ** 2) < 4.0 * np.sqrt(7.0 / n) * lam ** 2
 
 
+def _map_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_porous import map_symmetry_pvalues
+    r = oracle.run(W.porous_film(n_particles=200_000, precision="fp64", map=(8, 8), n_batch=16), library=library)
+    return min(map_symmetry_pvalues(r)) > 1e-3
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -117,6 +123,11 @@ MUTATIONS = [
      "double dist = m->Lambda[s.mode] * 2.0 * u[0];", _flight_shape_pin_ok),
     ("density of states missing a factor k", "double dos = k * k / (2.0 * ORC_PI * ORC_PI * vg);",
      "double dos = k / (2.0 * ORC_PI * ORC_PI * vg);", _film_pin_ok),
+    ("steady map cells indexed (y, z) instead of (z, y)",
+     "T[(size_t)k * ny + j] += s->sign * ((b - a) / vg);\n            q[(size_t)k * ny + j]",
+     "T[(size_t)j * nz + k] += s->sign * ((b - a) / vg);\n            q[(size_t)j * nz + k]", _map_pin_ok),
+    ("steady map time tallied without the particle's sign", "T[(size_t)k * ny + j] += s->sign * ((b - a) / vg);",
+     "T[(size_t)k * ny + j] += (b - a) / vg;", _map_pin_ok),
 ]
 
 

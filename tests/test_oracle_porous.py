@@ -6,7 +6,12 @@
   (which end segments and re-insert particles) change nothing;
 * pores only lower the conductivity (kappa_eff below the pore-free film);
 * Eq. 3 transient counts conserve energy exactly: every adiabatic-walled
-  particle alive at a sample time sits in exactly one grid cell.
+  particle alive at a sample time sits in exactly one grid cell;
+* steady maps over the unit cell: the solid fraction of each map cell
+  (exact total, point counts), the flux map partitions the scalar flux
+  exactly, the mirror symmetries of the unit cell (T odd in z about the
+  pore, even in y; the z flux even in both), and the flat maps of a film
+  without pores.
 """
 import numpy as np
 import pytest
@@ -188,3 +193,79 @@ def test_ttr_layer_energy_is_conserved(oracle):
     assert np.allclose(Tx.sum(axis=1) * L / nx, 1.0 * 30e-9, rtol=1e-12)
     # at the first sample (25 ps) the heat is still mostly in the top 60 nm
     assert Tx[0, -6:].sum() * L / nx > 0.8 * 30e-9
+
+
+def map_symmetry_pvalues(o):
+    """Chi-square p-values of the unit cell's mirror symmetries in the steady
+    maps: T(y, z) = -T(y, pitch - z) = T(pitch - y, z) and q(y, z) =
+    q(y, pitch - z) = q(pitch - y, z) (rows are z, columns y); each mirror
+    pair of cells counted once."""
+    from scipy import stats
+    out = []
+    for key, zsign in (("map_T", -1.0), ("map_q", 1.0)):
+        v, se = o[key], o[key + "_se"]
+        nz, ny = v.shape
+        for axis, sgn in ((0, zsign), (1, 1.0)):
+            flip, sflip = np.flip(v, axis), np.flip(se, axis)
+            d = (v - sgn * flip) / np.sqrt(se ** 2 + sflip ** 2)
+            half = d[: nz // 2, :] if axis == 0 else d[:, : ny // 2]
+            half = half[np.isfinite(half)]
+            out.append(stats.chi2.sf(np.sum(half ** 2), half.size))
+    return out
+
+
+@pytest.fixture(scope="module")
+def pored_maps(oracle):
+    return oracle.run(W.porous_film(n_particles=200_000, precision="fp64", map=(8, 8), n_batch=16))
+
+
+def test_map_solid_fractions(oracle):
+    pitch = 100e-9
+    for ny, nz, r in ((8, 8, 30e-9), (7, 5, 45e-9)):
+        o = oracle.run(W.porous_film(n_particles=64, precision="fp64", map=(ny, nz), radius=r))
+        f = o["map_solid"]
+        assert f.mean() == pytest.approx(1.0 - np.pi * (r / pitch) ** 2, abs=1e-13)
+        np.testing.assert_allclose(f, f[::-1, :], atol=1e-13)
+        np.testing.assert_allclose(f, f[:, ::-1], atol=1e-13)
+        # a lattice of 400 x 400 points per cell, counted outside the disk
+        m = 400
+        for k in range(nz):
+            z = (k + (np.arange(m) + 0.5) / m) * pitch / nz - 0.5 * pitch
+            for j in range(ny):
+                y = (j + (np.arange(m) + 0.5) / m) * pitch / ny - 0.5 * pitch
+                frac = np.mean(y[None, :] ** 2 + z[:, None] ** 2 >= r * r)
+                assert abs(frac - f[k, j]) < 3e-3, (ny, nz, k, j, frac, f[k, j])
+        # cells wholly inside the pore hold no solid and report no value
+        empty = f == 0.0
+        assert np.all(np.isnan(o["map_T"][empty])) and np.all(np.isfinite(o["map_T"][~empty]))
+
+
+def test_map_partitions_the_flux(pored_maps):
+    # the z displacements over the map cells add up to the whole displacement
+    o = pored_maps
+    V = o["map_solid"] * (100e-9 / 8) ** 2 * 300e-9
+    total = np.nansum(o["map_q"] * V)
+    assert total == pytest.approx(o["flux"] * (100e-9) ** 2 * 300e-9, rel=1e-12)
+
+
+def test_map_mirror_symmetries(pored_maps):
+    o = pored_maps
+    assert min(map_symmetry_pvalues(o)) > 1e-3, map_symmetry_pvalues(o)
+    # and the maps are not flat: heat piles up below the pore (T > 0 at
+    # z < pitch / 2 beside it) and the flux is lowest above and below it
+    T, q = o["map_T"], o["map_q"]
+    z = 5.0 * o["map_T_se"]
+    assert T[1, 3] > z[1, 3] and T[6, 3] < -z[6, 3]
+    assert q[0, 0] - q[0, 3] > 5.0 * np.hypot(o["map_q_se"][0, 0], o["map_q_se"][0, 3])
+
+
+def test_map_of_film_is_flat(oracle, analytic):
+    # no pores: no deviational temperature anywhere, the same flux everywhere
+    from scipy import stats
+    o = oracle.run(W.porous_film(n_particles=200_000, precision="fp64", map=(6, 6), radius=0.0, n_batch=16))
+    np.testing.assert_allclose(o["map_solid"], 1.0, rtol=1e-13)
+    zT = o["map_T"] / o["map_T_se"]
+    assert stats.chi2.sf(np.sum(zT ** 2), zT.size) > 1e-3
+    zq = (o["map_q"] - o["flux"]) / o["map_q_se"]
+    assert stats.chi2.sf(np.sum(zq ** 2), zq.size - 1) > 1e-3
+    assert abs(o["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 300e-9)) < 4.0 * o["kappa_se"]

@@ -115,18 +115,24 @@ def bulk(n_particles=1_000_000, seed=0x5EED_0000_0003, precision="fp64", max_sca
 
 def porous_film(n_particles=100_000_000, seed=0x5EED_0000_0004, precision="fp32",
                 thickness=300e-9, pitch=100e-9, radius=30e-9, max_scatter=40,
-                max_events=4096, material=None, n_hj=0):
+                max_events=4096, material=None, n_hj=0, map=None, n_batch=16):
     """Periodic porous film: film normal x (thickness 300 nm, diffuse faces),
     cylindrical pores along x on a square lattice in (y, z) (pitch 100 nm,
-    radius 30 nm, diffuse), 1 K across one period along z."""
+    radius 30 nm, diffuse), 1 K across one period along z.  ``map=(ny, nz)``
+    also asks for steady maps of T - T_eq(z) and the z flux over the unit cell
+    (error bars from ``n_batch`` groups)."""
+    run = _run(n_particles=n_particles, seed=seed, max_scatter=max_scatter,
+               max_events=max_events, precision=precision, n_hj=n_hj)
+    if map:
+        run["map"] = (int(map[0]), int(map[1]))
+        run["n_batch"] = int(n_batch)
     return {
         "material": copy.deepcopy(material or SILICON_LIKE),
         "geometry": {"kind": "porous", "L": float(thickness), "wall_lo": "diffuse",
                      "wall_hi": "diffuse", "pitch": float(pitch), "radius": float(radius),
                      "pore_wall": "diffuse", "cells_y": 1, "cells_z": 1},
         "source": {"kind": "gradient", "dTdz": -1.0 / float(pitch)},
-        "run": _run(n_particles=n_particles, seed=seed, max_scatter=max_scatter,
-                    max_events=max_events, precision=precision, n_hj=n_hj),
+        "run": run,
     }
 
 
