@@ -21,6 +21,9 @@ tests, none of which re-derives the oracle's own formulas):
   vanishing mean contribution after the first event.
 * Porous film: ray-cylinder intersections against brute-force marching,
   bounds and mirror symmetry; transient energy conservation (exact).
+* Steady maps over the unit cell: solid fractions against the exact total
+  and point counts; the flux map partitions the scalar flux; the unit
+  cell's mirror symmetries; flat maps for a film without pores.
   The porous-film conductivity itself has no closed form: parity unpinned
   beyond those checks.
 """
