@@ -339,7 +339,7 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--served-seconds", type=float, default=10.0,
+    ap.add_argument("--served-seconds", type=float, default=60.0,
                     help="length of the request stream of the served form (0 = skip)")
     args = ap.parse_args()
 
