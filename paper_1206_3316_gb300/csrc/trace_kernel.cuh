@@ -559,10 +559,12 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                     }
                 }
             }
-            if (oy > R(0)) { const R tf = M::div(pitch - y, oy); if (tf < d_b) { d_b = tf; kind = HIT_YHI; } }
-            else if (oy < R(0)) { const R tf = M::div(y, -oy); if (tf < d_b) { d_b = tf; kind = HIT_YLO; } }
-            if (oz > R(0)) { const R tf = M::div(pitch - z, oz); if (tf < d_b) { d_b = tf; kind = HIT_ZHI; } }
-            else if (oz < R(0)) { const R tf = M::div(z, -oz); if (tf < d_b) { d_b = tf; kind = HIT_ZLO; } }
+            // unit-cell faces ahead in y and z, one division each (a flight
+            // parallel to a face pair gets an infinite or NaN distance there)
+            const R tfy = M::div(oy > R(0) ? pitch - y : y, fabs(oy));
+            if (tfy < d_b) { d_b = tfy; kind = oy > R(0) ? HIT_YHI : HIT_YLO; }
+            const R tfz = M::div(oz > R(0) ? pitch - z : z, fabs(oz));
+            if (tfz < d_b) { d_b = tfz; kind = oz > R(0) ? HIT_ZHI : HIT_ZLO; }
         }
         bool hit = (kind != HIT_NONE) && (d_b <= ell);
         if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_WALLS && GEOM == LE_MC_GEOM_PLANES) {
@@ -810,9 +812,12 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 const bool zhi = periodic && kind == HIT_ZHI, zlo = periodic && kind == HIT_ZLO;
                 y = yhi ? R(0) : (ylo ? pitch : y);
                 z = zhi ? R(0) : (zlo ? pitch : z);
-                // unit-cell indices wrapped into the periodic domain
-                cy = yhi ? (cy + 1 == P.cells_y ? 0 : cy + 1) : (ylo ? (cy == 0 ? P.cells_y - 1 : cy - 1) : cy);
-                cz = zhi ? (cz + 1 == P.cells_z ? 0 : cz + 1) : (zlo ? (cz == 0 ? P.cells_z - 1 : cz - 1) : cz);
+                // unit-cell indices wrapped into the periodic domain (only the
+                // transient grid needs them)
+                if constexpr (TRANSIENT) {
+                    cy = yhi ? (cy + 1 == P.cells_y ? 0 : cy + 1) : (ylo ? (cy == 0 ? P.cells_y - 1 : cy - 1) : cy);
+                    cz = zhi ? (cz + 1 == P.cells_z ? 0 : cz + 1) : (zlo ? (cz == 0 ? P.cells_z - 1 : cz - 1) : cz);
+                }
             } else {
                 nox = scat ? sx : wox;
                 noy = scat ? sy : woy;
