@@ -31,6 +31,7 @@ import re
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -104,7 +105,7 @@ class ClockSampler:
     def __init__(self, device_index):
         self.device_index = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"le_mc_clocks_bench_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
@@ -230,7 +231,7 @@ def batched_measurement(P, torch, dev, stream, steps, launch):
     P.le_mc_destroy_material(mat)
 
     with P.Batch(probs) as bt:
-        cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.txt")
+        cache = os.path.join(ROOT, "_build", "autotune_cache.txt")
         os.makedirs(os.path.dirname(cache), exist_ok=True)
         cfg = bt.autotune(stream, cache_path=cache)
         cfg = dict(cfg, use_graph=True)
