@@ -641,11 +641,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             // steady maps (Eq. 4 per map cell): walk the cells of the (y, z)
             // map that the segment crosses, adding s x (time over the cell)
             // and s x (z displacement over the cell) to the run's FP64 map
-            // sums.  A segment crosses several cells, and reductions into
-            // global memory measured faster here than FP64 (or fixed-point
-            // integer) atomics on shared-memory copies.  Each crossing
-            // parameter comes from its own cell boundary, so the walk
-            // accumulates no drift.
+            // sums.  Reductions into global memory measured faster here than
+            // FP64 (or fixed-point integer) atomics on shared-memory copies.
+            // Each crossing parameter comes from its own cell boundary, so
+            // the walk accumulates no drift.
             const int ny = P.map_ny, nz = P.map_nz;
             const size_t cells = (size_t)ny * nz;
             // batch group of the particle pair (2i, 2i + 1), so that every
