@@ -72,3 +72,18 @@ def test_map_descriptors_rejected(P):
         with pytest.raises(P.LeMcError) as e:
             P.simulate(prob)
         assert e.value.status == 1
+
+
+def test_map_size_limits(P):
+    # one cell: the map is the whole unit cell, so its flux is the solid-averaged
+    # scalar flux; the largest map and batch count stay consistent too
+    g = P.simulate(W.porous_film(n_particles=200_000, map=(1, 1), n_batch=64))
+    solid = 1.0 - np.pi * 0.3 ** 2
+    assert g["map_solid"][0, 0] == pytest.approx(solid, rel=1e-12)
+    assert g["map_q"][0, 0] == pytest.approx(g["flux"] / solid, rel=1e-5)
+    big = P.simulate(W.porous_film(n_particles=200_000, map=(64, 64), n_batch=64))
+    V = big["map_solid"] * (100e-9 / 64) ** 2 * 300e-9
+    assert np.nansum(big["map_q"] * V) == pytest.approx(big["flux"] * (100e-9) ** 2 * 300e-9, rel=1e-5)
+    has = big["map_solid"] > 0
+    assert np.all(np.isfinite(big["map_T"][has])) and np.all(np.isnan(big["map_T"][~has]))
+    assert big["segments"] == g["segments"] and big["device_flags"] == 0
