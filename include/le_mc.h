@@ -50,6 +50,16 @@ extern "C" {
 #define LE_MC_MAX_HJ 128            /* per-scattering-index flux tallies       */
 #define LE_MC_MAX_MAP 64            /* steady map cells per axis               */
 
+/* Bits of le_mc_tallies.device_flags, set on the device (never a trap):
+ * REJECTION_EXHAUSTED: a rejection loop of step I (positions outside the
+ *   pores, pulse times >= 0) used all its 64 tries; that particle starts from
+ *   its last draw.
+ * BAD_LAUNCH: a trace kernel found a launch shape it cannot run (threads per
+ *   block not a multiple of 32, or above 512) and traced nothing; the entry
+ *   points validate shapes first, so this marks a library defect. */
+#define LE_MC_FLAG_REJECTION_EXHAUSTED 1u
+#define LE_MC_FLAG_BAD_LAUNCH 4u
+
 typedef enum {
     LE_MC_OK = 0,
     LE_MC_ERR_INVALID = 1, /* a descriptor field or argument is out of range     */
@@ -156,6 +166,13 @@ LE_MC_API le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le
  * fractions that normalise the steady maps (LE_MC_ARRAY_MAP_SOLID).
  * Errors: LE_MC_ERR_INVALID (not POROUS, sizes out of 1..LE_MC_MAX_MAP). */
 LE_MC_API le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32_t map_nz, double* fraction);
+
+/* Test hook for failure handling: the after-th next device allocation made by
+ * the library for a material, a run or a batch (0 = the very next one)
+ * reports out of memory, so the caller sees LE_MC_ERR_NOMEM from that call
+ * with nothing leaked; the hook then disarms itself.  after < 0 disarms it.
+ * Process-wide.  Errors: none. */
+LE_MC_API le_mc_status le_mc_test_fail_allocation(int32_t after);
 LE_MC_API le_mc_status le_mc_destroy_geometry(le_mc_geometry g);
 
 /* ---- run: sources (step I), termination (step VI), estimators (step V) ---- */
@@ -270,7 +287,7 @@ typedef struct {
     double kernel_ms;       /* device time of the trace kernel                    */
     double prepass_ms;      /* device time of the long-first classification pass  */
     uint32_t kernel_launches; /* kernels this run launched                        */
-    uint32_t device_flags;  /* device-side warning bits (0 = none)                */
+    uint32_t device_flags;  /* device-side status bits, LE_MC_FLAG_* (0 = none)  */
 } le_mc_tallies;
 
 /* Waits for the run, copies the tallies to the host and normalises them

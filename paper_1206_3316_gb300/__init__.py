@@ -16,7 +16,7 @@ from ._binding import (  # noqa: F401
     le_mc_material_table, le_mc_philox, le_mc_read_array, le_mc_read_tallies, le_mc_run, le_mc_sample_modes,
     le_mc_wait, lib, material_desc, run_desc, LIB_PATH, le_mc_server_cancel, le_mc_server_create,
     le_mc_server_destroy, le_mc_server_poll, le_mc_server_stats, le_mc_server_submit, le_mc_server_wait_all,
-    le_mc_run_noalloc, NOALLOC_MAX_PARTICLES, le_mc_map_solid,
+    le_mc_run_noalloc, NOALLOC_MAX_PARTICLES, le_mc_map_solid, le_mc_test_fail_allocation, DEVICE_FLAGS,
 )
 
 

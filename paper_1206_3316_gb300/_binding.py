@@ -127,6 +127,7 @@ SIGNATURES = {
                                        C.c_void_p, C.c_int32, C.POINTER(C.c_int32)]),
     "le_mc_alias_table": (_STATUS, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "le_mc_map_solid": (_STATUS, [C.POINTER(GeometryDesc), C.c_int32, C.c_int32, C.c_void_p]),
+    "le_mc_test_fail_allocation": (_STATUS, [C.c_int32]),
     "le_mc_create_geometry": (_STATUS, [C.POINTER(GeometryDesc), C.POINTER(_H)]),
     "le_mc_destroy_geometry": (_STATUS, [_H]),
     "le_mc_run": (_STATUS, [_H, _H, C.POINTER(RunDesc), C.c_void_p, C.POINTER(_H)]),
@@ -294,6 +295,13 @@ def le_mc_map_solid(desc, map_ny, map_nz):
     out = np.zeros((int(map_nz), int(map_ny)))
     _check(lib.le_mc_map_solid(C.byref(desc), int(map_ny), int(map_nz), out.ctypes.data), "le_mc_map_solid")
     return out
+
+
+def le_mc_test_fail_allocation(after):
+    _check(lib.le_mc_test_fail_allocation(int(after)), "le_mc_test_fail_allocation")
+
+
+DEVICE_FLAGS = {"rejection_exhausted": 1, "bad_launch": 4}
 
 
 def le_mc_create_geometry(desc):

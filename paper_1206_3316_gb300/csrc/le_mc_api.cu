@@ -45,6 +45,13 @@ le_mc_status fail(le_mc_status s, const char* fmt, const char* detail = nullptr)
     return s;
 }
 
+// Device allocations of materials and runs, through the failure-test hook.
+static cudaError_t alloc_async(void** p, size_t bytes, cudaStream_t s)
+{
+    if (alloc_fault_injected()) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
+}
+
 le_mc_status cuda_fail(cudaError_t e, const char* where)
 {
     if (e == cudaErrorMemoryAllocation) return fail(LE_MC_ERR_NOMEM, where, cudaGetErrorString(e));
@@ -226,6 +233,12 @@ le_mc_status le_mc_alias_table(const double* weights, int32_t n, uint32_t* thres
     return LE_MC_OK;
 }
 
+le_mc_status le_mc_test_fail_allocation(int32_t after)
+{
+    set_alloc_fault(after);
+    return LE_MC_OK;
+}
+
 le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32_t map_nz, double* fraction)
 {
     const char* why = nullptr;
@@ -282,11 +295,11 @@ le_mc_status le_mc_create_material(const le_mc_material_desc* desc, le_mc_materi
     }
     // stream-ordered pool on the legacy stream, complete before returning
     cudaError_t e = cudaGetDevice(&m->device);
-    if (e == cudaSuccess) e = cudaMallocAsync(&m->d_props32, props32.size() * sizeof(float), 0);
-    if (e == cudaSuccess) e = cudaMallocAsync(&m->d_props64, props64.size() * sizeof(double), 0);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_scat, n * sizeof(uint2), 0);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_emit, n * sizeof(uint2), 0);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&m->d_alias_init, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = alloc_async(&m->d_props32, props32.size() * sizeof(float), 0);
+    if (e == cudaSuccess) e = alloc_async(&m->d_props64, props64.size() * sizeof(double), 0);
+    if (e == cudaSuccess) e = alloc_async((void**)&m->d_alias_scat, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = alloc_async((void**)&m->d_alias_emit, n * sizeof(uint2), 0);
+    if (e == cudaSuccess) e = alloc_async((void**)&m->d_alias_init, n * sizeof(uint2), 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props32, props32.data(), props32.size() * sizeof(float), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_props64, props64.data(), props64.size() * sizeof(double), cudaMemcpyHostToDevice, 0);
     if (e == cudaSuccess) e = cudaMemcpyAsync(m->d_alias_scat, as.data(), n * sizeof(uint2), cudaMemcpyHostToDevice, 0);
@@ -385,7 +398,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     cudaError_t e = cudaEventCreate(&h->ev_start);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_mid);
     if (e == cudaSuccess) e = cudaEventCreate(&h->ev_stop);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&h->dev, h->dev_bytes, h->stream);
+    if (e == cudaSuccess) e = alloc_async((void**)&h->dev, h->dev_bytes, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->dev, 0, h->dev_bytes, h->stream);
     if (e != cudaSuccess) {
         le_mc_destroy_run(h);

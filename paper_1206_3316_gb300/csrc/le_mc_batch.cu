@@ -279,7 +279,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     b->sums.assign((size_t)n * 2, 0.0);
     b->counters.assign((size_t)n * CNT_N, 0ull);
     e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->dev, b->dev_bytes);
+    if (e == cudaSuccess) e = alloc_fault_injected() ? cudaErrorMemoryAllocation : cudaMalloc((void**)&b->dev, b->dev_bytes);
     if (e == cudaSuccess) e = cudaMemcpy(b->dev + b->off_inst, inst.data(), n * sizeof(BatchInstance), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->dev + b->off_offsets, offsets.data(), (n + 1) * sizeof(unsigned long long), cudaMemcpyHostToDevice);

@@ -4,6 +4,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <atomic>
 #include <limits>
 #include <vector>
 
@@ -197,6 +198,19 @@ void fill_consts(TraceParams& P)
     }
     fill_one<float>(P, P.c32);
     fill_one<double>(P, P.c64);
+}
+
+static std::atomic<int32_t> g_alloc_fault{-1};
+
+void set_alloc_fault(int32_t after) { g_alloc_fault.store(after < 0 ? -1 : after); }
+
+bool alloc_fault_injected()
+{
+    int32_t v = g_alloc_fault.load();
+    while (v >= 0) {
+        if (g_alloc_fault.compare_exchange_weak(v, v - 1)) return v == 0;
+    }
+    return false;
 }
 
 void fill_instance32(BatchInstance& b)

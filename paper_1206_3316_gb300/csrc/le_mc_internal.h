@@ -9,12 +9,17 @@
 
 namespace lemc {
 
-// Device-side warning bits (OR-ed into a status word, never a trap).
+// Device-side status bits (OR-ed into a status word, never a trap): the
+// LE_MC_FLAG_* values of the public header.
 enum : uint32_t {
-    FLAG_REJECTION_EXHAUSTED = 1u,  // a rejection loop used all its tries
-    FLAG_INDEX_CLAMPED = 2u,        // a bin / cell / mode index was clamped into range
-    FLAG_BAD_LAUNCH = 4u,           // kernel launched with an unexpected shape
+    FLAG_REJECTION_EXHAUSTED = LE_MC_FLAG_REJECTION_EXHAUSTED,
+    FLAG_BAD_LAUNCH = LE_MC_FLAG_BAD_LAUNCH,
 };
+
+// Test hook for failure handling (le_mc_test_fail_allocation): true when the
+// library's next device allocation is to report out of memory.
+bool alloc_fault_injected();
+void set_alloc_fault(int32_t after);
 
 // Global counters produced by a run (u64 each).
 enum { CNT_PARTICLES = 0, CNT_SEGMENTS, CNT_SCATTERS, CNT_WALL, CNT_PERIODIC, CNT_TRUNCATED,

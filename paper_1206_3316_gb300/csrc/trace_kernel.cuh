@@ -341,6 +341,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     constexpr bool FUSED = FusedTable<R, SRC, PROFILE>::value;
     const TraceParams& P = args.p;
     const RoundKeys& rk = args.rk;
+    // the per-warp queue claims and emission buffers assume whole warps and
+    // at most 512 threads; the host validates launch shapes, and a kernel
+    // given any other reports it and traces nothing
+    if ((blockDim.x & 31u) != 0u || blockDim.x > 512u) {
+        if (threadIdx.x == 0) atomicOr(P.flags, FLAG_BAD_LAUNCH);
+        return;
+    }
 
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_modes = P.n_modes;
