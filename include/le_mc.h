@@ -59,6 +59,10 @@ extern "C" {
  *   points validate shapes first, so this marks a library defect. */
 #define LE_MC_FLAG_REJECTION_EXHAUSTED 1u
 #define LE_MC_FLAG_BAD_LAUNCH 4u
+/* DEBUG_BOUNDS (debug builds, -DLEMC_DEBUG, only): a data-dependent index of
+ * a trace kernel (emission-buffer slot, mode, queue position, transient cell)
+ * was out of range; the access was redirected to index 0. */
+#define LE_MC_FLAG_DEBUG_BOUNDS 8u
 
 typedef enum {
     LE_MC_OK = 0,
@@ -212,7 +216,8 @@ typedef struct {
     int32_t n_batch;                /* profile and map batch groups (particle id
                                      * mod n_batch)                              */
     int32_t grid_nx, grid_ny, grid_nz; /* PULSE: counting grid over L x domain   */
-    int32_t n_samples;              /* PULSE: sample times (k + 1/2) sample_dt    */
+    int32_t n_samples;              /* PULSE, INITIAL: sample times (k + 1/2)
+                                     * sample_dt, k < n_samples <= 2^20        */
     double t_final;                 /* PULSE: end of the simulation [s]          */
     double sample_dt;               /* PULSE: sample spacing [s]                 */
     int32_t n_hj;                   /* flux split by scattering index j (0 = off;

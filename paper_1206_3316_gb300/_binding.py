@@ -14,7 +14,9 @@ import os
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libLeMC.so")
+# LE_MC_LIBRARY selects another build of the library (the checking variant
+# libLeMC_debug.so of build.build(debug=True)); there is no other backend
+LIB_PATH = os.environ.get("LE_MC_LIBRARY") or os.path.join(_PKG, "libLeMC.so")
 
 LE_MC_OK, LE_MC_ERR_INVALID, LE_MC_ERR_NOMEM, LE_MC_ERR_CUDA = 0, 1, 2, 3
 LE_MC_ERR_TIMEOUT, LE_MC_ERR_BUDGET, LE_MC_ERR_STATE, LE_MC_ERR_NODEV = 4, 5, 6, 7

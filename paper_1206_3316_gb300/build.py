@@ -17,6 +17,7 @@ SRC = os.path.join(PKG, "csrc")
 INC = os.path.join(ROOT, "include")
 OBJ = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libLeMC.so")
+LIB_DEBUG = os.path.join(PKG, "libLeMC_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP32 trajectories use approximate division / square root and flush denormals;
@@ -38,15 +39,21 @@ def _newest_input():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(OBJ, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Build libLeMC.so, or with ``debug`` the checking variant
+    libLeMC_debug.so (-DLEMC_DEBUG: out-of-range kernel indices are reported
+    in the run's device flags instead of being trusted)."""
+    lib = LIB_DEBUG if debug else LIB
+    obj_dir = os.path.join(OBJ, "debug") if debug else OBJ
+    flags = CUFLAGS + (["-DLEMC_DEBUG"] if debug else [])
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(obj_dir, exist_ok=True)
     exe = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(OBJ, os.path.splitext(src)[0] + ".o")
-        cmd = [exe] + CUFLAGS + ["-c", os.path.join(SRC, src), "-o", obj]
+        obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
+        cmd = [exe] + flags + ["-c", os.path.join(SRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]
         res = subprocess.run(cmd, capture_output=True, text=True)
@@ -58,13 +65,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     res = subprocess.run([exe] + ARCH + ["-shared", "-o", tmp] + objs, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force=True, verbose=True))
+    import sys
+    print(build(force=True, verbose=True, debug="--debug" in sys.argv))

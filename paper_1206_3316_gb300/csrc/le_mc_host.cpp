@@ -321,7 +321,7 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
         *why = "the flux split by scattering index (n_hj) is a steady estimator";
         return LE_MC_ERR_INVALID;
     }
-    if (r->n_samples < 0) { *why = "n_samples < 0"; return LE_MC_ERR_INVALID; }
+    if (r->n_samples < 0 || r->n_samples > (1 << 20)) { *why = "n_samples out of 0..2^20"; return LE_MC_ERR_INVALID; }
     if (r->n_samples > 0) {
         if (r->source != LE_MC_SRC_PULSE && r->source != LE_MC_SRC_INITIAL) {
             *why = "grid samples need the PULSE or INITIAL source";

@@ -14,6 +14,7 @@ namespace lemc {
 enum : uint32_t {
     FLAG_REJECTION_EXHAUSTED = LE_MC_FLAG_REJECTION_EXHAUSTED,
     FLAG_BAD_LAUNCH = LE_MC_FLAG_BAD_LAUNCH,
+    FLAG_DEBUG_BOUNDS = LE_MC_FLAG_DEBUG_BOUNDS,
 };
 
 // Test hook for failure handling (le_mc_test_fail_allocation): true when the

@@ -29,6 +29,32 @@
 
 namespace lemc {
 
+// Debug builds (-DLEMC_DEBUG) check the data-dependent indices of the trace
+// kernels: an index out of its range sets FLAG_DEBUG_BOUNDS in the lane's
+// status word and is replaced by 0, so the access stays in bounds and the
+// run reports the defect instead of faulting.  Release builds compile the
+// checks away.
+#ifdef LEMC_DEBUG
+#define LEMC_GUARD_INDEX(idx, n)                  \
+    do {                                          \
+        if (!((long long)(idx) >= 0 && (long long)(idx) < (long long)(n))) { \
+            flags |= FLAG_DEBUG_BOUNDS;           \
+            (idx) = 0;                            \
+        }                                         \
+    } while (0)
+#define LEMC_DEBUG_CHECK(ok)                                 \
+    do {                                                     \
+        if (!(ok)) flags |= FLAG_DEBUG_BOUNDS;               \
+    } while (0)
+#else
+#define LEMC_GUARD_INDEX(idx, n) \
+    do {                         \
+    } while (0)
+#define LEMC_DEBUG_CHECK(ok) \
+    do {                     \
+    } while (0)
+#endif
+
 struct KernelArgs {
     TraceParams p;
     RoundKeys rk;
@@ -497,6 +523,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             iy = (int)M::floor_(py / K.Dy * (R)P.gy);
             iz = (int)M::floor_(pz / K.Dz * (R)P.gz);
         }
+        // (a sample on the domain's far faces rounds one cell out; anything
+        // further means the position left the domain)
+        LEMC_DEBUG_CHECK(ix >= -1 && ix <= P.gx && iy >= -1 && iy <= P.gy && iz >= -1 && iz <= P.gz);
         ix = min(max(ix, 0), P.gx - 1);
         iy = min(max(iy, 0), P.gy - 1);
         iz = min(max(iz, 0), P.gz - 1);
@@ -618,9 +647,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 k_lo = (int)ceil(t / dts - R(0.5)) - 1;
                 k_end = (int)ceil(t_end / dts - R(0.5)) - 1;
             }
-            k_lo = max(k_lo, 0);
+            // Both start one below the true bound (the rounded quotient errs by
+            // less than one sample for n_samples <= 2^20, which the host
+            // enforces) and are clamped into [0, n_samples]: a segment after
+            // the last sample time has none, however far t_final lies beyond.
+            k_lo = min(max(k_lo, 0), ns);
             while (k_lo < ns && ts_of(k_lo) < t) ++k_lo;
-            k_end = max(k_end, k_lo);
+            k_end = min(max(k_end, k_lo), ns);
             while (k_end < ns && ts_of(k_end) < t_b && ts_of(k_end) <= t_end) ++k_end;
             const int n_s = k_end - k_lo;
             // (cy, cz are kept wrapped into the periodic domain)
@@ -767,7 +800,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const R lam_new = __uint_as_float(((uint32_t)mm < e.x) ? e.z : e.w);
             lam = scat ? lam_new : lam;
         } else {
-            const uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+            uint32_t m_new = alias_draw(s_scat, (uint32_t)n_modes, r.y);
+            LEMC_GUARD_INDEX(m_new, n_modes);
             const R lam_new = s_props[2 * m_new], vg_new = s_props[2 * m_new + 1];
             lam = scat ? lam_new : lam;
             vg = scat ? vg_new : vg;
@@ -889,7 +923,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             rec.L_axis = (double)Lacc;
             rec.x0 = (double)x0;
             rec.t0 = (double)t0;
-            P.records[pid - P.first] = rec;
+            uint32_t ri = pid - P.first;
+            LEMC_GUARD_INDEX(ri, P.n_particles);
+            P.records[ri] = rec;
         }
         pending = false;
     };
@@ -955,7 +991,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         if (!emit_particle<R, GEOM, SRC>(P, ctx, rk, SRC == LE_MC_SRC_INITIAL ? P.alias_init : P.alias_emit, id, ex, ey,
                                          ez, eox, eoy, eoz, et, em, es, ecy, ecz))
             flags |= FLAG_REJECTION_EXHAUSTED;
-        const int slot = base + __popc(before);
+        int slot = base + __popc(before);
+        LEMC_GUARD_INDEX(slot, kBufSlots);
         buf.x[slot] = ex;
         buf.ox[slot] = eox;
         buf.oy[slot] = eoy;
@@ -973,6 +1010,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
 
     // start this lane's next particle from emission-buffer slot `slot`
     auto take = [&](int slot) {
+        LEMC_GUARD_INDEX(slot, kBufSlots);
         x = buf.x[slot];
         ox = buf.ox[slot];
         oy = buf.oy[slot];
@@ -996,6 +1034,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             instw = bi.inst_id;
         }
         mode0 = ms & 0x7FFFFFFFu;
+        LEMC_GUARD_INDEX(mode0, n_modes);
         sign = (ms >> 31) ? -1 : 1;
         if constexpr (FUSED) {
             lam = __uint_as_float(s_fused[mode0].z);
@@ -1059,6 +1098,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                     valid = false;
                 } else if (q < n_long) {
                     pos = long_region[q];
+                    LEMC_GUARD_INDEX(pos, n_pos);
                     valid = true;
                 } else {
                     pos = (uint32_t)(q - n_long);

@@ -389,6 +389,22 @@ def test_transient_standard_errors_match_seed_scatter(P):
     assert emp[keep].sum() / poisson[keep].sum() < 0.8
 
 
+def test_samples_stop_at_the_last_sample_time(P, oracle):
+    # t_final (2 ns) far beyond the sampled window (40 samples, 400 ps): the
+    # segments after the last sample time place no sample, every particle is
+    # traced, and an FP64 run counts exactly what the oracle counts
+    p = W.porous_pulse(n_particles=200_000, grid=(8, 16, 16), n_samples=40)
+    g = P.simulate(p)
+    assert g["particles"] == 200_000 and g["device_flags"] == 0
+    counts = g["grid"].reshape(40, -1).sum(axis=1)
+    assert np.all(np.diff(counts) >= 0) and counts[-1] <= 200_000
+    q = W.porous_pulse(n_particles=5_000, grid=(8, 16, 16), n_samples=40, precision="fp64",
+                       material=dict(W.GRAY_UNIT, tau=2e-10, v=1000.0))
+    gq, oq = P.simulate(q), oracle.run(q)
+    assert gq["particles"] == oq["particles"] == 5_000
+    np.testing.assert_array_equal(gq["grid"], oq["grid"])
+
+
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
     # picks): below the pore-free film times the solid fraction, and the same
