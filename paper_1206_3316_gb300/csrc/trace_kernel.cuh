@@ -556,6 +556,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 const int v = __shfl_sync(FULL, inc, own + bit - 1);
                 if (v <= j) own += bit;
             }
+            LEMC_GUARD_INDEX(own, 32);
             const int own_excl = __shfl_sync(FULL, excl, own);
             if (j < total)
                 place_sample(J.k0[own] + (j - own_excl), J.x[own], J.y[own], J.z[own], J.ox[own], J.oy[own], J.oz[own],
@@ -692,6 +693,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const int g = (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
             double* mT = P.prof + (size_t)g * cells;
             double* mQ = P.prof + ((size_t)P.n_batch + g) * cells;
+            // (a position on the cell's far faces rounds at most one map cell out)
+            LEMC_DEBUG_CHECK(y * K.map_iy > R(-1) && y * K.map_iy < (R)(ny + 1) && z * K.map_iz > R(-1) &&
+                             z * K.map_iz < (R)(nz + 1));
             int j = min(max((int)M::floor_(y * K.map_iy), 0), ny - 1);
             int k = min(max((int)M::floor_(z * K.map_iz), 0), nz - 1);
             const bool up_y = oy > R(0), up_z = oz > R(0);
@@ -732,6 +736,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
             const R lo = fmin(x, x_new), hi = fmax(x, x_new);
             int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
+            // (a wall position rounds at most one bin out)
+            LEMC_DEBUG_CHECK(k0 >= -1 && k1 <= nb);
             k0 = min(max(k0, 0), nb - 1);
             k1 = min(max(k1, 0), nb - 1);
             const double s = (double)sign;
@@ -979,6 +985,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         EmitCtx<R> ctx;
         if constexpr (BATCH) {
             eb = batch_find(P.offsets, (uint32_t)P.n_instances, pos);
+            LEMC_GUARD_INDEX(eb, P.n_instances);
             id = (uint32_t)(pos - P.offsets[eb]);
             ctx = batch_ctx<R>(P.instances[eb]);
         } else {
