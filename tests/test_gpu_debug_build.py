@@ -33,6 +33,14 @@ CASES = {
     "pulse_fp32": (W.porous_pulse(n_particles=200_000, grid=(8, 16, 16), n_samples=40), {}),
     "initial_fp32": (W.porous_initial(n_particles=200_000), {}),
     "ttr_fp64": (W.ttr_film(n_particles=20_000, precision="fp64", n_samples=20), {}),
+    "film_partial_aniso_hj_fp32": (W.silicon_film(n_particles=300_000, specularity=0.5,
+                                                  material=dict(W.SILICON_LIKE, scatter_g=0.4), n_hj=8), {}),
+    "porous_first_event_fp32": (W.with_run(W.porous_film(n_particles=300_000), max_events=1), {}),
+    "porous_first_path_fp64": (W.with_run(W.porous_film(n_particles=20_000, precision="fp64"), max_collisions=1),
+                               {"record_particles": True}),
+    "film_piece_fp32": (W.with_run(W.silicon_film(n_particles=70_001), first_particle=123_457), {}),
+    "film_tiny_fp32": (W.silicon_film(n_particles=33), {"record_particles": True}),
+    "slab_one_fp64": (W.gray_slab(n_particles=1, n_bins=4), {}),
 }
 '''
 
