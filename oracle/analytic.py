@@ -337,3 +337,81 @@ def slab_multimode_psi(Lambda, q_emit, p_scat, L, M=200, richardson=True):
         return p1
     p2 = solve(2 * M)
     return (4 * p2 - p1) / 3
+
+
+def porous_first_flight_distance(L, pitch, radius, pos, omega):
+    """Distance along unit directions ``omega`` (n x 3) from points ``pos``
+    (n x 3, inside the solid of the unit cell) to the first boundary of the
+    cell: the film faces x = 0, L, the unit-cell faces y, z = 0, pitch, or the
+    cylindrical pore of the given radius along x through the cell centre.
+    Written with numpy from the geometry alone (the ray-boundary algebra)."""
+    x, y, z = pos[:, 0], pos[:, 1], pos[:, 2]
+    ox, oy, oz = omega[:, 0], omega[:, 1], omega[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        dx = np.where(ox > 0, (L - x) / ox, np.where(ox < 0, x / -ox, np.inf))
+        dy = np.where(oy > 0, (pitch - y) / oy, np.where(oy < 0, y / -oy, np.inf))
+        dz = np.where(oz > 0, (pitch - z) / oz, np.where(oz < 0, z / -oz, np.inf))
+        d = np.minimum(dx, np.minimum(dy, dz))
+        if radius > 0:
+            ry, rz = y - 0.5 * pitch, z - 0.5 * pitch
+            a = oy * oy + oz * oz
+            b = ry * oy + rz * oz
+            c = ry * ry + rz * rz - radius * radius
+            disc = b * b - a * c
+            t = (-b - np.sqrt(np.maximum(disc, 0.0))) / a  # nearer root; c > 0 outside the pore
+            hit = (a > 0) & (disc >= 0) & (b < 0) & (t >= 0)
+            d = np.where(hit, np.minimum(d, t), d)
+    return d
+
+
+def _first_flight_samples(L, pitch, radius, m, seed):
+    """Scrambled Sobol points of the gradient source in a pored cell: positions
+    uniform in the solid, directions with the |mu_z| law about z; returns
+    |mu_z| and the distance to the first boundary of each."""
+    from scipy.stats import qmc
+    u = qmc.Sobol(d=5, scramble=True, seed=seed).random_base2(m)
+    pos = np.column_stack([u[:, 0] * L, u[:, 1] * pitch, u[:, 2] * pitch])
+    solid = (pos[:, 1] - 0.5 * pitch) ** 2 + (pos[:, 2] - 0.5 * pitch) ** 2 >= radius ** 2
+    pos, u = pos[solid], u[solid]
+    # |mu| law on [-1, 1] by inverting its CDF: |mu| = sqrt(|2w - 1|), sign of 2w - 1
+    w = u[:, 3]
+    mu = np.where(w < 0.5, -np.sqrt(np.abs(1.0 - 2.0 * w)), np.sqrt(np.abs(2.0 * w - 1.0)))
+    phi = 2.0 * np.pi * u[:, 4]
+    s = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+    omega = np.column_stack([s * np.cos(phi), s * np.sin(phi), mu])
+    return np.abs(mu), porous_first_flight_distance(L, pitch, radius, pos, omega)
+
+
+def kappa_first_event_porous(mat, L, pitch, radius, m=18, scrambles=4, chunk=4096):
+    """Conductivity of a pored film (gradient along z) when every particle
+    stops at its first event of any kind (relaxation, film face, pore or
+    unit-cell face: ``max_events = 1``).
+
+    A particle emitted in mode b, uniformly in the solid with the |mu_z| law
+    about z and sign sgn(mu_z) (dT/dz < 0), contributes s L_z = |mu_z|
+    min(l, d), l exponential of mean Lambda_b and d its distance to the first
+    boundary; the mean over l is |mu_z| Lambda_b (1 - exp(-d / Lambda_b)).
+    Modes are emitted with probability C_b v_b / sum C v, and the gradient
+    source's normalisation gives kappa = (1/2) (solid fraction) sum_b C_b v_b
+    E[|mu_z| Lambda_b (1 - exp(-d / Lambda_b))] (the bulk limit d -> inf is
+    (1/3) sum C v Lambda).  The mean over positions and directions is taken
+    by scrambled Sobol quasi-Monte Carlo (2^m points, positions in the pore
+    rejected), independently scrambled ``scrambles`` times.  Returns (kappa,
+    standard error of the scramble mean)."""
+    _, v, tau, C = mode_table(mat)
+    lam = v * tau
+    frac = 1.0 - math.pi * radius * radius / (pitch * pitch)
+    vals = []
+    for r in range(scrambles):
+        amu, d = _first_flight_samples(L, pitch, radius, m, 1206 + r)
+        total = 0.0
+        for i in range(0, lam.size, 64):
+            lb = lam[i:i + 64]
+            acc = np.zeros(lb.size)
+            for j in range(0, d.size, chunk):
+                dd, aa = d[j:j + chunk, None], amu[j:j + chunk, None]
+                acc += np.sum(aa * lb[None, :] * -np.expm1(-dd / lb[None, :]), axis=0)
+            total += float(np.sum(C[i:i + 64] * v[i:i + 64] * acc / d.size))
+        vals.append(0.5 * frac * total)
+    vals = np.array(vals)
+    return float(vals.mean()), float(vals.std(ddof=1) / math.sqrt(len(vals))) if len(vals) > 1 else 0.0

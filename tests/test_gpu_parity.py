@@ -405,6 +405,17 @@ def test_samples_stop_at_the_last_sample_time(P, oracle):
     np.testing.assert_array_equal(gq["grid"], oq["grid"])
 
 
+def test_first_event_pored_film_against_quadrature(P, analytic):
+    # config-2 steady at full size with max_events = 1, FP32: against the
+    # quasi-Monte Carlo first-event conductivity (numpy ray algebra)
+    pin, pin_se = analytic.kappa_first_event_porous(W.SILICON_LIKE, 300e-9, 100e-9, 30e-9, m=17)
+    g = P.simulate(W.with_run(W.porous_film(n_particles=100_000_000), max_events=1), arrays=False)
+    z = (g["kappa"] - pin) / np.hypot(g["kappa_se"], pin_se)
+    print(f"\nfirst-event pored film: GPU {g['kappa']:.4f} +- {g['kappa_se']:.4f}, quadrature {pin:.4f} +- {pin_se:.4f}")
+    assert abs(z) < 4.0, z
+    assert abs(g["kappa"] / pin - 1.0) < 2e-3
+
+
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
     # picks): below the pore-free film times the solid fraction, and the same

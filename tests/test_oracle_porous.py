@@ -11,7 +11,12 @@
   (exact total, point counts), the flux map partitions the scalar flux
   exactly, the mirror symmetries of the unit cell (T odd in z about the
   pore, even in y; the z flux even in both), and the flat maps of a film
-  without pores.
+  without pores;
+* first-event truncation (max_events = 1) in the pored cell: each particle's
+  mean contribution is |mu_z| Lambda (1 - exp(-d / Lambda)) for its distance d
+  to the first boundary, and the quasi-Monte Carlo mean of that (numpy ray
+  algebra, independent of the oracle) pins the emission law, the signs and
+  the normalisation of the gradient source in pored geometries.
 """
 import numpy as np
 import pytest
@@ -269,3 +274,24 @@ def test_map_of_film_is_flat(oracle, analytic):
     zq = (o["map_q"] - o["flux"]) / o["map_q_se"]
     assert stats.chi2.sf(np.sum(zq ** 2), zq.size - 1) > 1e-3
     assert abs(o["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 300e-9)) < 4.0 * o["kappa_se"]
+
+
+def first_event_pin_z(oracle, mat, radius, n=1_000_000, library=None, m=16):
+    """z-score of the oracle's first-event pored-film conductivity against
+    the quasi-Monte Carlo value (both errors combined)."""
+    from oracle import analytic
+    pin, pin_se = analytic.kappa_first_event_porous(mat, 300e-9, 100e-9, radius, m=m)
+    prob = W.with_run(W.porous_film(n_particles=n, precision="fp64", material=mat, radius=radius), max_events=1)
+    o = oracle.run(prob, library=library)
+    return (o["kappa"] - pin) / np.hypot(o["kappa_se"], pin_se)
+
+
+@pytest.mark.parametrize("lam,radius", [(2e-8, 30e-9), (2e-7, 30e-9), (5e-8, 45e-9), (1e-7, 0.0)])
+def test_first_event_pored_film_against_quadrature(oracle, lam, radius):
+    z = first_event_pin_z(oracle, dict(W.GRAY_UNIT, tau=lam, v=1.0), radius)
+    assert abs(z) < 4.0, z
+
+
+def test_first_event_silicon_pored_film_against_quadrature(oracle):
+    z = first_event_pin_z(oracle, W.SILICON_LIKE, 30e-9, m=15)
+    assert abs(z) < 4.0, z
