@@ -11,6 +11,7 @@
 
 #include "le_mc_internal.h"
 #include "trace_kernel.cuh"
+#include "le_mc_params.h"
 
 namespace lemc {
 cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
@@ -413,44 +414,12 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     memset(&a, 0, sizeof(a));
     TraceParams& P = a.p;
     const bool fp32 = r.precision == LE_MC_PREC_FP32;
-    P.props = fp32 ? m->d_props32 : m->d_props64;
-    P.alias_scat = m->d_alias_scat;
-    P.alias_emit = m->d_alias_emit;
-    P.alias_init = m->d_alias_init;
-    P.n_modes = m->n_modes;
-    P.scatter_g = m->desc.scatter_g;
+    MaterialView mv;
+    material_view(m, &mv);
+    fill_material(P, mv, fp32);
     const le_mc_geometry_desc& G = g->desc;
-    P.geom = G.kind;
-    P.wall_lo = G.wall_lo;
-    P.wall_hi = G.wall_hi;
-    P.pore_wall = G.pore_wall;
-    P.spec_lo = G.spec_lo;
-    P.spec_hi = G.spec_hi;
-    P.spec_pore = G.spec_pore;
-    P.cells_y = G.kind == LE_MC_GEOM_POROUS ? G.cells_y : 1;
-    P.cells_z = G.kind == LE_MC_GEOM_POROUS ? G.cells_z : 1;
-    P.L = G.kind == LE_MC_GEOM_BULK ? 1.0 : G.L;
-    P.pitch = G.kind == LE_MC_GEOM_POROUS ? G.pitch : 1.0;
-    P.radius = G.kind == LE_MC_GEOM_POROUS ? G.radius : 0.0;
-    P.src = r.source;
-    P.dT_lo = r.dT_lo;
-    P.dT_hi = r.dT_hi;
-    P.dTdz = r.dTdz;
-    P.p_sx = r.pulse_sigma_x;
-    P.p_st = r.pulse_sigma_t;
-    P.p_tc = r.pulse_t_center;
-    P.p_y0 = r.pulse_y0;
-    P.p_z0 = r.pulse_z0;
-    P.init_dT = r.init_dT;
-    P.init_x_lo = r.init_x_lo;
-    P.init_x_hi = r.init_x_hi;
-    P.n_particles = (uint32_t)r.n_particles;
-    P.key0 = (uint32_t)r.seed;
-    P.key1 = (uint32_t)(r.seed >> 32);
-    P.inst = r.instance_id;
-    P.max_scatter = r.max_scatter;
-    P.max_events = r.max_events;
-    P.max_collisions = r.max_collisions;
+    fill_geometry(P, G);
+    fill_run(P, r);
     P.n_bins_x = r.n_bins_x;
     P.n_batch = profile ? r.n_batch : 1;
     P.map_ny = has_map ? r.map_ny : 0;
@@ -472,11 +441,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     P.flags = reinterpret_cast<unsigned int*>(h->dev + h->off_flags);
     P.refill_min = r.refill_min > 0 ? r.refill_min : kDefaultRefillMin;
     P.chunk = r.chunk > 0 ? r.chunk : kDefaultChunk;
-    P.first = r.first_particle;
-    for (int i = 0; i < 10; ++i) {
-        a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
-        a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
-    }
+    fill_round_keys(a);
     if (h->long_cap > 0) {
         P.long_list = reinterpret_cast<uint32_t*>(h->dev + h->off_long_list);
         P.long_bits = reinterpret_cast<uint32_t*>(h->dev + h->off_long_bits);
@@ -487,13 +452,13 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     }
     fill_consts(P);
 
+    // (the steady maps live in global memory only; slab profiles also have a
+    // shared-memory copy per block)
+    const int smem_prof = has_map ? 0 : (int)h->prof_len;
     // launch shape: persistent grid of (SMs x resident blocks).  By default
     // 512 threads per block, or 256 when that keeps more warps resident (a
     // kernel instance whose registers leave room for only one 512-thread
     // block per SM)
-    // (the steady maps live in global memory only; slab profiles also have a
-    // shared-memory copy per block)
-    const int smem_prof = has_map ? 0 : (int)h->prof_len;
     auto shape_for = [&](int t, size_t* sm_bytes, int* resident) {
         cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, smem_prof,
                                                 (int)h->hj_len, sm_bytes)

@@ -14,6 +14,7 @@
 
 #include "le_mc_internal.h"
 #include "trace_kernel.cuh"
+#include "le_mc_params.h"
 
 namespace lemc {
 cudaError_t batch_attr_f32(int src, bool diff, int threads, size_t smem, int* per_sm);
@@ -88,32 +89,14 @@ KernelArgs make_args(le_mc_batch b)
     memset(&a, 0, sizeof(a));
     TraceParams& P = a.p;
     const le_mc_run_desc& r = b->run0;
-    P.props = fp32(b) ? b->mv.props32 : b->mv.props64;
-    P.alias_scat = b->mv.alias_scat;
-    P.alias_emit = b->mv.alias_emit;
-    P.n_modes = b->mv.n_modes;
-    P.scatter_g = b->mv.scatter_g;
-    P.geom = LE_MC_GEOM_PLANES;
-    P.wall_lo = b->geo0.wall_lo;
-    P.wall_hi = b->geo0.wall_hi;
+    fill_material(P, b->mv, fp32(b));
+    fill_geometry(P, b->geo0);
+    fill_run(P, r);
+    // (per-instance: thickness, drive, size and instance word come from the
+    // instance table; the shared geometry is PLANES with diffuse pores unused)
     P.pore_wall = LE_MC_WALL_DIFFUSE;
-    P.spec_lo = b->geo0.spec_lo;
-    P.spec_hi = b->geo0.spec_hi;
-    P.cells_y = P.cells_z = 1;
-    P.L = b->geo0.L;
-    P.pitch = 1.0;
-    P.radius = 0.0;
-    P.src = r.source;
-    P.dT_lo = r.dT_lo;
-    P.dT_hi = r.dT_hi;
-    P.dTdz = r.dTdz;
     P.n_particles = 0;
-    P.key0 = (uint32_t)r.seed;
-    P.key1 = (uint32_t)(r.seed >> 32);
     P.inst = 0;
-    P.max_scatter = r.max_scatter;
-    P.max_events = r.max_events;
-    P.max_collisions = r.max_collisions;
     P.n_batch = 1;
     P.sums = nullptr;
     P.counters = nullptr;
@@ -135,10 +118,7 @@ KernelArgs make_args(le_mc_batch b)
     P.inst_sums = reinterpret_cast<double*>(b->dev + b->off_sums);
     P.inst_counters = reinterpret_cast<unsigned long long*>(b->dev + b->off_counters);
     fill_consts(P);
-    for (int i = 0; i < 10; ++i) {
-        a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
-        a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
-    }
+    fill_round_keys(a);
     return a;
 }
 

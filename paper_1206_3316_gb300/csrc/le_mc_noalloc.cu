@@ -27,14 +27,15 @@
 
 #include "le_mc_internal.h"
 #include "trace_kernel.cuh"
+#include "le_mc_params.h"
 
 namespace lemc {
 cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
                              size_t smem, cudaStream_t st);
 cudaError_t launch_trace_f64(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
                              size_t smem, cudaStream_t st);
-cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
-cudaError_t occupancy_trace_f64(int geom, int src, bool profile, int threads, size_t smem, int* per_sm);
+cudaError_t occupancy_trace_for_f32(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm);
+cudaError_t occupancy_trace_for_f64(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm);
 cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
                            size_t* bytes);
 cudaError_t smem_trace_f64(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
@@ -126,34 +127,10 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     KernelArgs a;
     memset(&a, 0, sizeof(a));
     TraceParams& P = a.p;
-    P.props = fp32 ? mv.props32 : mv.props64;
-    P.alias_scat = mv.alias_scat;
-    P.alias_emit = mv.alias_emit;
-    P.n_modes = mv.n_modes;
-    P.scatter_g = mv.scatter_g;
-    P.geom = G.kind;
-    P.wall_lo = G.wall_lo;
-    P.wall_hi = G.wall_hi;
-    P.pore_wall = G.pore_wall;
-    P.spec_lo = G.spec_lo;
-    P.spec_hi = G.spec_hi;
-    P.spec_pore = G.spec_pore;
-    P.cells_y = G.kind == LE_MC_GEOM_POROUS ? G.cells_y : 1;
-    P.cells_z = G.kind == LE_MC_GEOM_POROUS ? G.cells_z : 1;
-    P.L = G.kind == LE_MC_GEOM_BULK ? 1.0 : G.L;
-    P.pitch = G.kind == LE_MC_GEOM_POROUS ? G.pitch : 1.0;
-    P.radius = G.kind == LE_MC_GEOM_POROUS ? G.radius : 0.0;
-    P.src = r.source;
-    P.dT_lo = r.dT_lo;
-    P.dT_hi = r.dT_hi;
-    P.dTdz = r.dTdz;
+    fill_material(P, mv, fp32);
+    fill_geometry(P, G);
+    fill_run(P, r);
     P.n_particles = (uint32_t)N;
-    P.key0 = (uint32_t)r.seed;
-    P.key1 = (uint32_t)(r.seed >> 32);
-    P.inst = r.instance_id;
-    P.max_scatter = r.max_scatter;
-    P.max_events = r.max_events;
-    P.max_collisions = r.max_collisions;
     P.n_batch = 1;
     P.sums = d_sums;
     P.counters = d_counters;
@@ -169,12 +146,8 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     }
     P.refill_min = r.refill_min > 0 ? r.refill_min : 1;
     P.chunk = r.chunk > 0 ? r.chunk : 32;
-    P.first = r.first_particle;
     fill_consts(P);
-    for (int i = 0; i < 10; ++i) {
-        a.rk.k0[i] = P.key0 + (uint32_t)i * 0x9E3779B9u;
-        a.rk.k1[i] = P.key1 + (uint32_t)i * 0xBB67AE85u;
-    }
+    fill_round_keys(a);
 
     int threads = r.threads_per_block > 0 ? r.threads_per_block : 256;
     size_t smem = 0;
@@ -183,8 +156,8 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     int sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-        e = fp32 ? occupancy_trace_f32(G.kind, r.source, false, threads, smem, &per_sm)
-                 : occupancy_trace_f64(G.kind, r.source, false, threads, smem, &per_sm);
+        e = fp32 ? occupancy_trace_for_f32(P, false, threads, smem, &per_sm)
+                 : occupancy_trace_for_f64(P, false, threads, smem, &per_sm);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;
     if (e == cudaSuccess && r.blocks_per_sm > 0 && r.blocks_per_sm < per_sm) per_sm = r.blocks_per_sm;
     int blocks = sms * per_sm;
