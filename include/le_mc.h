@@ -60,8 +60,10 @@ extern "C" {
 #define LE_MC_FLAG_REJECTION_EXHAUSTED 1u
 #define LE_MC_FLAG_BAD_LAUNCH 4u
 /* DEBUG_BOUNDS (debug builds, -DLEMC_DEBUG, only): a data-dependent index of
- * a trace kernel (emission-buffer slot, mode, queue position, transient cell)
- * was out of range; the access was redirected to index 0. */
+ * a trace kernel (emission-buffer slot, mode, queue position, batch
+ * instance, sample-job owner, record slot) was out of range and its access was
+ * redirected to index 0, or a transient cell, slab-profile bin or map cell
+ * was computed more than one cell outside its grid. */
 #define LE_MC_FLAG_DEBUG_BOUNDS 8u
 
 typedef enum {
@@ -69,8 +71,8 @@ typedef enum {
     LE_MC_ERR_INVALID = 1, /* a descriptor field or argument is out of range     */
     LE_MC_ERR_NOMEM = 2,   /* a host or device allocation failed                 */
     LE_MC_ERR_CUDA = 3,    /* a CUDA runtime call failed                         */
-    LE_MC_ERR_TIMEOUT = 4, /* a bounded device-side wait gave up                 */
-    LE_MC_ERR_BUDGET = 5,  /* a device-side bound was hit that invalidates output */
+    LE_MC_ERR_TIMEOUT = 4, /* a bounded wait ended first (le_mc_server_wait_all) */
+    LE_MC_ERR_BUDGET = 5,  /* reserved: no entry point returns it at present      */
     LE_MC_ERR_STATE = 6,   /* the handle is unusable (earlier failure) or busy    */
     LE_MC_ERR_NODEV = 7    /* no usable CUDA device                              */
 } le_mc_status;
