@@ -173,12 +173,6 @@ LE_MC_API le_mc_status le_mc_create_geometry(const le_mc_geometry_desc* desc, le
  * Errors: LE_MC_ERR_INVALID (not POROUS, sizes out of 1..LE_MC_MAX_MAP). */
 LE_MC_API le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32_t map_nz, double* fraction);
 
-/* Test hook for failure handling: the after-th next device allocation made by
- * the library for a material, a run or a batch (0 = the very next one)
- * reports out of memory, so the caller sees LE_MC_ERR_NOMEM from that call
- * with nothing leaked; the hook then disarms itself.  after < 0 disarms it.
- * Process-wide.  Errors: none. */
-LE_MC_API le_mc_status le_mc_test_fail_allocation(int32_t after);
 LE_MC_API le_mc_status le_mc_destroy_geometry(le_mc_geometry g);
 
 /* ---- run: sources (step I), termination (step VI), estimators (step V) ---- */
@@ -215,13 +209,17 @@ typedef struct {
     uint32_t max_scatter;           /* terminate at this scattering event (0 = none) */
     uint32_t max_events;            /* terminate after this many segments (>= 1) */
     int32_t n_bins_x;               /* WALLS: T(x), q(x) profile bins (0 = off)   */
-    int32_t n_batch;                /* profile and map batch groups (particle id
-                                     * mod n_batch)                              */
-    int32_t grid_nx, grid_ny, grid_nz; /* PULSE: counting grid over L x domain   */
+    int32_t n_batch;                /* batch groups of the error bars: slab
+                                     * profiles group particle ids mod n_batch,
+                                     * maps group particle pairs (2i, 2i + 1)
+                                     * mod n_batch, so that every group holds
+                                     * both signs of the gradient source        */
+    int32_t grid_nx, grid_ny, grid_nz; /* PULSE, INITIAL: counting grid over the
+                                        * L x domain                          */
     int32_t n_samples;              /* PULSE, INITIAL: sample times (k + 1/2)
                                      * sample_dt, k < n_samples <= 2^20        */
-    double t_final;                 /* PULSE: end of the simulation [s]          */
-    double sample_dt;               /* PULSE: sample spacing [s]                 */
+    double t_final;                 /* PULSE, INITIAL: end of the simulation [s] */
+    double sample_dt;               /* PULSE, INITIAL: sample spacing [s]        */
     int32_t n_hj;                   /* flux split by scattering index j (0 = off;
                                      * steady sources only)                     */
     int32_t record_particles;       /* 1: keep one le_mc_particle per particle   */
@@ -274,7 +272,10 @@ typedef struct le_mc_run_s* le_mc_run_handle;
 LE_MC_API le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc* desc,
                        void* stream, le_mc_run_handle* out);
 
-/* Blocks until the run's device work is complete. */
+/* Blocks until the run's device work is complete.
+ * Errors: LE_MC_ERR_INVALID (null handle), LE_MC_ERR_STATE (the run failed
+ * earlier), LE_MC_ERR_CUDA (the device work failed; the handle then reports
+ * LE_MC_ERR_STATE). */
 LE_MC_API le_mc_status le_mc_wait(le_mc_run_handle h);
 
 typedef struct {
@@ -486,7 +487,7 @@ LE_MC_API le_mc_status le_mc_server_destroy(le_mc_server s);
  * device, so make that first call before any stream capture.  Every call
  * shares the array: calls whose device work overlaps in time race on it, so
  * the caller must serialise them.  Steady WALLS / GRADIENT runs only (no
- * profiles, H_j, grid or records).  Asynchronous on `stream`.
+ * profiles, maps, H_j, grid or records).  Asynchronous on `stream`.
  * Errors: LE_MC_ERR_INVALID (null pointer, bad descriptor, n_particles above
  * the limit, arrays requested), LE_MC_ERR_CUDA. */
 #define LE_MC_NOALLOC_MAX_PARTICLES (1u << 22)
@@ -507,14 +508,22 @@ LE_MC_API le_mc_status le_mc_sample_modes(le_mc_material m, int32_t which, const
 /* Current device: SM count and name (NULL-safe). */
 LE_MC_API le_mc_status le_mc_device_info(int32_t* sm_count, char* name, size_t name_capacity);
 
-/* Thread-local description of the last failure on this thread ("" if none). */
 /* sizeof of the ABI structs, for binding checks: which = 0 material_desc,
  * 1 geometry_desc, 2 run_desc, 3 tallies, 4 particle, 5 launch_config;
  * -1 if unknown. */
 LE_MC_API int32_t le_mc_struct_size(int32_t which);
 
+/* Thread-local description of the last failure on this thread ("" if none). */
 LE_MC_API const char* le_mc_last_error(void);
+/* LE_MC_ABI_VERSION of the built library. */
 LE_MC_API int32_t le_mc_abi_version(void);
+
+/* Test hook for failure handling: the after-th next device allocation made by
+ * the library for a material, a run or a batch (0 = the very next one)
+ * reports out of memory, so the caller sees LE_MC_ERR_NOMEM from that call
+ * with nothing leaked; the hook then disarms itself.  after < 0 disarms it.
+ * Process-wide.  Errors: none. */
+LE_MC_API le_mc_status le_mc_test_fail_allocation(int32_t after);
 
 #ifdef __cplusplus
 }
