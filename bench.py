@@ -61,10 +61,12 @@ LANES_PER_SM = 128  # FP32/INT32 lanes issuing one operation per clock
 
 
 def _sha_kernel_sources():
-    """Hash of the kernel sources with comments and whitespace removed, so
-    that only edits which can change the compiled code invalidate a capture."""
+    """Hash of the film kernel's sources (its body, helpers and parameter
+    layout, and the launcher that picks its instance and launch bounds) with
+    comments and whitespace removed, so that only edits which can change the
+    compiled code invalidate a capture."""
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h"):
+    for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h", "trace_f32.cu"):
         with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f)) as fh:
             txt = fh.read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
