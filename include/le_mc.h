@@ -338,13 +338,18 @@ LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out
  *                      error; NaN where a cell holds no solid
  *   MAP_SOLID         : double[map_nz][map_ny]  solid fraction of each map
  *                      cell (exact, from the pore's circle)
+ *   MAP_T_LOCAL       : double[map_nz][map_ny]  local temperature T - T_0 of
+ *                      each map cell: MAP_T plus the imposed linear T_eq(z) -
+ *                      T_0 = (z - pitch/2) dT/dz at the cell's centre (T_0 the
+ *                      control temperature, reached at the unit cell's mid-
+ *                      plane z = pitch/2); NaN where a cell holds no solid
  * Errors: LE_MC_ERR_INVALID (array not produced by this run, capacity too
  * small), LE_MC_ERR_STATE, LE_MC_ERR_CUDA. */
 enum { LE_MC_ARRAY_T = 0, LE_MC_ARRAY_T_SE = 1, LE_MC_ARRAY_Q = 2, LE_MC_ARRAY_Q_SE = 3,
        LE_MC_ARRAY_H = 4, LE_MC_ARRAY_H_SE = 5, LE_MC_ARRAY_GRID = 6, LE_MC_ARRAY_PARTICLES = 7,
        LE_MC_ARRAY_GRID_T = 8, LE_MC_ARRAY_GRID_TX = 9, LE_MC_ARRAY_GRID_T_SE = 10, LE_MC_ARRAY_GRID_TX_SE = 11,
        LE_MC_ARRAY_MAP_T = 12, LE_MC_ARRAY_MAP_T_SE = 13, LE_MC_ARRAY_MAP_Q = 14, LE_MC_ARRAY_MAP_Q_SE = 15,
-       LE_MC_ARRAY_MAP_SOLID = 16 };
+       LE_MC_ARRAY_MAP_SOLID = 16, LE_MC_ARRAY_MAP_T_LOCAL = 17 };
 LE_MC_API le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size_t capacity,
                               size_t* written);
 

@@ -50,7 +50,7 @@ def simulate(problem, stream=None, arrays=True, record_particles=False, launch=N
                         out["T_x_se"] = le_mc_read_array(h, "grid_Tx_se").reshape(run["n_samples"], gx)
                     if tuple(run.get("map", (0, 0))) != (0, 0):
                         my, mz = run["map"]
-                        for k in ("map_T", "map_T_se", "map_q", "map_q_se", "map_solid"):
+                        for k in ("map_T", "map_T_se", "map_q", "map_q_se", "map_solid", "map_T_local"):
                             out[k] = le_mc_read_array(h, k).reshape(mz, my)
                 if record_particles:
                     out["particles_rec"] = le_mc_read_array(h, "particles")

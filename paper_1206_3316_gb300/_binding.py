@@ -29,7 +29,7 @@ SRC = {"walls": 0, "gradient": 1, "pulse": 2, "initial": 3}
 PREC = {"fp64": 0, "fp32": 1}
 ARRAY = {"T": 0, "T_se": 1, "q": 2, "q_se": 3, "H": 4, "H_se": 5, "grid": 6, "particles": 7,
          "grid_T": 8, "grid_Tx": 9, "grid_T_se": 10, "grid_Tx_se": 11,
-         "map_T": 12, "map_T_se": 13, "map_q": 14, "map_q_se": 15, "map_solid": 16}
+         "map_T": 12, "map_T_se": 13, "map_q": 14, "map_q_se": 15, "map_solid": 16, "map_T_local": 17}
 MAX_BRANCHES = 4
 
 

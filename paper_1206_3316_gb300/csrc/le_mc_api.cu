@@ -591,7 +591,7 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
         bytes = (size_t)r.n_samples * r.grid_nx * sizeof(double);
         break;
     case LE_MC_ARRAY_MAP_T: case LE_MC_ARRAY_MAP_T_SE: case LE_MC_ARRAY_MAP_Q: case LE_MC_ARRAY_MAP_Q_SE:
-    case LE_MC_ARRAY_MAP_SOLID:
+    case LE_MC_ARRAY_MAP_SOLID: case LE_MC_ARRAY_MAP_T_LOCAL:
         if (r.map_ny <= 0 || r.map_nz <= 0) return fail(LE_MC_ERR_INVALID, "le_mc_read_array: run has no maps");
         bytes = (size_t)r.map_ny * r.map_nz * sizeof(double);
         break;
@@ -627,14 +627,24 @@ le_mc_status le_mc_read_array(le_mc_run_handle h, int32_t which, void* dst, size
                 finalize_grid_tx(&h->geo->desc, &r, h->mat->sums, t.E_eff, counts.data(), se ? nullptr : out,
                                  se ? out : nullptr);
         }
-    } else if (which >= LE_MC_ARRAY_MAP_T && which <= LE_MC_ARRAY_MAP_SOLID) {
+    } else if (which >= LE_MC_ARRAY_MAP_T && which <= LE_MC_ARRAY_MAP_T_LOCAL) {
         const size_t cells = (size_t)r.map_ny * r.map_nz;
         std::vector<double> raw(h->prof_len), out(5 * cells);
         e = cudaMemcpy(raw.data(), h->dev + h->off_prof, raw.size() * sizeof(double), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess) {
             finalize_map(&h->geo->desc, &r, h->mat->sums, raw.data(), out.data(), out.data() + cells,
                          out.data() + 2 * cells, out.data() + 3 * cells, out.data() + 4 * cells);
-            memcpy(dst, out.data() + (size_t)(which - LE_MC_ARRAY_MAP_T) * cells, bytes);
+            if (which == LE_MC_ARRAY_MAP_T_LOCAL) {
+                // add the imposed linear T_eq(z) - T_0 at each cell's centre
+                const le_mc_geometry_desc& G = h->geo->desc;
+                const double dz = G.pitch / r.map_nz;
+                for (int k = 0; k < r.map_nz; ++k)
+                    for (int j = 0; j < r.map_ny; ++j)
+                        out[(size_t)k * r.map_ny + j] += ((k + 0.5) * dz - 0.5 * G.pitch) * r.dTdz;
+                memcpy(dst, out.data(), bytes);
+            } else {
+                memcpy(dst, out.data() + (size_t)(which - LE_MC_ARRAY_MAP_T) * cells, bytes);
+            }
         }
     } else if (which == LE_MC_ARRAY_PARTICLES) {
         e = cudaMemcpy(dst, h->dev + h->off_records, bytes, cudaMemcpyDeviceToHost);

@@ -57,6 +57,16 @@ def test_silicon_maps_against_oracle(P, oracle):
     assert np.nansum(g["map_q"] * V) == pytest.approx(g["flux"] * (100e-9) ** 2 * 300e-9, rel=1e-5)
     assert min(map_symmetry_pvalues(g)) > 1e-3, map_symmetry_pvalues(g)
     assert g["device_flags"] == 0
+    # the local temperature adds the imposed T_eq(z): it falls along z, is odd
+    # about the mid-plane, and the deviation bends it around the pore
+    zc = (np.arange(8) + 0.5) * (100e-9 / 8) - 50e-9
+    has = g["map_solid"] > 0
+    assert np.array_equal(np.isnan(g["map_T_local"]), ~has)
+    np.testing.assert_allclose((g["map_T_local"] - g["map_T"])[has], ((zc * -1e7)[:, None] * np.ones((1, 8)))[has],
+                               rtol=1e-12, atol=1e-12)
+    rows = np.nanmean(g["map_T_local"], axis=1)
+    assert np.all(np.diff(rows) < 0)
+    np.testing.assert_allclose(g["map_T_local"], -g["map_T_local"][::-1, :], atol=6 * np.nanmax(g["map_T_se"]))
     print(f"\nmap T range {np.nanmin(g['map_T']):.3f} .. {np.nanmax(g['map_T']):.3f} K, "
           f"q_z range {np.nanmin(g['map_q']):.3e} .. {np.nanmax(g['map_q']):.3e} W/m^2, "
           f"largest T error {np.nanmax(g['map_T_se']):.4f} K")
