@@ -415,3 +415,37 @@ def kappa_first_event_porous(mat, L, pitch, radius, m=18, scrambles=4, chunk=409
         vals.append(0.5 * frac * total)
     vals = np.array(vals)
     return float(vals.mean()), float(vals.std(ddof=1) / math.sqrt(len(vals))) if len(vals) > 1 else 0.0
+
+
+def ballistic_slab_fractions(L, x_lo, x_hi, v, times, nx, n_mu=20000):
+    """Free streaming between specular walls: particles start uniformly in
+    x_lo < x < x_hi at t = 0 with isotropic directions (mu_x uniform on
+    [-1, 1]) and speed v, never relax, and reflect specularly at x = 0 and
+    x = L.  Returns the fraction of them in each of nx equal slabs of [0, L]
+    at each time (array [len(times)][nx]).
+
+    Mirror-unfolding the walls, a particle at x0 moving with mu sits at fold(x0
+    + mu v t), fold the reflection of the line onto [0, L] (period 2L).  For a
+    given displacement D the starting interval [x_lo + D, x_hi + D] is cut
+    by the images 2nL + [a, b] and 2nL - [b, a] of slab [a, b]; the lengths of
+    those pieces over x_hi - x_lo are the slab fractions, exact for each mu,
+    and the midpoint rule over n_mu values of mu does the direction average
+    (the integrand is continuous and piecewise smooth in mu)."""
+    times = np.asarray(times, dtype=float)
+    mu = (np.arange(n_mu) + 0.5) / n_mu * 2.0 - 1.0
+    edges = np.linspace(0.0, L, nx + 1)
+    out = np.zeros((times.size, nx))
+    w = x_hi - x_lo
+    for it, t in enumerate(times):
+        D = mu * v * t
+        lo, hi = x_lo + D, x_hi + D
+        nmin = int(np.floor(lo.min() / (2 * L))) - 1
+        nmax = int(np.ceil(hi.max() / (2 * L))) + 1
+        for j in range(nx):
+            a, b = edges[j], edges[j + 1]
+            acc = np.zeros(n_mu)
+            for n in range(nmin, nmax + 1):
+                for ia, ib in ((2 * n * L + a, 2 * n * L + b), (2 * n * L - b, 2 * n * L - a)):
+                    acc += np.clip(np.minimum(hi, ib) - np.maximum(lo, ia), 0.0, None)
+            out[it, j] = float(np.mean(acc)) / w
+    return out

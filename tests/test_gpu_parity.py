@@ -416,6 +416,31 @@ def test_first_event_pored_film_against_quadrature(P, analytic):
     assert abs(g["kappa"] / pin - 1.0) < 2e-3
 
 
+def test_ballistic_spreading_between_specular_faces(P, oracle, analytic):
+    # a never-relaxing initial excess between specular faces: FP64 counts are
+    # the oracle's exactly, FP32 counts of 1e7 particles follow the folded
+    # free-streaming fractions slab by slab and sample by sample
+    L, v, dt, ns, nx = 300e-9, 1000.0, 20e-12, 30, 10
+
+    def prob(n, precision):
+        p = W.porous_initial(n_particles=n, precision=precision, material=dict(W.GRAY_UNIT, tau=1.0, v=v),
+                             x_range=(200e-9, 260e-9), grid=(nx, 1, 1), n_samples=ns, sample_dt=dt,
+                             t_final=ns * dt, radius=0.0)
+        p["geometry"].update(wall_lo="specular", wall_hi="specular")
+        return p
+
+    q = prob(50_000, "fp64")
+    np.testing.assert_array_equal(P.simulate(q)["grid"], oracle.run(q)["grid"])
+    n = 10_000_000
+    g = P.simulate(prob(n, "fp32"))
+    frac = analytic.ballistic_slab_fractions(L, 200e-9, 260e-9, v, (np.arange(ns) + 0.5) * dt, nx)
+    c = g["grid"].reshape(ns, nx).astype(float)
+    e = frac * n
+    z = np.where(e > 5, (c - e) / np.sqrt(np.maximum(e * (1.0 - frac), 1e-300)), 0.0)
+    assert np.abs(z).max() < 5.0, np.abs(z).max()
+    assert np.all(c[frac == 0] == 0) and g["device_flags"] == 0
+
+
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
     # picks): below the pore-free film times the solid fraction, and the same

@@ -92,6 +92,14 @@ def _first_event_pin_ok(oracle, analytic, library):
     return abs(first_event_pin_z(oracle, dict(W.GRAY_UNIT, tau=5e-8, v=1.0), 45e-9, n=400_000, library=library)) < 4.0
 
 
+def _ballistic_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_porous import ballistic_spread_zmax
+    try:
+        return ballistic_spread_zmax(oracle, library=library, n=100_000) < 5.0
+    except AssertionError:
+        return False
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -133,6 +141,8 @@ MUTATIONS = [
      "T[(size_t)j * nz + k] += s->sign * ((b - a) / vg);\n            q[(size_t)j * nz + k]", _map_pin_ok),
     ("steady map time tallied without the particle's sign", "T[(size_t)k * ny + j] += s->sign * ((b - a) / vg);",
      "T[(size_t)k * ny + j] += (b - a) / vg;", _map_pin_ok),
+    ("sample positions interpolated from t = 0 instead of the segment start",
+     "double d = vg * (ts - t_a);", "double d = vg * ts;", _ballistic_pin_ok),
     ("gradient-source positions not restricted to the solid",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                if (!in_pore(p, yl, zl)) break;",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                break;", _first_event_pin_ok),

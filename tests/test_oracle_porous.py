@@ -12,6 +12,9 @@
   exactly, the mirror symmetries of the unit cell (T odd in z about the
   pore, even in y; the z flux even in both), and the flat maps of a film
   without pores;
+* free streaming between specular faces: an initial excess that never
+  relaxes spreads as the folded kinematics predict slab by slab and sample
+  by sample (the Eq. 3 positions interpolated at the sample times);
 * first-event truncation (max_events = 1) in the pored cell: each particle's
   mean contribution is |mu_z| Lambda (1 - exp(-d / Lambda)) for its distance d
   to the first boundary, and the quasi-Monte Carlo mean of that (numpy ray
@@ -295,3 +298,27 @@ def test_first_event_pored_film_against_quadrature(oracle, lam, radius):
 def test_first_event_silicon_pored_film_against_quadrature(oracle):
     z = first_event_pin_z(oracle, W.SILICON_LIKE, 30e-9, m=15)
     assert abs(z) < 4.0, z
+
+
+def ballistic_spread_zmax(oracle, seed=5, library=None, n=200_000):
+    """Largest |z| of the slab counts of a never-relaxing initial excess
+    between specular faces against the folded free-streaming fractions."""
+    from oracle import analytic
+    L, v, dt, ns, nx = 300e-9, 1000.0, 20e-12, 30, 10
+    p = W.porous_initial(n_particles=n, seed=seed, precision="fp64", material=dict(W.GRAY_UNIT, tau=1.0, v=v),
+                         x_range=(200e-9, 260e-9), grid=(nx, 1, 1), n_samples=ns, sample_dt=dt, t_final=ns * dt,
+                         radius=0.0)
+    p["geometry"].update(wall_lo="specular", wall_hi="specular")
+    o = oracle.run(p, library=library)
+    frac = analytic.ballistic_slab_fractions(L, 200e-9, 260e-9, v, (np.arange(ns) + 0.5) * dt, nx)
+    c = o["grid"].reshape(ns, nx).astype(float)
+    e = frac * n
+    sd = np.sqrt(np.maximum(e * (1.0 - frac), 1e-300))
+    z = np.where(e > 5, (c - e) / sd, 0.0)
+    # slabs the kinematics leave empty must stay empty
+    assert np.all(c[frac == 0] == 0)
+    return float(np.max(np.abs(z)))
+
+
+def test_ballistic_spreading_between_specular_faces(oracle):
+    assert ballistic_spread_zmax(oracle) < 5.0
