@@ -441,6 +441,12 @@ def test_ballistic_spreading_between_specular_faces(P, oracle, analytic):
     assert np.all(c[frac == 0] == 0) and g["device_flags"] == 0
 
 
+def test_pulse_emission_times_fp32(P):
+    # grid totals of 1e7 FP32 particles against the truncated Gaussian time law
+    from tests.test_oracle_porous import pulse_totals_zmax
+    assert pulse_totals_zmax(None, n=10_000_000, precision="fp32", run=P.simulate) < 5.0
+
+
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
     # picks): below the pore-free film times the solid fraction, and the same

@@ -15,6 +15,10 @@
 * free streaming between specular faces: an initial excess that never
   relaxes spreads as the folded kinematics predict slab by slab and sample
   by sample (the Eq. 3 positions interpolated at the sample times);
+* surface pulse emission times: with adiabatic faces every particle emitted
+  before a sample time is counted at it, so the grid total at t_k is a
+  binomial draw of the Gaussian time law truncated at t >= 0 (negative
+  times redrawn);
 * first-event truncation (max_events = 1) in the pored cell: each particle's
   mean contribution is |mu_z| Lambda (1 - exp(-d / Lambda)) for its distance d
   to the first boundary, and the quasi-Monte Carlo mean of that (numpy ray
@@ -322,3 +326,25 @@ def ballistic_spread_zmax(oracle, seed=5, library=None, n=200_000):
 
 def test_ballistic_spreading_between_specular_faces(oracle):
     assert ballistic_spread_zmax(oracle) < 5.0
+
+
+def pulse_totals_zmax(oracle, library=None, n=200_000, precision="fp64", run=None):
+    """Largest |z| of the pulse's per-sample grid totals against N F(t_k),
+    F the Gaussian CDF of the emission time conditioned on t >= 0.  ``run``
+    replaces the oracle (the GPU tests pass the library's simulate)."""
+    from scipy.stats import norm
+    tc, st, dt, ns = 50e-12, 100e-12, 10e-12, 40
+    p = W.porous_pulse(n_particles=n, precision=precision, material=dict(W.GRAY_UNIT, tau=1e-10, v=1000.0),
+                       grid=(4, 6, 6), n_samples=ns, sample_dt=dt, t_final=ns * dt)
+    p["source"].update(t_center=tc, sigma_t=st)
+    r = run(p) if run is not None else oracle.run(p, library=library)
+    tot = r["grid"].reshape(ns, -1).sum(axis=1).astype(float)
+    tk = (np.arange(ns) + 0.5) * dt
+    p0 = norm.cdf(-tc / st)
+    F = (norm.cdf((tk - tc) / st) - p0) / (1.0 - p0)
+    sd = np.sqrt(n * F * (1.0 - F))
+    return float(np.max(np.abs(tot - n * F) / sd))
+
+
+def test_pulse_emission_times(oracle):
+    assert pulse_totals_zmax(oracle) < 5.0
