@@ -116,6 +116,8 @@ _lib = None
 def _bind(handle):
     handle.orc_run.restype = C.c_int
     handle.orc_run.argtypes = [C.POINTER(Problem), C.POINTER(Result)] + [C.c_void_p] * 9
+    handle.orc_emit.restype = C.c_int
+    handle.orc_emit.argtypes = [C.POINTER(Problem), C.c_uint64, C.c_int, C.c_void_p, C.c_void_p]
     return handle
 
 
@@ -301,13 +303,14 @@ def first_boundary(prob, pos, direction):
     return t, k.value
 
 
-def emit(prob, first, n):
+def emit(prob, first, n, library=None):
     """Initial states of particles first..first+n-1: columns (sign, x, y, z,
     ox, oy, oz, t0) and the mode ids."""
     p = to_problem(prob)
     out = np.zeros((n, 8))
     modes = np.zeros(n, dtype=np.int32)
-    rc = lib().orc_emit(C.byref(p), first, n, out.ctypes.data, modes.ctypes.data)
+    L = library if library is not None else lib()
+    rc = L.orc_emit(C.byref(p), first, n, out.ctypes.data, modes.ctypes.data)
     if rc:
         raise ValueError("oracle rejected the problem")
     return out, modes

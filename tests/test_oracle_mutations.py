@@ -105,6 +105,11 @@ def _pulse_time_pin_ok(oracle, analytic, library):
     return pulse_totals_zmax(oracle, library=library, n=100_000) < 5.0
 
 
+def _pulse_lateral_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_porous import pulse_lateral_pvalues
+    return min(pulse_lateral_pvalues(oracle, library=library)) > 1e-3
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -150,6 +155,9 @@ MUTATIONS = [
      "double d = vg * (ts - t_a);", "double d = vg * ts;", _ballistic_pin_ok),
     ("pulse times below zero moved to zero instead of redrawn", "if (t0 >= 0.0) { s->t = t0; break; }",
      "if (t0 < 0.0) t0 = 0.0;\n            { s->t = t0; break; }", _pulse_time_pin_ok),
+    ("pulse lateral radius with a Gaussian variance halved",
+     "double r = p->pulse_sigma_x * sqrt(-2.0 * log(v[0]));", "double r = p->pulse_sigma_x * sqrt(-log(v[0]));",
+     _pulse_lateral_pin_ok),
     ("gradient-source positions not restricted to the solid",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                if (!in_pore(p, yl, zl)) break;",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                break;", _first_event_pin_ok),

@@ -15,6 +15,10 @@
 * free streaming between specular faces: an initial excess that never
   relaxes spreads as the folded kinematics predict slab by slab and sample
   by sample (the Eq. 3 positions interpolated at the sample times);
+* surface pulse lateral law and directions: without pores the emitted
+  positions are a 2-D Gaussian about (y0, z0), so r^2 / (2 sigma^2) is
+  exponential (KS), and directions follow the cosine law into the film
+  (|mu_x|^2 uniform, KS);
 * surface pulse emission times: with adiabatic faces every particle emitted
   before a sample time is counted at it, so the grid total at t_k is a
   binomial draw of the Gaussian time law truncated at t >= 0 (negative
@@ -348,3 +352,23 @@ def pulse_totals_zmax(oracle, library=None, n=200_000, precision="fp64", run=Non
 
 def test_pulse_emission_times(oracle):
     assert pulse_totals_zmax(oracle) < 5.0
+
+
+def pulse_lateral_pvalues(oracle, library=None, n=100_000):
+    """KS p-values of the pulse's emitted lateral radius (r^2 / 2 sigma^2
+    against Exp(1), minimum-image distance in the periodic domain) and of its
+    direction cosine into the film (mu_x^2 against U(0, 1)), without pores."""
+    from scipy import stats
+    p = W.porous_pulse(n_particles=n, grid=(4, 8, 8), n_samples=10, radius=0.0)
+    st, _ = oracle.emit(p, 0, n, library=library)
+    g, src = p["geometry"], p["source"]
+    Dy, Dz = g["pitch"] * g["cells_y"], g["pitch"] * g["cells_z"]
+    dy = np.mod(st[:, 2] - src["y0"] + 0.5 * Dy, Dy) - 0.5 * Dy
+    dz = np.mod(st[:, 3] - src["z0"] + 0.5 * Dz, Dz) - 0.5 * Dz
+    r2 = (dy * dy + dz * dz) / (2.0 * src["sigma_x"] ** 2)
+    return stats.kstest(r2, "expon").pvalue, stats.kstest(st[:, 4] ** 2, "uniform").pvalue
+
+
+def test_pulse_lateral_law_and_directions(oracle):
+    p_r, p_mu = pulse_lateral_pvalues(oracle)
+    assert p_r > 1e-3 and p_mu > 1e-3, (p_r, p_mu)
