@@ -208,7 +208,9 @@ typedef struct {
     uint32_t instance_id;           /* 4th counter word: independent streams     */
     uint32_t max_scatter;           /* terminate at this scattering event (0 = none) */
     uint32_t max_events;            /* terminate after this many segments (>= 1) */
-    int32_t n_bins_x;               /* WALLS: T(x), q(x) profile bins (0 = off)   */
+    int32_t n_bins_x;               /* profile bins along x (0 = off): WALLS,
+                                     * T(x) and q_x(x); GRADIENT between planes,
+                                     * T(x) and the in-plane flux q_z(x)        */
     int32_t n_batch;                /* batch groups of the error bars: slab
                                      * profiles group particle ids mod n_batch,
                                      * maps group particle pairs (2i, 2i + 1)
@@ -305,8 +307,11 @@ LE_MC_API le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out
 
 /* Arrays of a finished run, copied into caller memory of `capacity` bytes
  * (*written receives the byte count; call with dst = NULL to query it):
- *   T, T_SE, Q, Q_SE : double[n_bins_x]  slab temperature T - T_eq (energy
- *                      temperature) and heat flux per bin, batch-mean errors
+ *   T, T_SE, Q, Q_SE : double[n_bins_x]  temperature T - T_eq (energy
+ *                      temperature) of each slab along x and the heat flux
+ *                      there along the flux axis (x for WALLS; z for
+ *                      GRADIENT: the in-plane flux of a film by depth), with
+ *                      batch-mean errors
  *   H, H_SE          : double[n_hj]      flux carried between scattering
  *                      events j and j+1 (j = 0: emission to first scattering)
  *   GRID             : int32[n_samples][grid_nz][grid_ny][grid_nx] signed

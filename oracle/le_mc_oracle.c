@@ -535,12 +535,21 @@ static double first_boundary(const orc_problem* p, const orc_state* s, int* kind
 /* ------------------------------------------------------------------------ */
 /* Step V: sample the contribution of a segment.                             */
 /* ------------------------------------------------------------------------ */
+/* Slab profiles along x (Eq. 4 per bin): the time a segment spends in each
+ * bin, and the displacement it makes there along the flux axis -- x for the
+ * walls source, z for the gradient source (the in-plane flux of a film by
+ * depth: the z displacement over an x-length len is len |oz / ox|, signed by
+ * oz).  Batch groups: particle ids mod n_batch, or particle pairs (2i, 2i + 1)
+ * for the gradient source, whose even and odd ids carry opposite signs. */
 static void tally_slab_bins(const orc_problem* p, const orc_mat* m, orc_tally* tl, uint64_t pid,
-                            int sign, double xa, double xb, double ox, double dt_seg, int mode)
+                            int sign, double xa, double xb, double ox, double oz, double seg, double dt_seg,
+                            int mode)
 {
+    const int grad = p->src_kind == ORC_SRC_GRADIENT;
     int nb = p->n_bins_x;
     double dx = p->L / nb;
-    int g = (int)(pid % (uint64_t)(p->n_batch > 0 ? p->n_batch : 1));
+    uint64_t B = (uint64_t)(p->n_batch > 0 ? p->n_batch : 1);
+    int g = (int)((grad ? pid >> 1 : pid) % B);
     double* T = tl->T_sum + (size_t)g * nb;
     double* q = tl->q_sum + (size_t)g * nb;
     double lo = fmin(xa, xb), hi = fmax(xa, xb);
@@ -551,6 +560,7 @@ static void tally_slab_bins(const orc_problem* p, const orc_mat* m, orc_tally* t
     if (k1 < 0) k1 = 0;
     if (ox == 0.0) { /* a flight parallel to the walls stays in one bin */
         T[k0] += sign * dt_seg;
+        if (grad) q[k0] += sign * (oz * seg);
         return;
     }
     double speed_x = m->v[mode] * fabs(ox);
@@ -561,7 +571,10 @@ static void tally_slab_bins(const orc_problem* p, const orc_mat* m, orc_tally* t
         double len = b - a;
         if (len <= 0.0) continue;
         T[k] += sign * (len / speed_x);
-        q[k] += sign * (ox > 0.0 ? len : -len);
+        if (grad)
+            q[k] += sign * (len * oz / fabs(ox));
+        else
+            q[k] += sign * (ox > 0.0 ? len : -len);
     }
 }
 
@@ -771,7 +784,7 @@ static void trace_particle(const orc_problem* p, const orc_mat* m, uint64_t pid,
         double x_new = s.x + dxs;
         if (hit && kind == HIT_XLO) x_new = 0.0;
         if (hit && kind == HIT_XHI) x_new = p->L;
-        if (p->n_bins_x > 0) tally_slab_bins(p, m, tl, pid, s.sign, xa, x_new, s.ox, dt_seg, s.mode);
+        if (p->n_bins_x > 0) tally_slab_bins(p, m, tl, pid, s.sign, xa, x_new, s.ox, s.oz, seg, dt_seg, s.mode);
         if (map_cells(p) > 0) tally_map(p, m, tl, pid, &s, seg);
         double dL = axis_x ? (x_new - xa) : dz;
         L_axis += dL;
@@ -1061,8 +1074,17 @@ int orc_run(const orc_problem* p, orc_result* res, double* T_mean, double* T_se,
             for (int k = 0; k < nb; ++k) {
                 double sT = 0, sT2 = 0, sq = 0, sq2 = 0;
                 for (int g = 0; g < B; ++g) {
-                    /* group g holds the particles with id = g mod B */
-                    double ng = (double)(N / B + ((uint64_t)g < N % B ? 1 : 0));
+                    /* group g holds the particles with id = g mod B, or (gradient
+                     * source) the particle pairs (2q, 2q + 1) with q = g mod B */
+                    double ng = 0.0;
+                    if (p->src_kind == ORC_SRC_GRADIENT) {
+                        for (uint64_t e = 0; e < 2; ++e) {
+                            uint64_t Q = N > e ? (N - e + 1) / 2 : 0;
+                            ng += (double)(Q / B + ((uint64_t)g < Q % B ? 1 : 0));
+                        }
+                    } else {
+                        ng = (double)(N / B + ((uint64_t)g < N % B ? 1 : 0));
+                    }
                     if (ng <= 0) ng = 1;
                     double Tg = P / ng * tot.T_sum[(size_t)g * nb + k] / (m.C_tot * dx);
                     double qg = P / ng * tot.q_sum[(size_t)g * nb + k] / dx;

@@ -301,7 +301,10 @@ int check_run(const le_mc_geometry_desc* g, const le_mc_run_desc* r, int n_modes
     }
     if (r->n_bins_x < 0 || r->n_bins_x > LE_MC_MAX_BINS_X) { *why = "n_bins_x out of range"; return LE_MC_ERR_INVALID; }
     if (r->n_bins_x > 0) {
-        if (r->source != LE_MC_SRC_WALLS) { *why = "profiles need the WALLS source"; return LE_MC_ERR_INVALID; }
+        if (r->source != LE_MC_SRC_WALLS && !(r->source == LE_MC_SRC_GRADIENT && g->kind == LE_MC_GEOM_PLANES)) {
+            *why = "profiles need the WALLS source, or the GRADIENT source between planes";
+            return LE_MC_ERR_INVALID;
+        }
         if (r->n_batch < 1 || r->n_batch > LE_MC_MAX_BATCH) { *why = "n_batch out of 1..64"; return LE_MC_ERR_INVALID; }
     }
     if (r->map_ny < 0 || r->map_nz < 0 || r->map_ny > LE_MC_MAX_MAP || r->map_nz > LE_MC_MAX_MAP ||
@@ -455,7 +458,17 @@ void finalize_profile(const le_mc_geometry_desc* g, const le_mc_run_desc* r, con
     for (int k = 0; k < nb; ++k) {
         double sT = 0.0, sq = 0.0, sT2 = 0.0, sq2 = 0.0, totT = 0.0, totq = 0.0;
         for (int b = 0; b < B; ++b) {
-            double ng = (double)(N / B + ((unsigned long long)b < N % B ? 1 : 0));
+            // particles in group b: ids b mod B, or (gradient source) the
+            // particle pairs (2q, 2q + 1) with q = b mod B
+            double ng = 0.0;
+            if (r->source == LE_MC_SRC_GRADIENT) {
+                for (unsigned long long e = 0; e < 2; ++e) {
+                    const unsigned long long Q = N > e ? (N - e + 1) / 2 : 0;
+                    ng += (double)(Q / B + ((unsigned long long)b < Q % B ? 1 : 0));
+                }
+            } else {
+                ng = (double)(N / B + ((unsigned long long)b < N % B ? 1 : 0));
+            }
             if (ng <= 0.0) ng = 1.0;
             const double Tg = P / ng * tb[(size_t)b * nb + k] / (ms.C_tot * dx);
             const double qg = P / ng * qb[(size_t)b * nb + k] / dx;

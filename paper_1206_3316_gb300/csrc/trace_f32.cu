@@ -42,6 +42,8 @@ cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t*
         return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, true>(__VA_ARGS__);                            \
     if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_WALLS)                                         \
         return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false>(__VA_ARGS__);                           \
+    if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_GRADIENT && profile)                           \
+        return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, true>(__VA_ARGS__);                         \
     if (geom == LE_MC_GEOM_PLANES && src == LE_MC_SRC_GRADIENT)                                      \
         return FN<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false>(__VA_ARGS__);                        \
     if (geom == LE_MC_GEOM_BULK && src == LE_MC_SRC_GRADIENT)                                        \

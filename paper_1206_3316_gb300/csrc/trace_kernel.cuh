@@ -725,10 +725,16 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             }
         }
         if constexpr (PROFILE && !POROUS) {
-            // time and x-displacement spent in each bin along x (slab)
+            // time spent in each bin along x, and the displacement along the
+            // flux axis made there: x for the walls source (slab), z for the
+            // gradient source (the in-plane flux of a film by depth)
             const int nb = P.n_bins_x;
             const R dx = L / (R)nb;
-            const int g = (int)((pid - P.first) % (uint32_t)P.n_batch);
+            // batch group: particle ids mod n_batch, or particle pairs (2i,
+            // 2i + 1) for the gradient source, whose even and odd ids carry
+            // opposite signs
+            const int g = AXIS_X ? (int)((pid - P.first) % (uint32_t)P.n_batch)
+                                 : (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
             const size_t stride = (size_t)nb + 1;
             double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
             double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
@@ -743,9 +749,11 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const double s = (double)sign;
             if (ox == R(0)) {
                 atomicAdd(&Td[k0], s * (double)(seg / vg));
+                if constexpr (!AXIS_X) atomicAdd(&qd[k0], s * (double)(oz * seg));
             } else {
                 const R w = R(1) / (vg * fabs(ox));  // time per unit x
-                const R qs = ox > R(0) ? R(1) : R(-1);
+                // displacement along the flux axis per unit x
+                const R qs = AXIS_X ? (ox > R(0) ? R(1) : R(-1)) : M::div(oz, fabs(ox));
                 if (k0 == k1) {
                     const R len = hi - lo;
                     atomicAdd(&Td[k0], s * (double)(len * w));

@@ -447,6 +447,27 @@ def test_pulse_emission_times_fp32(P):
     assert pulse_totals_zmax(None, n=10_000_000, precision="fp32", run=P.simulate) < 5.0
 
 
+def test_film_in_plane_flux_by_depth(P, oracle, analytic):
+    # q_z(x) of a film under the gradient source: an FP64 gray film gives the
+    # oracle's profile (same particles), and 1e7 FP32 silicon-like particles
+    # follow the depth form of the Fuchs-Sondheimer solution bin by bin
+    from scipy import stats
+    mat = dict(W.GRAY_UNIT, tau=2e-8, v=1.0)
+    p = W.silicon_film(n_particles=50_000, thickness=40e-9, material=mat, precision="fp64", dTdz=-1e6, max_scatter=40)
+    p["run"].update(n_bins_x=10, n_batch=16)
+    g, o = P.simulate(p), oracle.run(p)
+    for k in ("q", "q_se", "T", "T_se"):
+        np.testing.assert_allclose(g[k], o[k], rtol=1e-9, atol=1e-9 * np.abs(o[k]).max(), err_msg=k)
+    f = W.silicon_film(n_particles=10_000_000)
+    f["run"].update(n_bins_x=20, n_batch=32)
+    g = P.simulate(f)
+    pin = analytic.film_flux_profile(W.SILICON_LIKE, 100e-9, 20, dTdz=f["source"]["dTdz"])
+    z = (g["q"] - pin) / g["q_se"]
+    assert stats.chi2.sf(np.sum(z ** 2), z.size) > 1e-3, np.round(z, 2)
+    assert stats.chi2.sf(np.sum((g["T"] / g["T_se"]) ** 2), 20) > 1e-3
+    assert np.mean(g["q"]) == pytest.approx(g["flux"], rel=1e-5)
+
+
 def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     # config-2 steady at full size (1e8 particles, the launch shape le_mc_run
     # picks): below the pore-free film times the solid fraction, and the same

@@ -110,6 +110,14 @@ def _pulse_lateral_pin_ok(oracle, analytic, library):
     return min(pulse_lateral_pvalues(oracle, library=library)) > 1e-3
 
 
+def _film_profile_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_transport import film_profile_pvalues
+    try:
+        return min(film_profile_pvalues(oracle, analytic, library=library)) > 1e-3
+    except AssertionError:  # the bins no longer partition the flux
+        return False
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -158,6 +166,8 @@ MUTATIONS = [
     ("pulse lateral radius with a Gaussian variance halved",
      "double r = p->pulse_sigma_x * sqrt(-2.0 * log(v[0]));", "double r = p->pulse_sigma_x * sqrt(-log(v[0]));",
      _pulse_lateral_pin_ok),
+    ("in-plane flux by depth without the 1/|ox| of the path's slope", "q[k] += sign * (len * oz / fabs(ox));",
+     "q[k] += sign * (len * oz);", _film_profile_pin_ok),
     ("gradient-source positions not restricted to the solid",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                if (!in_pore(p, yl, zl)) break;",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                break;", _first_event_pin_ok),

@@ -301,3 +301,30 @@ def test_truncation_study_predicts_dropped_flux(oracle):
     f = oracle.run(W.silicon_film(n_particles=400_000, precision="fp64", n_hj=16))
     sf = study(f["H"], f["H_se"])
     assert sf["k_s"] <= 3 and np.all(np.abs(f["H"][1:]) < 4.0 * f["H_se"][1:])
+
+
+def film_profile_pvalues(oracle, analytic, L=40e-9, lam=2e-8, n=400_000, library=None):
+    """chi-square p-values of a gray film's depth profiles under the gradient
+    source: the in-plane flux q_z(x) against the depth form of the
+    Fuchs-Sondheimer solution, and T(x) against zero (no deviational
+    temperature in a uniformly driven film)."""
+    from scipy import stats
+    mat = dict(W.GRAY_UNIT, tau=lam, v=1.0)
+    p = W.silicon_film(n_particles=n, thickness=L, material=mat, precision="fp64", dTdz=-1e6, max_scatter=40)
+    p["run"].update(n_bins_x=10, n_batch=16)
+    o = oracle.run(p, library=library)
+    pin = analytic.film_flux_profile(mat, L, 10, dTdz=-1e6)
+    zq = (o["q"] - pin) / o["q_se"]
+    zT = o["T"] / o["T_se"]
+    assert np.mean(o["q"]) == pytest.approx(o["flux"], rel=1e-12)  # the bins partition the flux
+    return stats.chi2.sf(np.sum(zq ** 2), zq.size), stats.chi2.sf(np.sum(zT ** 2), zT.size)
+
+
+@pytest.mark.parametrize("L", [40e-9, 10e-9])
+def test_film_in_plane_flux_by_depth(oracle, analytic, L):
+    # the depth form of the thin-film solution: its slab means average to the
+    # Fuchs-Sondheimer factor, and the oracle's q_z(x) follows it bin by bin
+    assert np.mean(analytic.film_flux_profile(W.SILICON_LIKE, 100e-9, 20)) / 1e6 == pytest.approx(
+        analytic.kappa_film(W.SILICON_LIKE, 100e-9), rel=1e-6)
+    pq, pT = film_profile_pvalues(oracle, analytic, L=L)
+    assert pq > 1e-3 and pT > 1e-3, (pq, pT)
