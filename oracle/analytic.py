@@ -483,3 +483,83 @@ def film_flux_profile(mat, L, n_bins, dTdz=-1.0e6, n_mu=400):
         qb = (C[i:i + 256] * v[i:i + 256] * lam[i:i + 256] / 3.0)[:, None]
         out += np.sum(qb * (1.0 - red), axis=0)
     return out * abs(dTdz)
+
+
+def porous_free_path_distance(L, pitch, radius, pos, omega, max_cells=64):
+    """Distance along unit directions ``omega`` from points ``pos`` in the solid
+    of the unit cell [0, L] x [0, pitch]^2 to the first film face (x = 0, L) or
+    pore surface, the unit-cell faces being crossed freely (the periodic
+    lattice of pores, one centred in every pitch x pitch cell).  A pore lies
+    inside its cell (2 radius < pitch), so only the pores of the cells the
+    ray's (y, z) projection passes through can be hit: those cells are walked
+    in order (a 2-D cell walk), the first pore hit ending the walk.  Rays
+    still running after ``max_cells`` cells (probability < 1e-8 here) keep
+    their film-face distance.  Returns the distances and the number of rays
+    cut short."""
+    x, y, z = pos[:, 0], pos[:, 1], pos[:, 2]
+    ox, oy, oz = omega[:, 0], omega[:, 1], omega[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(ox > 0, (L - x) / ox, np.where(ox < 0, x / -ox, np.inf))
+        ci = np.floor(y / pitch)
+        cj = np.floor(z / pitch)
+        a = oy * oy + oz * oz
+        active = a > 0
+        t_in = np.zeros_like(d)
+        for _ in range(max_cells):
+            if not active.any():
+                break
+            # pore of the current cell: |(y, z) + t (oy, oz) - c| = radius
+            ry = y - (ci + 0.5) * pitch
+            rz = z - (cj + 0.5) * pitch
+            b = ry * oy + rz * oz
+            c = ry * ry + rz * rz - radius * radius
+            disc = b * b - a * c
+            t = (-b - np.sqrt(np.maximum(disc, 0.0))) / a
+            hit = active & (disc >= 0) & (t >= 0) & (radius > 0)
+            d = np.where(hit & (t < d), t, d)
+            # leave the cell through the face ahead in y or z
+            ty = np.where(oy > 0, ((ci + 1) * pitch - y) / oy, np.where(oy < 0, (ci * pitch - y) / oy, np.inf))
+            tz = np.where(oz > 0, ((cj + 1) * pitch - z) / oz, np.where(oz < 0, (cj * pitch - z) / oz, np.inf))
+            step_y = ty <= tz
+            t_in = np.minimum(ty, tz)
+            ci = np.where(step_y, ci + np.sign(oy), ci)
+            cj = np.where(step_y, cj, cj + np.sign(oz))
+            active = active & ~hit & (t_in < d)
+    return d, int(np.sum(active))
+
+
+def kappa_free_path_porous(mat, L, pitch, radius, m=17, scrambles=4, chunk=4096):
+    """Conductivity of a pored film (gradient along z) when every particle
+    stops at its first relaxation or film-face or pore hit, crossings of the
+    periodic unit-cell faces not counted (``max_collisions = 1``): the
+    ``kappa_first_event_porous`` construction with the distance to the first
+    boundary taken through the periodic lattice of pores.  Returns (kappa,
+    standard error of the scramble mean)."""
+    from scipy.stats import qmc
+    _, v, tau, C = mode_table(mat)
+    lam = v * tau
+    frac = 1.0 - math.pi * radius * radius / (pitch * pitch)
+    vals = []
+    for r in range(scrambles):
+        u = qmc.Sobol(d=5, scramble=True, seed=1206 + r).random_base2(m)
+        pos = np.column_stack([u[:, 0] * L, u[:, 1] * pitch, u[:, 2] * pitch])
+        solid = (pos[:, 1] - 0.5 * pitch) ** 2 + (pos[:, 2] - 0.5 * pitch) ** 2 >= radius ** 2
+        pos, u = pos[solid], u[solid]
+        w = u[:, 3]
+        mu = np.where(w < 0.5, -np.sqrt(np.abs(1.0 - 2.0 * w)), np.sqrt(np.abs(2.0 * w - 1.0)))
+        phi = 2.0 * np.pi * u[:, 4]
+        s = np.sqrt(np.maximum(0.0, 1.0 - mu * mu))
+        omega = np.column_stack([s * np.cos(phi), s * np.sin(phi), mu])
+        d, _ = porous_free_path_distance(L, pitch, radius, pos, omega)
+        amu = np.abs(mu)
+        total = 0.0
+        for i in range(0, lam.size, 64):
+            lb = lam[i:i + 64]
+            acc = np.zeros(lb.size)
+            for j in range(0, d.size, chunk):
+                dd, aa = d[j:j + chunk, None], amu[j:j + chunk, None]
+                acc += np.sum(aa * lb[None, :] * -np.expm1(-dd / lb[None, :]), axis=0)
+            total += float(np.sum(C[i:i + 64] * v[i:i + 64] * acc / d.size))
+        vals.append(0.5 * frac * total)
+    vals = np.array(vals)
+    return float(vals.mean()), float(vals.std(ddof=1) / math.sqrt(len(vals)))

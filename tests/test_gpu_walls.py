@@ -80,6 +80,18 @@ def test_first_free_path_overestimates_pored_film(P, oracle):
     assert _z(first, o, "kappa") < 3.0
 
 
+def test_first_free_path_pored_film_against_quadrature(P, analytic):
+    # config-2 steady at full size, max_collisions = 1, FP32: against the
+    # quasi-Monte Carlo first-free-path conductivity through the periodic
+    # lattice of pores (numpy ray algebra)
+    pin, pin_se = analytic.kappa_free_path_porous(W.SILICON_LIKE, 300e-9, 100e-9, 30e-9, m=16)
+    g = P.simulate(W.with_run(W.porous_film(n_particles=100_000_000), max_collisions=1), arrays=False)
+    z = (g["kappa"] - pin) / np.hypot(g["kappa_se"], pin_se)
+    print(f"\nfirst free path, pored film: GPU {g['kappa']:.4f} +- {g['kappa_se']:.4f}, "
+          f"quadrature {pin:.4f} +- {pin_se:.4f}")
+    assert abs(z) < 4.0, z
+
+
 def test_invalid_specularity_rejected(P):
     prob = W.silicon_film(n_particles=10, specularity=1.5)
     with pytest.raises(Exception):

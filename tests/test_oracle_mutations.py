@@ -118,6 +118,11 @@ def _film_profile_pin_ok(oracle, analytic, library):
         return False
 
 
+def _free_path_pin_ok(oracle, analytic, library):
+    from tests.test_oracle_porous import free_path_pin_z
+    return abs(free_path_pin_z(oracle, dict(W.GRAY_UNIT, tau=2e-7, v=1.0), 30e-9, n=400_000, library=library)) < 4.0
+
+
 MUTATIONS = [
     ("diffuse wall re-emission not Lambertian", "dir_axis(0, sqrt(u[2]), u[3], &s.ox, &s.oy, &s.oz);",
      "dir_axis(0, u[2], u[3], &s.ox, &s.oy, &s.oz);", _uniform_pin_ok),
@@ -168,6 +173,8 @@ MUTATIONS = [
      _pulse_lateral_pin_ok),
     ("in-plane flux by depth without the 1/|ox| of the path's slope", "q[k] += sign * (len * oz / fabs(ox));",
      "q[k] += sign * (len * oz);", _film_profile_pin_ok),
+    ("first-free-path cap also counting crossings of periodic unit-cell faces",
+     "n_scat + n_wall >= p->max_collisions", "n_scat + n_wall + n_per >= p->max_collisions", _free_path_pin_ok),
     ("gradient-source positions not restricted to the solid",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                if (!in_pore(p, yl, zl)) break;",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                break;", _first_event_pin_ok),

@@ -23,6 +23,9 @@
   before a sample time is counted at it, so the grid total at t_k is a
   binomial draw of the Gaussian time law truncated at t >= 0 (negative
   times redrawn);
+* first-free-path truncation (max_collisions = 1): the same construction with
+  the distance to the first film face or pore taken through the periodic
+  lattice of pores (a 2-D walk over the unit cells the ray crosses);
 * first-event truncation (max_events = 1) in the pored cell: each particle's
   mean contribution is |mu_z| Lambda (1 - exp(-d / Lambda)) for its distance d
   to the first boundary, and the quasi-Monte Carlo mean of that (numpy ray
@@ -372,3 +375,24 @@ def pulse_lateral_pvalues(oracle, library=None, n=100_000):
 def test_pulse_lateral_law_and_directions(oracle):
     p_r, p_mu = pulse_lateral_pvalues(oracle)
     assert p_r > 1e-3 and p_mu > 1e-3, (p_r, p_mu)
+
+
+def free_path_pin_z(oracle, mat, radius, n=1_000_000, library=None, m=16):
+    """z-score of the oracle's first-free-path pored-film conductivity against
+    the quasi-Monte Carlo value through the periodic lattice of pores."""
+    from oracle import analytic
+    pin, pin_se = analytic.kappa_free_path_porous(mat, 300e-9, 100e-9, radius, m=m)
+    prob = W.with_run(W.porous_film(n_particles=n, precision="fp64", material=mat, radius=radius), max_collisions=1)
+    o = oracle.run(prob, library=library)
+    return (o["kappa"] - pin) / np.hypot(o["kappa_se"], pin_se)
+
+
+@pytest.mark.parametrize("lam,radius", [(2e-8, 30e-9), (2e-7, 30e-9), (5e-8, 45e-9)])
+def test_first_free_path_pored_film_against_quadrature(oracle, lam, radius):
+    z = free_path_pin_z(oracle, dict(W.GRAY_UNIT, tau=lam, v=1.0), radius)
+    assert abs(z) < 4.0, z
+
+
+def test_first_free_path_silicon_pored_film_against_quadrature(oracle):
+    z = free_path_pin_z(oracle, W.SILICON_LIKE, 30e-9, m=15)
+    assert abs(z) < 4.0, z
