@@ -19,8 +19,8 @@
  *
  * Parity status of each function: see the pin list in the Python wrapper
  * (oracle/oracle.py).  The porous-film effective conductivity has no closed
- * form: parity unpinned beyond bounds, symmetry and the exact per-particle
- * invariants.
+ * form: parity unpinned beyond bounds, symmetry, the exact per-particle
+ * invariants and its first-event and first-free-path truncations.
  */
 #include <math.h>
 #include <pthread.h>

@@ -20,12 +20,19 @@ tests, none of which re-derives the oracle's own formulas):
   (the analytic thin-film solution) and the bulk sum (1/3) sum C v^2 tau;
   vanishing mean contribution after the first event.
 * Porous film: ray-cylinder intersections against brute-force marching,
-  bounds and mirror symmetry; transient energy conservation (exact).
+  bounds and mirror symmetry; transient energy conservation (exact); its
+  first-event and first-free-path conductivities against quasi-Monte Carlo
+  means of each particle's closed-form first-flight contribution.  The
+  full (untruncated) porous-film conductivity has no closed form: parity
+  unpinned beyond those checks.
 * Steady maps over the unit cell: solid fractions against the exact total
   and point counts; the flux map partitions the scalar flux; the unit
   cell's mirror symmetries; flat maps for a film without pores.
-  The porous-film conductivity itself has no closed form: parity unpinned
-  beyond those checks.
+* Transient estimator: free streaming between specular faces (slab
+  fractions from the unfolded kinematics); pulse emission times (truncated
+  Gaussian law) and lateral law (Rayleigh radius, cosine directions).
+* Film depth profile of the in-plane flux: the depth form of the thin-film
+  solution.
 """
 from __future__ import annotations
 
