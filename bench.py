@@ -66,7 +66,7 @@ def _sha_kernel_sources():
     comments and whitespace removed, so that only edits which can change the
     compiled code invalidate a capture."""
     h = hashlib.sha256()
-    for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h", "trace_f32.cu"):
+    for f in ("trace_kernel.cuh", "device_math.cuh", "le_mc_internal.h", "trace_launch.cu"):
         with open(os.path.join(ROOT, "paper_1206_3316_gb300", "csrc", f)) as fh:
             txt = fh.read()
         txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)

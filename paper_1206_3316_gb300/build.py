@@ -24,7 +24,13 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # FP64 arithmetic is unaffected by these flags.
 CUFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden", "-I" + INC,
                   "-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
-SOURCES = ["trace_f32.cu", "trace_f64.cu", "le_mc_api.cu", "le_mc_batch.cu", "le_mc_server.cu", "le_mc_noalloc.cu", "le_mc_diag.cu", "le_mc_host.cpp"]
+# (source, object name, extra flags): the trace kernels' source is compiled
+# once per trajectory precision
+SOURCES = [("trace_launch.cu", "trace_f32", ["-DLEMC_PREC_BITS=32"]),
+           ("trace_launch.cu", "trace_f64", ["-DLEMC_PREC_BITS=64"]),
+           ("le_mc_api.cu", "le_mc_api", []), ("le_mc_batch.cu", "le_mc_batch", []),
+           ("le_mc_server.cu", "le_mc_server", []), ("le_mc_noalloc.cu", "le_mc_noalloc", []),
+           ("le_mc_diag.cu", "le_mc_diag", []), ("le_mc_host.cpp", "le_mc_host", [])]
 
 
 def nvcc():
@@ -51,9 +57,10 @@ def build(force: bool = False, verbose: bool = False, debug: bool = False) -> st
     os.makedirs(obj_dir, exist_ok=True)
     exe = nvcc()
 
-    def compile_one(src):
-        obj = os.path.join(obj_dir, os.path.splitext(src)[0] + ".o")
-        cmd = [exe] + flags + ["-c", os.path.join(SRC, src), "-o", obj]
+    def compile_one(item):
+        src, name, extra = item
+        obj = os.path.join(obj_dir, name + ".o")
+        cmd = [exe] + flags + extra + ["-c", os.path.join(SRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd += ["-Xptxas", "-v"]
         res = subprocess.run(cmd, capture_output=True, text=True)

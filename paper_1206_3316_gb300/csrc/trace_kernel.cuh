@@ -1223,14 +1223,17 @@ __global__ void __launch_bounds__(256) classify_kernel(const __grid_constant__ K
     const int lane = threadIdx.x & 31;
     const unsigned lanemask_lt = (1u << lane) - 1u;
     const bool batch = P.instances != nullptr;
-    const uint32_t N = batch ? (uint32_t)P.offsets[P.n_instances] : P.n_particles;
-    const uint32_t stride = gridDim.x * blockDim.x;
+    // N may reach 2^32 - 1: the loop index and the bound test are 64-bit, so
+    // neither w0 + stride nor w0 + lane can wrap around below N
+    const unsigned long long N = batch ? P.offsets[P.n_instances] : (unsigned long long)P.n_particles;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
     // whole warps iterate together so the ballots below see full masks
-    const uint32_t first = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u;
-    for (uint32_t w0 = first; w0 < N; w0 += stride) {
-        const uint32_t pid = w0 + (uint32_t)lane;
+    const unsigned long long first = (unsigned long long)((blockIdx.x * blockDim.x + threadIdx.x) & ~31u);
+    for (unsigned long long w0 = first; w0 < N; w0 += stride) {
+        const unsigned long long pid64 = w0 + (unsigned long long)lane;
+        const uint32_t pid = (uint32_t)pid64;
         bool is_long = false, is_ext = false;
-        if (pid < N) {
+        if (pid64 < N) {
             uint32_t id = batch ? pid : P.first + pid, inst = P.inst;
             R cut = consts_of<R>(P).lam_cut;
             if (batch) {

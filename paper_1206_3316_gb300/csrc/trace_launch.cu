@@ -1,8 +1,22 @@
-// Instantiations and launchers of the float trace kernels (one translation
-// unit per trajectory precision so the two compile in parallel).
+// Instantiations and launchers of the trace kernels in one trajectory
+// precision.  The build compiles this file twice, with LEMC_PREC_BITS=32
+// (float kernels, launchers named *_f32) and LEMC_PREC_BITS=64 (double
+// kernels, *_f64), so the two precisions compile in parallel from one source.
 #include <cuda_runtime.h>
 
 #include "trace_kernel.cuh"
+
+#if !defined(LEMC_PREC_BITS)
+#error "compile with -DLEMC_PREC_BITS=32 or -DLEMC_PREC_BITS=64"
+#elif LEMC_PREC_BITS == 32
+using Real = float;
+#define LEMC_NAME(fn) fn##_f32
+#elif LEMC_PREC_BITS == 64
+using Real = double;
+#define LEMC_NAME(fn) fn##_f64
+#else
+#error "LEMC_PREC_BITS must be 32 or 64"
+#endif
 
 namespace lemc {
 
@@ -10,7 +24,7 @@ namespace {
 template <int G, int S, bool PR, bool DF = false>
 cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem, cudaStream_t st)
 {
-    auto k = trace_entry<float, G, S, PR, false, DF>();
+    auto k = trace_entry<Real, G, S, PR, false, DF>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     if (blocks <= 0) return cudaSuccess;
@@ -21,7 +35,7 @@ cudaError_t launch_one(const KernelArgs& a, int blocks, int threads, size_t smem
 template <int G, int S, bool PR, bool DF = false>
 cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
 {
-    auto k = trace_entry<float, G, S, PR, false, DF>();
+    auto k = trace_entry<Real, G, S, PR, false, DF>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
@@ -30,7 +44,7 @@ cudaError_t occupancy_one(int threads, size_t smem, int* per_sm)
 template <int G, int S, bool PR>
 cudaError_t smem_one(int n_modes, int threads, int prof_len, int hj_len, size_t* bytes)
 {
-    *bytes = trace_smem_bytes<float, G, S, PR>(n_modes, threads, prof_len, hj_len);
+    *bytes = trace_smem_bytes<Real, G, S, PR>(n_modes, threads, prof_len, hj_len);
     return cudaSuccess;
 }
 }  // namespace
@@ -67,7 +81,7 @@ static bool all_diffuse(const TraceParams& p)
            (p.geom != LE_MC_GEOM_POROUS || p.pore_wall == LE_MC_WALL_DIFFUSE) && p.aniso == 0 && p.n_hj == 0;
 }
 
-cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
+cudaError_t LEMC_NAME(launch_trace)(const KernelArgs& a, int geom, int src, bool profile, int blocks, int threads,
                               size_t smem, cudaStream_t st)
 {
     if (all_diffuse(a.p) && !profile) {
@@ -78,64 +92,64 @@ cudaError_t launch_trace_f32(const KernelArgs& a, int geom, int src, bool profil
     LEMC_DISPATCH(launch_one, a, blocks, threads, smem, st)
 }
 
-cudaError_t occupancy_trace_f32(int geom, int src, bool profile, int threads, size_t smem, int* per_sm)
+cudaError_t LEMC_NAME(occupancy_trace)(int geom, int src, bool profile, int threads, size_t smem, int* per_sm)
 {
     LEMC_DISPATCH(occupancy_one, threads, smem, per_sm)
 }
 
 // Occupancy of the kernel that launch_trace picks for these parameters.
-cudaError_t occupancy_trace_for_f32(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm)
+cudaError_t LEMC_NAME(occupancy_trace_for)(const TraceParams& p, bool profile, int threads, size_t smem, int* per_sm)
 {
     if (all_diffuse(p) && !profile) {
         if (p.geom == LE_MC_GEOM_PLANES)
             return occupancy_one<LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(threads, smem, per_sm);
         return occupancy_one<LE_MC_GEOM_POROUS, LE_MC_SRC_GRADIENT, false, true>(threads, smem, per_sm);
     }
-    return occupancy_trace_f32(p.geom, p.src, profile, threads, smem, per_sm);
+    return LEMC_NAME(occupancy_trace)(p.geom, p.src, profile, threads, smem, per_sm);
 }
 
-cudaError_t smem_trace_f32(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
+cudaError_t LEMC_NAME(smem_trace)(int geom, int src, bool profile, int n_modes, int threads, int prof_len, int hj_len,
                             size_t* bytes)
 {
     LEMC_DISPATCH(smem_one, n_modes, threads, prof_len, hj_len, bytes)
 }
 
 // Batch mode: PLANES geometry with the WALLS or GRADIENT source.
-cudaError_t batch_attr_f32(int src, bool diff, int threads, size_t smem, int* per_sm)
+cudaError_t LEMC_NAME(batch_attr)(int src, bool diff, int threads, size_t smem, int* per_sm)
 {
-    auto k = src == LE_MC_SRC_WALLS ? trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>
-             : diff                 ? trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>
-                                    : trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>;
+    auto k = src == LE_MC_SRC_WALLS ? trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>
+             : diff                 ? trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>
+                                    : trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
 }
 
 // Launch only (no attribute calls), so it can be captured into a graph.
-cudaError_t batch_launch_f32(const KernelArgs& a, int src, bool diff, int blocks, int threads, size_t smem,
+cudaError_t LEMC_NAME(batch_launch)(const KernelArgs& a, int src, bool diff, int blocks, int threads, size_t smem,
                               cudaStream_t st)
 {
     if (blocks <= 0) return cudaSuccess;
     if (src == LE_MC_SRC_WALLS)
-        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true><<<blocks, threads, smem, st>>>(a);
+        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true><<<blocks, threads, smem, st>>>(a);
     else if (diff)
-        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true><<<blocks, threads, smem, st>>>(a);
+        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true><<<blocks, threads, smem, st>>>(a);
     else
-        trace_kernel<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true><<<blocks, threads, smem, st>>>(a);
+        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true><<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
-size_t batch_smem_f32(int src, int n_modes, int threads, int n_instances)
+size_t LEMC_NAME(batch_smem)(int src, int n_modes, int threads, int n_instances)
 {
     return src == LE_MC_SRC_WALLS
-               ? trace_smem_bytes<float, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>(n_modes, threads, 0, 0, n_instances)
-               : trace_smem_bytes<float, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(n_modes, threads, 0, 0,
+               ? trace_smem_bytes<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>(n_modes, threads, 0, 0, n_instances)
+               : trace_smem_bytes<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>(n_modes, threads, 0, 0,
                                                                                             n_instances);
 }
 
-cudaError_t launch_classify_f32(const KernelArgs& a, int blocks, cudaStream_t st)
+cudaError_t LEMC_NAME(launch_classify)(const KernelArgs& a, int blocks, cudaStream_t st)
 {
-    classify_kernel<float><<<blocks, 256, 0, st>>>(a);
+    classify_kernel<Real><<<blocks, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
