@@ -191,6 +191,9 @@ struct MaterialView {
 };
 bool material_view(le_mc_material m, MaterialView* out);
 void material_retain(le_mc_material m);
+// Marks a material whose tables le_mc_run_noalloc work has read (its release
+// then waits for the device before freeing them).
+void material_mark_noalloc(le_mc_material m);
 void material_drop(le_mc_material m);
 le_mc_status set_error(le_mc_status s, const char* what, const char* detail);
 
@@ -218,6 +221,10 @@ void finalize_map(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const M
                   double* T, double* T_se, double* q, double* q_se, double* solid);
 // Solid fraction of each of the ny x nz map cells of a unit cell ([nz][ny]).
 void map_solid_fractions(double pitch, double radius, int ny, int nz, double* frac);
+// Truncation study of the flux split by scattering index (le_mc_truncation_study).
+int truncation_study(const double* H, const double* se, int n, double resolved, int first, le_mc_truncation* out,
+                     const char** why);
+double truncation_tail(const le_mc_truncation* t, int K);
 double flux_scale(const le_mc_geometry_desc* g, const le_mc_run_desc* r, const MaterialSums& ms,
                   double* P_out, double* Vref_out, double* Vsolid_out);
 

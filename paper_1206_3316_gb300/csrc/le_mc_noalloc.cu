@@ -19,7 +19,16 @@
 // device, so that first call should be made before any stream capture.
 // All calls share the array: calls whose device work overlaps in time (on
 // different streams, or from different host threads) race on it and must
-// be serialised by the caller.
+// be serialised by the caller.  The cached address belongs to the device
+// context that existed at the first call; after cudaDeviceReset it is stale,
+// so the library must not be used across a reset.
+//
+// The kernels hold no reference on the material (taking one would allocate
+// nothing, but releasing it would need a completion callback or event that
+// this entry point may not create), so the material is marked instead and
+// le_mc_destroy_material waits for the whole device before freeing its
+// tables.  Device status bits of the last call stay in the array and are
+// read back with le_mc_noalloc_flags.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -113,6 +122,7 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
     e = scratch_address(dev, &scratch);
     if (e != cudaSuccess) return set_cuda_error(e, "le_mc_run_noalloc: cudaGetSymbolAddress");
     cudaStream_t st = (cudaStream_t)stream;
+    material_mark_noalloc(m);
     const bool fp32 = r.precision == LE_MC_PREC_FP32;
     const uint64_t N = r.n_particles;
     const bool long_first = G.kind != LE_MC_GEOM_BULK && r.schedule != 2 && N >= 4096;
@@ -169,6 +179,26 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
         e = fp32 ? launch_trace_f32(a, G.kind, r.source, false, blocks, threads, smem, st)
                  : launch_trace_f64(a, G.kind, r.source, false, blocks, threads, smem, st);
     if (e != cudaSuccess) return set_cuda_error(e, "le_mc_run_noalloc: launch");
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_noalloc_flags(void* stream, uint32_t* flags)
+{
+    if (!flags) return set_error(LE_MC_ERR_INVALID, "le_mc_noalloc_flags", "null argument");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_cuda_error(e, "le_mc_noalloc_flags");
+    unsigned char* scratch = nullptr;
+    e = scratch_address(dev, &scratch);
+    if (e != cudaSuccess) return set_cuda_error(e, "le_mc_noalloc_flags: cudaGetSymbolAddress");
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t word = 0;
+    // a pageable destination: the copy is complete when cudaMemcpyAsync
+    // returns; the stream synchronisation makes that explicit
+    e = cudaMemcpyAsync(&word, scratch + 8, sizeof(word), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_cuda_error(e, "le_mc_noalloc_flags: copy");
+    *flags = word;
     return LE_MC_OK;
 }
 
