@@ -371,6 +371,36 @@ typedef struct {
 
 LE_MC_API le_mc_status le_mc_destroy_run(le_mc_run_handle h);
 
+/* ---- choosing the scattering cap K_s from the flux split -------------------
+ * The paper truncates histories of non-absorbing domains after about 40
+ * relaxation events, chosen where the flux carried between the j-th and
+ * (j+1)-th relaxation, <H_j>, becomes of the order of its own statistical
+ * uncertainty; it notes that <H_j> decays exponentially, which keeps the
+ * error of the cap under control (termination discussion after Eq. 4, its
+ * Fig. 2 c-d).  This host-only study reads the H / H_se arrays of a run with
+ * n_hj > 0 (LE_MC_ARRAY_H, LE_MC_ARRAY_H_SE):
+ *   k_s    the first j with |<H_j>| <= its standard error (n if none);
+ *   ratio, amp, sign: the geometric law sign amp ratio^j fitted by weighted
+ *          least squares on log |<H_j>| (weights (H_j / se_j)^2) over the
+ *          contiguous run of indices from `first` on whose |<H_j>| exceeds
+ *          `resolved` standard errors (ratio = NaN if fewer than n_fit = 2);
+ * and le_mc_truncation_tail gives the flux a cap K drops, the extrapolated
+ * sum_{j >= K} <H_j> = sign amp ratio^K / (1 - ratio) (0 unless 0 < ratio
+ * < 1).  Errors: LE_MC_ERR_INVALID (null pointer, n out of 1..LE_MC_MAX_HJ,
+ * resolved <= 0, first < 0, a non-finite H or negative H_se). */
+typedef struct {
+    int32_t k_s;        /* first j with |H_j| <= H_se_j                     */
+    int32_t n_fit;      /* indices in the fitted run                        */
+    double ratio;       /* decay ratio of |H_j| per relaxation (NaN: no fit) */
+    double amp;         /* |H_j| ~ amp ratio^j                              */
+    double sign;        /* sign of the fitted terms' sum                    */
+} le_mc_truncation;
+LE_MC_API le_mc_status le_mc_truncation_study(const double* H, const double* H_se, int32_t n, double resolved,
+                                              int32_t first, le_mc_truncation* out);
+/* Extrapolated flux dropped by a cap at K relaxations (K >= 0) from a study;
+ * host-only.  Errors: LE_MC_ERR_INVALID (null pointer, K < 0). */
+LE_MC_API le_mc_status le_mc_truncation_tail(const le_mc_truncation* study, int32_t K, double* dropped);
+
 /* ---- batches: many instances of one problem family in one launch ---------
  * Not in the paper: the instances are independent simulations of the method
  * (same steps I-VI), packed into one persistent launch so that small
@@ -494,15 +524,31 @@ LE_MC_API le_mc_status le_mc_server_destroy(le_mc_server s);
  * limited to LE_MC_NOALLOC_MAX_PARTICLES per call (larger problems are
  * traced in pieces with first_particle and the caller adds the pieces).
  * The array's device address is looked up during the first call on each
- * device, so make that first call before any stream capture.  Every call
- * shares the array: calls whose device work overlaps in time race on it, so
- * the caller must serialise them.  Steady WALLS / GRADIENT runs only (no
- * profiles, maps, H_j, grid or records).  Asynchronous on `stream`.
+ * device, so make that first call before any stream capture; the address is
+ * kept for the life of the process, so do not use the library across a
+ * cudaDeviceReset.  Every call shares the array: calls whose device work
+ * overlaps in time race on it, so the caller must serialise them.  Steady
+ * WALLS / GRADIENT runs only (no profiles, maps, H_j, grid or records).
+ * Asynchronous on `stream`.
+ * Lifetime: the call takes no reference on the material, so the material
+ * must outlive the call's device work; le_mc_destroy_material on a material
+ * this entry point has used waits for the whole device before it frees the
+ * tables, which makes an early destroy safe but costs a device-wide
+ * synchronisation.
+ * Device status bits (LE_MC_FLAG_*, e.g. REJECTION_EXHAUSTED from a pored
+ * film's position draws) are not part of d_sums / d_counters; they stay in
+ * the library's array until the next call and are read with
+ * le_mc_noalloc_flags.
  * Errors: LE_MC_ERR_INVALID (null pointer, bad descriptor, n_particles above
  * the limit, arrays requested), LE_MC_ERR_CUDA. */
 #define LE_MC_NOALLOC_MAX_PARTICLES (1u << 22)
 LE_MC_API le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_run_desc* desc,
                                          double* d_sums, unsigned long long* d_counters, void* stream);
+/* Device status bits (LE_MC_FLAG_*) of the last le_mc_run_noalloc call on the
+ * current device, copied into *flags once `stream` (the stream of that call)
+ * has finished its work.  Synchronous; allocates nothing.
+ * Errors: LE_MC_ERR_INVALID (null flags), LE_MC_ERR_CUDA. */
+LE_MC_API le_mc_status le_mc_noalloc_flags(void* stream, uint32_t* flags);
 
 /* ---- diagnostics ---------------------------------------------------------- */
 /* Philox4x32-10 of n counters (4 words each) under one key, computed by a GPU

@@ -16,7 +16,7 @@ from ._binding import (  # noqa: F401
     le_mc_material_table, le_mc_philox, le_mc_read_array, le_mc_read_tallies, le_mc_run, le_mc_sample_modes,
     le_mc_wait, lib, material_desc, run_desc, LIB_PATH, le_mc_server_cancel, le_mc_server_create,
     le_mc_server_destroy, le_mc_server_poll, le_mc_server_stats, le_mc_server_submit, le_mc_server_wait_all,
-    le_mc_run_noalloc, NOALLOC_MAX_PARTICLES, le_mc_map_solid, le_mc_test_fail_allocation, DEVICE_FLAGS,
+    le_mc_run_noalloc, le_mc_noalloc_flags, le_mc_truncation_study, le_mc_truncation_tail, NOALLOC_MAX_PARTICLES, le_mc_map_solid, le_mc_test_fail_allocation, DEVICE_FLAGS,
 )
 
 
@@ -156,45 +156,15 @@ def truncation_study(H, H_se, resolved=3.0, first=2):
     (the ``H`` / ``H_se`` arrays of a run with ``n_hj`` > 0), as the paper does
     empirically after its Fig. 2: <H_j> is the flux carried between the j-th
     and (j+1)-th relaxation of a history (j = 0: emission to the first).
+    The arithmetic is the library's (le_mc_truncation_study); this wrapper
+    returns a dict with
+      k_s      the first j at which |<H_j>| falls to its own standard error;
+      ratio    the geometric decay ratio of |<H_j>| fitted over the resolved,
+               contiguous run of indices from ``first`` on (None if no fit);
+      tail(K)  the flux the cap K drops, extrapolated from that fit."""
+    import math
 
-    Returns a dict with
-      k_s      the first j at which |<H_j>| falls to its own standard error
-               (collecting later terms adds noise, not information);
-      ratio    the geometric decay ratio of |<H_j>| fitted, by weighted least
-               squares on log |<H_j>|, over the contiguous run of indices from
-               ``first`` on that are resolved to ``resolved`` standard errors
-               (None if fewer than two are);
-      tail(K)  a function: the flux the cap K drops, sum_{j >= K} <H_j>,
-               extrapolated from that fit (0 when the split is not decaying).
-    Host-side arithmetic on the tallies; the tracing itself is unchanged."""
-    import numpy as np
-
-    H = np.asarray(H, dtype=np.float64)
-    se = np.asarray(H_se, dtype=np.float64)
-    n = H.size
-    below = np.nonzero(np.abs(H) <= se)[0]
-    k_s = int(below[0]) if below.size else n
-    # the decaying range: the contiguous run of resolved terms from `first` on
-    # (isolated noise excursions further out must not enter the fit)
-    idx = np.arange(n)
-    ok = np.zeros(n, dtype=bool)
-    for j in range(first, n):
-        if not (se[j] > 0 and np.abs(H[j]) > resolved * se[j]):
-            break
-        ok[j] = True
-    ratio, amp, sgn = None, 0.0, 0.0
-    if ok.sum() >= 2:
-        j, y = idx[ok], np.log(np.abs(H[ok]))
-        w = (np.abs(H[ok]) / se[ok]) ** 2  # 1 / var(log|H|)
-        A = np.vstack([np.ones_like(j, dtype=np.float64), j]).T
-        coef = np.linalg.lstsq(A * np.sqrt(w)[:, None], y * np.sqrt(w), rcond=None)[0]
-        ratio = float(np.exp(coef[1]))
-        amp = float(np.exp(coef[0]))
-        sgn = float(np.sign(np.sum(H[ok])))
-
-    def tail(K):
-        if ratio is None or not (0.0 < ratio < 1.0):
-            return 0.0
-        return sgn * amp * ratio ** K / (1.0 - ratio)
-
-    return {"k_s": k_s, "ratio": ratio, "tail": tail}
+    t = le_mc_truncation_study(H, H_se, resolved, first)
+    ratio = None if math.isnan(t.ratio) else float(t.ratio)
+    return {"k_s": int(t.k_s), "ratio": ratio, "n_fit": int(t.n_fit),
+            "tail": lambda K: le_mc_truncation_tail(t, K)}

@@ -122,6 +122,11 @@ _STATUS = C.c_int
 _H = C.c_void_p
 
 # name -> (restype, argtypes)
+class Truncation(C.Structure):
+    _fields_ = [("k_s", C.c_int32), ("n_fit", C.c_int32), ("ratio", C.c_double), ("amp", C.c_double),
+                ("sign", C.c_double)]
+
+
 SIGNATURES = {
     "le_mc_create_material": (_STATUS, [C.POINTER(MaterialDesc), C.POINTER(_H)]),
     "le_mc_destroy_material": (_STATUS, [_H]),
@@ -156,6 +161,10 @@ SIGNATURES = {
     "le_mc_server_stats": (_STATUS, [_H, C.POINTER(ServerCounters)]),
     "le_mc_server_destroy": (_STATUS, [_H]),
     "le_mc_run_noalloc": (_STATUS, [_H, _H, C.POINTER(RunDesc), C.c_void_p, C.c_void_p, C.c_void_p]),
+    "le_mc_noalloc_flags": (_STATUS, [C.c_void_p, C.POINTER(C.c_uint32)]),
+    "le_mc_truncation_study": (_STATUS, [C.c_void_p, C.c_void_p, C.c_int32, C.c_double, C.c_int32,
+                                         C.POINTER(Truncation)]),
+    "le_mc_truncation_tail": (_STATUS, [C.POINTER(Truncation), C.c_int32, C.POINTER(C.c_double)]),
     "le_mc_struct_size": (C.c_int32, [C.c_int32]),
     "le_mc_last_error": (C.c_char_p, []),
     "le_mc_abi_version": (C.c_int32, []),
@@ -492,3 +501,31 @@ def le_mc_run_noalloc(mat, geo, desc, d_sums, d_counters, stream=None):
     are device addresses owned by the caller (ints, e.g. tensor.data_ptr())."""
     _check(lib.le_mc_run_noalloc(mat, geo, C.byref(desc), int(d_sums), int(d_counters), _stream_ptr(stream)),
            "le_mc_run_noalloc")
+
+
+def le_mc_noalloc_flags(stream=None):
+    """Device status bits (LE_MC_FLAG_*) of the last le_mc_run_noalloc call on
+    the current device, after `stream` has finished."""
+    f = C.c_uint32(0)
+    _check(lib.le_mc_noalloc_flags(_stream_ptr(stream), C.byref(f)), "le_mc_noalloc_flags")
+    return int(f.value)
+
+
+def le_mc_truncation_study(H, H_se, resolved=3.0, first=2):
+    """Host-only study of the flux split by scattering index (see
+    include/le_mc.h): returns the le_mc_truncation fields as a dict."""
+    import numpy as np
+    H = np.ascontiguousarray(H, dtype=np.float64)
+    se = np.ascontiguousarray(H_se, dtype=np.float64)
+    if H.shape != se.shape or H.ndim != 1:
+        raise ValueError("H and H_se must be 1-D arrays of one length")
+    t = Truncation()
+    _check(lib.le_mc_truncation_study(H.ctypes.data, se.ctypes.data, int(H.size), float(resolved), int(first),
+                                      C.byref(t)), "le_mc_truncation_study")
+    return t
+
+
+def le_mc_truncation_tail(study, K):
+    d = C.c_double(0.0)
+    _check(lib.le_mc_truncation_tail(C.byref(study), int(K), C.byref(d)), "le_mc_truncation_tail")
+    return float(d.value)

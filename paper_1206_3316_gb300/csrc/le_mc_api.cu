@@ -81,6 +81,9 @@ struct le_mc_material_s {
     uint2* d_alias_scat = nullptr;
     uint2* d_alias_emit = nullptr;
     uint2* d_alias_init = nullptr;
+    // set once le_mc_run_noalloc has launched work reading these tables: such
+    // work holds no reference, so releasing the tables waits for the device
+    std::atomic<bool> noalloc_used{false};
 };
 
 struct le_mc_geometry_s {
@@ -119,9 +122,14 @@ void material_release(le_mc_material m)
     // Every run and batch that used the tables has finished (they hold a
     // reference until destroyed, and destroying them waits for their device
     // work), so the stream-ordered frees need no device-wide synchronisation.
+    // le_mc_run_noalloc holds no reference (it may not allocate one), and its
+    // kernels may still be reading the tables on a stream the legacy stream
+    // does not order against, so a material it has used waits for the whole
+    // device first.
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(m->device);
+    if (m->noalloc_used.load()) cudaDeviceSynchronize();
     if (m->d_props32) cudaFreeAsync(m->d_props32, 0);
     if (m->d_props64) cudaFreeAsync(m->d_props64, 0);
     if (m->d_alias_scat) cudaFreeAsync(m->d_alias_scat, 0);
@@ -165,6 +173,11 @@ bool geometry_view(le_mc_geometry g, le_mc_geometry_desc* out)
     if (!g) return false;
     *out = g->desc;
     return true;
+}
+
+void material_mark_noalloc(le_mc_material m)
+{
+    if (m) m->noalloc_used.store(true);
 }
 
 void material_retain(le_mc_material m)
@@ -249,6 +262,23 @@ le_mc_status le_mc_map_solid(const le_mc_geometry_desc* g, int32_t map_ny, int32
     if (map_ny < 1 || map_nz < 1 || map_ny > LE_MC_MAX_MAP || map_nz > LE_MC_MAX_MAP)
         return fail(LE_MC_ERR_INVALID, "le_mc_map_solid: map_ny, map_nz out of 1..LE_MC_MAX_MAP");
     map_solid_fractions(g->pitch, g->radius, map_ny, map_nz, fraction);
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_truncation_study(const double* H, const double* H_se, int32_t n, double resolved, int32_t first,
+                                    le_mc_truncation* out)
+{
+    const char* why = "";
+    if (truncation_study(H, H_se, n, resolved, first, out, &why) != LE_MC_OK)
+        return fail(LE_MC_ERR_INVALID, "le_mc_truncation_study", why);
+    return LE_MC_OK;
+}
+
+le_mc_status le_mc_truncation_tail(const le_mc_truncation* study, int32_t K, double* dropped)
+{
+    if (!study || !dropped) return fail(LE_MC_ERR_INVALID, "le_mc_truncation_tail: null pointer");
+    if (K < 0) return fail(LE_MC_ERR_INVALID, "le_mc_truncation_tail: K must be >= 0");
+    *dropped = truncation_tail(study, K);
     return LE_MC_OK;
 }
 

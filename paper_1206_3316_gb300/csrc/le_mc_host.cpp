@@ -631,4 +631,64 @@ void finalize_hj(const le_mc_run_desc* r, double scale, const double* raw, doubl
     }
 }
 
+// ---- choosing the scattering cap from the flux split (<H_j> discussion) ----
+// The paper stops collecting contributions once <H_j> (the flux carried
+// between the j-th and (j+1)-th relaxation) is of the order of its own
+// statistical uncertainty, and notes that the exponential decay of <H_j>
+// keeps the error of such a cap under control.  Reading: K_s is the first j
+// with |<H_j>| <= its standard error; the decay is fitted as a geometric law
+// |<H_j>| = amp ratio^j by weighted least squares on log |<H_j>| (weights
+// 1 / var(log |H_j|) = (H_j / se_j)^2) over the contiguous run of indices
+// from `first` on that are resolved to `resolved` standard errors; the flux a
+// cap K drops is then the geometric tail sum_{j >= K} = sign amp ratio^K /
+// (1 - ratio).
+int truncation_study(const double* H, const double* se, int n, double resolved, int first, le_mc_truncation* out,
+                     const char** why)
+{
+    if (!H || !se || !out) { *why = "null pointer"; return LE_MC_ERR_INVALID; }
+    if (n < 1 || n > LE_MC_MAX_HJ) { *why = "n out of 1..LE_MC_MAX_HJ"; return LE_MC_ERR_INVALID; }
+    if (!(resolved > 0.0)) { *why = "resolved must be > 0"; return LE_MC_ERR_INVALID; }
+    if (first < 0) { *why = "first must be >= 0"; return LE_MC_ERR_INVALID; }
+    for (int j = 0; j < n; ++j)
+        if (!isfinite(H[j]) || !(se[j] >= 0.0)) { *why = "H must be finite and H_se >= 0"; return LE_MC_ERR_INVALID; }
+    memset(out, 0, sizeof(*out));
+    out->k_s = n;
+    for (int j = 0; j < n; ++j)
+        if (fabs(H[j]) <= se[j]) { out->k_s = j; break; }
+    // weighted least squares of y = c0 + c1 j over the resolved run
+    double S = 0, Sx = 0, Sy = 0, Sxx = 0, Sxy = 0, Hsum = 0;
+    int m = 0;
+    for (int j = first; j < n; ++j) {
+        if (!(se[j] > 0.0 && fabs(H[j]) > resolved * se[j])) break;
+        const double w = (H[j] / se[j]) * (H[j] / se[j]);
+        const double y = log(fabs(H[j]));
+        S += w;
+        Sx += w * j;
+        Sy += w * y;
+        Sxx += w * (double)j * j;
+        Sxy += w * j * y;
+        Hsum += H[j];
+        ++m;
+    }
+    out->n_fit = m;
+    out->ratio = std::numeric_limits<double>::quiet_NaN();
+    if (m >= 2) {
+        const double det = S * Sxx - Sx * Sx;
+        if (det > 0.0) {
+            const double c1 = (S * Sxy - Sx * Sy) / det;
+            const double c0 = (Sy - c1 * Sx) / S;
+            out->ratio = exp(c1);
+            out->amp = exp(c0);
+            out->sign = Hsum > 0.0 ? 1.0 : (Hsum < 0.0 ? -1.0 : 0.0);
+        }
+    }
+    return LE_MC_OK;
+}
+
+double truncation_tail(const le_mc_truncation* t, int K)
+{
+    if (!(t->ratio > 0.0 && t->ratio < 1.0)) return 0.0;
+    return t->sign * t->amp * pow(t->ratio, (double)K) / (1.0 - t->ratio);
+}
+
 }  // namespace lemc

@@ -496,11 +496,10 @@ def test_scattering_cap_drops_exactly_the_later_flux_split(P):
     # The same histories cut at K relaxations lose exactly the flux carried
     # after the K-th one: kappa(64) - kappa(K) = -(sum_{j >= K} <H_j>) / (dT/dz),
     # up to summation order; the truncation study predicts that loss.
-    from tests.test_oracle_transport import _truncation_study
     full = P.simulate(W.porous_film(n_particles=20_000_000, max_scatter=64, n_hj=64))
     H, se = full["H"], full["H_se"]
     dTdz = -1.0 / 100e-9
-    st = _truncation_study()(H, se)
+    st = P.truncation_study(H, se)
     for K in (2, 4, 8):
         cut = P.simulate(W.porous_film(n_particles=20_000_000, max_scatter=K), arrays=False)
         lost = full["kappa"] - cut["kappa"]

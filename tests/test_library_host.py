@@ -152,3 +152,36 @@ def test_map_solid_fractions_match_oracle(P, oracle):
             P.le_mc_map_solid(g, ny, nz)
     with pytest.raises(P.LeMcError):
         P.le_mc_map_solid(P.geometry_desc({"kind": "planes", "L": 1e-7}), 4, 4)
+
+
+def test_truncation_study_exact_and_against_independent_fit(P):
+    # An exactly geometric split is recovered exactly: ratio, amplitude, the
+    # tail sum_{j >= K} H_j in closed form, and K_s where the terms fall to
+    # their standard errors.
+    j = np.arange(40)
+    H = -3.0 * 0.5 ** j
+    se = np.full(40, 3.0 * 0.5 ** 12)
+    st = P.truncation_study(H, se, resolved=3.0, first=2)
+    assert st["k_s"] == 12  # |H_12| == se
+    assert st["ratio"] == pytest.approx(0.5, rel=1e-12)
+    for K in (2, 5, 9):
+        assert st["tail"](K) == pytest.approx(-3.0 * 0.5 ** K / (1 - 0.5), rel=1e-12)
+    # noisy split: the fit equals numpy's weighted least squares on the same run
+    rng = np.random.Generator(np.random.PCG64(7))
+    H = 2.0 * 0.7 ** j * (1 + 0.05 * rng.standard_normal(40))
+    se = 0.02 * np.ones(40)
+    st = P.truncation_study(H, se, resolved=3.0, first=2)
+    run = [k for k in range(2, 40)]
+    stop = next(k for k in run if not abs(H[k]) > 3.0 * se[k])
+    idx = np.arange(2, stop)
+    w = (H[idx] / se[idx]) ** 2
+    A = np.vstack([np.ones(idx.size), idx]).T * np.sqrt(w)[:, None]
+    c = np.linalg.lstsq(A, np.log(np.abs(H[idx])) * np.sqrt(w), rcond=None)[0]
+    assert st["n_fit"] == idx.size
+    assert st["ratio"] == pytest.approx(np.exp(c[1]), rel=1e-10)
+    assert st["tail"](6) == pytest.approx(np.exp(c[0]) * np.exp(c[1]) ** 6 / (1 - np.exp(c[1])), rel=1e-9)
+    # nothing resolved beyond `first`: no fit, no extrapolated tail
+    st = P.truncation_study([1.0, 0.5, 0.01, 0.0], [0.1, 0.1, 0.1, 0.1])
+    assert st["ratio"] is None and st["tail"](2) == 0.0 and st["k_s"] == 2
+    with pytest.raises(P.LeMcError):
+        P.truncation_study([1.0, np.nan], [0.1, 0.1])

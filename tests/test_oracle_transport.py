@@ -273,22 +273,13 @@ def test_two_slab_solvers_agree(analytic):
     assert abs(analytic.slab_solution(50.0, M=400)["psi"] / (4.0 / (3 * 50.0 + 4.0)) - 1) < 0.01
 
 
-def _truncation_study():
-    # the package's host-side helper, loaded without the CUDA library
-    import os
-    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
-                            "paper_1206_3316_gb300", "__init__.py")).read()
-    ns = {}
-    exec(src[src.index("def truncation_study"):], ns)
-    return ns["truncation_study"]
-
-
-def test_truncation_study_predicts_dropped_flux(oracle):
+def test_truncation_study_predicts_dropped_flux(oracle, built_library):
     # Pored film, flux split by scattering index up to 64 relaxations: the
     # geometric extrapolation of the resolved, decaying <H_j> predicts the flux
     # a cap K drops (measured directly as the sum of the later <H_j>) within
     # the statistical error of that sum; the paper's noise criterion gives K_s.
-    study = _truncation_study()
+    # (The study is the library's host-only arithmetic, fed the oracle's split.)
+    study = built_library.truncation_study
     p = W.porous_film(n_particles=2_000_000, precision="fp64", max_scatter=64, n_hj=64)
     r = oracle.run(p)
     H, se = r["H"], r["H_se"]
