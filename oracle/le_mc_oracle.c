@@ -18,9 +18,12 @@
  * draw, and the frame in which directions are built.
  *
  * Parity status of each function: see the pin list in the Python wrapper
- * (oracle/oracle.py).  The porous-film effective conductivity has no closed
- * form: parity unpinned beyond bounds, symmetry, the exact per-particle
- * invariants and its first-event and first-free-path truncations.
+ * (oracle/oracle.py).  The full (untruncated) porous-film effective
+ * conductivity has no closed form: parity unpinned.  It is bounded by the
+ * zero-radius (film) limit, the upper bound kappa_film (1 - porosity),
+ * symmetry, the exact per-particle invariants, its first-event and
+ * first-free-path truncations (pinned by quadrature) and the pore wall's
+ * Lambertian law (pinned by the invariance of a uniform isotropic excess).
  */
 #include <math.h>
 #include <pthread.h>

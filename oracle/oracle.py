@@ -22,9 +22,16 @@ tests, none of which re-derives the oracle's own formulas):
 * Porous film: ray-cylinder intersections against brute-force marching,
   bounds and mirror symmetry; transient energy conservation (exact); its
   first-event and first-free-path conductivities against quasi-Monte Carlo
-  means of each particle's closed-form first-flight contribution.  The
-  full (untruncated) porous-film conductivity has no closed form: parity
-  unpinned beyond those checks.
+  means of each particle's closed-form first-flight contribution; the pore
+  wall's Lambertian re-emission by the invariance of a uniform isotropic
+  excess in a pored cell (counts stay in proportion to the solid volume and
+  whole; a law uniform in the cosine, or about the wrong normal, fails it).
+  The full (untruncated) porous-film conductivity has no closed form: parity
+  unpinned.  What bounds it: the zero-radius limit (the Fuchs-Sondheimer
+  film), the upper bound kappa_film (1 - porosity), the first-event and
+  first-free-path pins above (same emission law, signs and normalisation),
+  the pinned pore-wall law, and the flux split by scattering index, whose
+  tail the truncation study extrapolates.
 * Steady maps over the unit cell: solid fractions against the exact total
   and point counts; the flux map partitions the scalar flux; the unit
   cell's mirror symmetries; flat maps for a film without pores.

@@ -44,6 +44,21 @@ def _uniform_pin_ok(oracle, analytic, library):
     return min(uniform_equilibrium_pvalues(r["grid"], p["geometry"])) > 1e-4
 
 
+def _pore_uniform_pin_ok(oracle, analytic, library):
+    # A uniform isotropic excess in a pored cell stays uniform (counts in
+    # proportion to the solid volume) and whole (adiabatic walls) only if the
+    # pore wall re-emits with the cosine law about the normal pointing into
+    # the solid.  (Segment cap 4096: a law that sends particles into the pore
+    # pins them to the wall in zero-length segments, which the cap ends.)
+    p = W.porous_initial(n_particles=200_000, precision="fp64", radius=30e-9, max_events=4096)
+    r = oracle.run(p, library=library)
+    totals = r["grid"].reshape(r["grid"].shape[0], -1).sum(axis=1)
+    if not np.all(totals == 200_000):
+        return False
+    from tests.test_oracle_porous import uniform_equilibrium_pvalues
+    return min(uniform_equilibrium_pvalues(r["grid"], p["geometry"])) > 1e-4
+
+
 def _specular_pin_ok(oracle, analytic, library):
     r = oracle.run(W.silicon_film(n_particles=1_000_000, precision="fp64", specularity=0.25), library=library)
     return abs(r["kappa"] - analytic.kappa_film(W.SILICON_LIKE, 100e-9, 0.25)) < 4.0 * r["kappa_se"]
@@ -175,6 +190,15 @@ MUTATIONS = [
      "q[k] += sign * (len * oz);", _film_profile_pin_ok),
     ("first-free-path cap also counting crossings of periodic unit-cell faces",
      "n_scat + n_wall >= p->max_collisions", "n_scat + n_wall + n_per >= p->max_collisions", _free_path_pin_ok),
+    ("pore-wall re-emission uniform in the cosine (not Lambertian)",
+     "double mu = sqrt(u[2]);\n                        double st = sqrt(fmax(0.0, 1.0 - mu * mu));\n"
+     "                        double phi = ORC_TWO_PI * u[3];",
+     "double mu = u[2];\n                        double st = sqrt(fmax(0.0, 1.0 - mu * mu));\n"
+     "                        double phi = ORC_TWO_PI * u[3];", _pore_uniform_pin_ok),
+    ("pore-wall cosine law about the normal pointing into the pore",
+     "s.oy = mu * ny - st * sn * nz;\n                        s.oz = mu * nz + st * sn * ny;",
+     "s.oy = -mu * ny - st * sn * nz;\n                        s.oz = -mu * nz + st * sn * ny;",
+     _pore_uniform_pin_ok),
     ("gradient-source positions not restricted to the solid",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                if (!in_pore(p, yl, zl)) break;",
      "                s->cy = cy; s->cz = cz; s->y = yl; s->z = zl;\n                break;", _first_event_pin_ok),
