@@ -42,7 +42,7 @@ extern "C" {
 #define LE_MC_API
 #endif
 
-#define LE_MC_ABI_VERSION 3
+#define LE_MC_ABI_VERSION 4
 #define LE_MC_MAX_BRANCHES 4
 #define LE_MC_MAX_MODES 4096        /* mode tables live in shared memory       */
 #define LE_MC_MAX_BINS_X 256        /* slab profile bins                       */
@@ -298,6 +298,11 @@ typedef struct {
     double prepass_ms;      /* device time of the long-first classification pass  */
     uint32_t kernel_launches; /* kernels this run launched                        */
     uint32_t device_flags;  /* device-side status bits, LE_MC_FLAG_* (0 = none)  */
+    uint32_t long_listed;   /* particles served from the long-first list (their
+                             * emission mean free path above long_mfp_cut)    */
+    uint32_t extreme_traced; /* particles traced apart, one per warp whose idle
+                             * lanes precompute its random words (above 32 x
+                             * long_mfp_cut; 0 when more than the list holds) */
 } le_mc_tallies;
 
 /* Waits for the run, copies the tallies to the host and normalises them

@@ -81,7 +81,7 @@ class Tallies(C.Structure):
         (n, C.c_uint64) for n in ("particles", "segments", "scatters", "wall_hits", "periodic",
                                   "truncated", "absorbed")] + [
         ("kernel_ms", C.c_double), ("prepass_ms", C.c_double), ("kernel_launches", C.c_uint32),
-        ("device_flags", C.c_uint32)]
+        ("device_flags", C.c_uint32), ("long_listed", C.c_uint32), ("extreme_traced", C.c_uint32)]
 
 
 class Particle(C.Structure):

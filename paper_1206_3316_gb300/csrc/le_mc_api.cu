@@ -111,6 +111,7 @@ struct le_mc_run_s {
     unsigned long long counters[CNT_N] = {};
     unsigned int flags = 0;
     uint32_t launches = 0;
+    uint32_t long_listed = 0, extreme_traced = 0;
 };
 
 namespace {
@@ -569,6 +570,18 @@ static le_mc_status fetch_header(le_mc_run_handle h)
     memcpy(h->sums, tmp + h->off_sums, sizeof(h->sums));
     memcpy(h->counters, tmp + h->off_counters, sizeof(h->counters));
     memcpy(&h->flags, tmp + h->off_flags, sizeof(h->flags));
+    if (h->long_cap > 0 && h->launches > 0) {
+        unsigned int cnt[3] = {0, 0, 0};
+        e = cudaMemcpy(cnt, h->dev + h->off_long_count, sizeof(cnt), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            h->failed = true;
+            return cuda_fail(e, "le_mc_read_tallies: copy");
+        }
+        // the trace kernel's reading of the two lists (all-or-nothing extreme list)
+        const bool overflow = cnt[1] > h->ext_cap;
+        h->extreme_traced = overflow ? 0u : cnt[1];
+        h->long_listed = (cnt[0] < h->long_cap ? cnt[0] : h->long_cap) + (overflow ? h->ext_cap : 0u);
+    }
     h->have_header = true;
     return LE_MC_OK;
 }
@@ -589,6 +602,8 @@ le_mc_status le_mc_read_tallies(le_mc_run_handle h, le_mc_tallies* out)
     out->prepass_ms = pre;
     out->kernel_launches = h->launches;
     out->device_flags = h->flags;
+    out->long_listed = h->long_listed;
+    out->extreme_traced = h->extreme_traced;
     return LE_MC_OK;
 }
 
