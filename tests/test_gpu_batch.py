@@ -128,12 +128,19 @@ def test_batched_films_each_instance_against_its_pin(P, oracle, analytic):
     with P.Batch(probs) as b:
         b.launch()
         got = b.results()
+    from scipy import stats
     zs = []
     for p, g in zip(probs, got):
         pin = analytic.kappa_film(W.SILICON_LIKE, p["geometry"]["L"])
-        zs.append(abs(g["kappa"] - pin) / g["kappa_se"])
+        zs.append((g["kappa"] - pin) / g["kappa_se"])
         assert g["particles"] == p["run"]["n_particles"] and g["device_flags"] == 0
-    assert max(zs) < 4.5, max(zs)
+    zs = np.array(zs)
+    # the 256 instances are independent: sum z^2 is chi-square with 256
+    # degrees of freedom under the pins
+    p_all = stats.chi2.sf(np.sum(zs ** 2), zs.size)
+    print(f"\n256 batched films against Fuchs-Sondheimer: sum z^2 = {np.sum(zs ** 2):.1f}, p = {p_all:.3g}, "
+          f"max |z| = {np.abs(zs).max():.2f}")
+    assert p_all > 1e-3
     small = [i for i, p in enumerate(probs) if p["run"]["n_particles"] <= 100_000][:24]
     for i in small:
         o = oracle.run(W.with_run(probs[i], precision="fp64"))

@@ -175,20 +175,52 @@ def test_porous_fp32_vs_oracle(P, oracle):
     assert abs(g["periodic"] / o["periodic"] - 1) < 0.02
 
 
+def homogeneity_pvalues(g, o, n_g, n_o, min_expected=5.0):
+    """Eq. 3 transient grids of two independent runs (n_g and n_o particles,
+    all of one sign): for each sample time, the Pearson chi-square p-value of
+    'both runs put a particle in each cell with the same probability'.  The
+    categories are the cells plus 'not in the grid yet' (not yet emitted);
+    categories whose expected count is below min_expected in either run are
+    pooled into one."""
+    from scipy import stats
+    out = []
+    for k in range(g.shape[0]):
+        a = g[k].ravel().astype(np.float64)
+        b = o[k].ravel().astype(np.float64)
+        a = np.append(a, n_g - a.sum())
+        b = np.append(b, n_o - b.sum())
+        tot = a + b
+        ea, eb = tot * n_g / (n_g + n_o), tot * n_o / (n_g + n_o)
+        small = (ea < min_expected) | (eb < min_expected)
+        if small.any():
+            a = np.append(a[~small], a[small].sum())
+            b = np.append(b[~small], b[small].sum())
+            ea = np.append(ea[~small], ea[small].sum())
+            eb = np.append(eb[~small], eb[small].sum())
+        keep = (ea > 0) & (eb > 0)
+        chi2 = ((a - ea) ** 2 / ea + (b - eb) ** 2 / eb)[keep].sum()
+        out.append(stats.chi2.sf(chi2, max(int(keep.sum()) - 1, 1)))
+    return np.array(out)
+
+
 def test_pulse_fp32_energy_conservation_and_oracle(P, oracle):
-    prob = W.porous_pulse(n_particles=50_000, grid=(4, 12, 12), n_samples=40, sample_dt=25e-12, t_final=1e-9)
+    # surface pulse on a coarse grid whose 40 samples reach t_final: every
+    # emitted particle is counted once per sample, and cell by cell, sample
+    # by sample, the FP32 counts of 2e6 particles and the FP64 oracle's of
+    # 1e6 come from the same cell probabilities (chi-square per sample time,
+    # p = 1e-3 over all 40 together)
+    ns = 40
+    prob = W.porous_pulse(n_particles=2_000_000, grid=(4, 12, 12), n_samples=ns, sample_dt=25e-12, t_final=1e-9)
     g = P.simulate(prob, record_particles=True)
     t0 = g["particles_rec"]["t0"]
-    ts = (np.arange(40) + 0.5) * 25e-12
-    emitted = np.array([(t0 <= t).sum() for t in ts])
-    assert np.array_equal(g["grid"].reshape(40, -1).sum(axis=1), emitted)
-    o = oracle.run(W.with_run(prob, precision="fp64"))
-    # per-sample depth profile (sum over y, z): Poisson-level agreement
-    gd = g["grid"].sum(axis=(2, 3)).astype(np.float64)
-    od = o["grid"].sum(axis=(2, 3)).astype(np.float64)
-    m = (gd + od) > 50
-    z = np.abs(gd - od)[m] / np.sqrt(gd + od)[m]
-    assert np.mean(z ** 2) < 3.0
+    ts = (np.arange(ns) + 0.5) * 25e-12
+    emitted = np.searchsorted(np.sort(t0), ts, side="right")
+    assert np.array_equal(g["grid"].reshape(ns, -1).sum(axis=1), emitted)
+    n_o = 1_000_000
+    o = oracle.run(W.with_run(prob, precision="fp64", n_particles=n_o, seed=prob["run"]["seed"] + 1))
+    pv = homogeneity_pvalues(g["grid"], o["grid"], 2_000_000, n_o)
+    print(f"\npulse grid, FP32 GPU vs FP64 oracle: min p over {ns} samples {pv.min():.3g}")
+    assert pv.min() > 1e-3 / ns, pv
 
 
 # ------------------------------------------- full size, launch invariance
@@ -408,12 +440,17 @@ def test_samples_stop_at_the_last_sample_time(P, oracle):
 def test_first_event_pored_film_against_quadrature(P, analytic):
     # config-2 steady at full size with max_events = 1, FP32: against the
     # quasi-Monte Carlo first-event conductivity (numpy ray algebra)
-    pin, pin_se = analytic.kappa_first_event_porous(W.SILICON_LIKE, 300e-9, 100e-9, 30e-9, m=17)
+    # (2^19 scrambled Sobol points x 4 scrambles: the pin's own error is below
+    # 1e-4 of kappa, the GPU's at 1e8 particles about 1.1e-4, so 3 sigma of
+    # the difference stays below 1e-3)
+    pin, pin_se = analytic.kappa_first_event_porous(W.SILICON_LIKE, 300e-9, 100e-9, 30e-9, m=19)
     g = P.simulate(W.with_run(W.porous_film(n_particles=100_000_000), max_events=1), arrays=False)
-    z = (g["kappa"] - pin) / np.hypot(g["kappa_se"], pin_se)
+    sig = np.hypot(g["kappa_se"], pin_se)
+    z = (g["kappa"] - pin) / sig
     print(f"\nfirst-event pored film: GPU {g['kappa']:.4f} +- {g['kappa_se']:.4f}, quadrature {pin:.4f} +- {pin_se:.4f}")
-    assert abs(z) < 4.0, z
-    assert abs(g["kappa"] / pin - 1.0) < 2e-3
+    assert 3.0 * sig < 1e-3 * pin
+    assert abs(z) < 3.0, z
+    assert abs(g["kappa"] / pin - 1.0) < 1e-3
 
 
 def test_ballistic_spreading_between_specular_faces(P, oracle, analytic):
@@ -480,16 +517,27 @@ def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     assert _z(g, o, "kappa") < 3.0
 
 
-def test_pulse_full_size_conserves_every_particle(P):
+def test_pulse_full_size_conserves_every_particle(P, oracle):
     # config-2 transient at full size: with adiabatic walls every particle is
     # counted exactly once at every sample after the pulse has been emitted
-    # (emission times beyond 17 sigma of the 300 ps pulse do not occur)
+    # (emission times beyond 17 sigma of the 300 ps pulse do not occur).  The
+    # 32 x 64 x 64 grid summed over 8 x 8 x 8 blocks is the 4 x 8 x 8 grid of
+    # the same domain, on which the FP64 oracle counts 1e6 particles: per
+    # sample time the two come from the same cell probabilities.
     n = 100_000_000
-    g = P.simulate(W.porous_pulse(n_particles=n))
+    prob = W.porous_pulse(n_particles=n)
+    g = P.simulate(prob)
     sums = g["grid"].reshape(g["grid"].shape[0], -1).sum(axis=1, dtype=np.int64)
     assert sums[-1] == n
     assert np.all(np.diff(sums[:60]) >= 0)  # the count only grows while the pulse emits
     assert g["device_flags"] == 0
+    ns = g["grid"].shape[0]
+    coarse = g["grid"].reshape(ns, 8, 8, 8, 8, 4, 8).sum(axis=(2, 4, 6), dtype=np.int64)
+    n_o = 1_000_000
+    o = oracle.run(W.porous_pulse(n_particles=n_o, precision="fp64", grid=(4, 8, 8), seed=prob["run"]["seed"] + 1))
+    pv = homogeneity_pvalues(coarse, o["grid"], n, n_o)
+    print(f"\nfull-size pulse, 4 x 8 x 8 blocks vs the FP64 oracle: min p over {ns} samples {pv.min():.3g}")
+    assert pv.min() > 1e-3 / ns, np.sort(pv)[:5]
 
 
 def test_scattering_cap_drops_exactly_the_later_flux_split(P):
