@@ -34,6 +34,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -58,6 +60,33 @@ WORKLOAD = ("silicon-like thin film 100 nm, diffuse walls, gradient along z, LA 
 #   event counters and termination tests                                    6
 OPS_PER_SEGMENT = 84
 LANES_PER_SM = 128  # FP32/INT32 lanes issuing one operation per clock
+
+# The other kernels timed here, counted the same way (lane operations from
+# the algorithm; a transcendental, reciprocal or square root counts as one):
+#   gray slab, walls source, black walls, one mode, 50-bin profile: the film's
+#     84 without the Eq. 2 table lookup (one mode: -4), plus the profile: bin
+#     range (2 floors, 2 clamps), time per unit x (rcp, mul), two partial-bin
+#     and one whole-bin range update of T and q (6 shared FP64 adds, 10
+#     products)                                                             +22
+OPS_SLAB = 84 - 4 + 22
+#   pored film, steady: the film's 84 plus the cylinder (squared norms and the
+#     dot product 6, discriminant 2, sqrt, difference, reciprocal, product,
+#     clamp, two tests, compare/select 3: 16), two unit-cell faces ahead
+#     (select numerator, reciprocal, product, compare, select: 10), y and z
+#     advance (2), pore-wall normal and cosine law about it (2 differences, 2
+#     products, 6 multiply-adds: 10), outcome selects for the cylinder and the
+#     faces (6) and periodic re-insertion (4)                                 +48
+OPS_POROUS = 84 + 48
+#   surface pulse: the pored film's segment plus the segment end time (rcp,
+#     multiply-add), the sample index range (2 products, 2 ceilings, 2 clamps,
+#     2 compares) and the deferred job record (11 shared stores): +21 per
+#     segment; per sample update: owner search (5 shuffles, 5 compares),
+#     interpolated position (1 product, 1 multiply-add, 3 multiply-adds), cell
+#     (3 products, 3 floors, 6 clamps, 3 index multiply-adds) and the int32
+#     reduction: 31
+OPS_PULSE_SEG = OPS_POROUS + 21
+OPS_PULSE_SAMPLE = 31
+BYTES_PULSE_SAMPLE = 4  # one int32 reduction into the grid per sample update
 
 
 def _sha_kernel_sources():
@@ -294,6 +323,89 @@ def served_measurement(P, seconds, max_slots=16):
     return out
 
 
+def config_measurements(P, torch, dev, stream, flush, steps, warmup, peak_ops, peaks):
+    """The other workloads of the method, each timed alone with CUDA events on
+    its launching stream (trace kernel only, from le_mc_tallies.kernel_ms,
+    and the whole le_mc_run step), L2 flushed before every step:
+      slab          gray slab, Kn = 1, black walls at T_eq +- 1 K, T(x) and
+                    q(x) on 50 bins, 1e8 particles (FP64, the configuration's
+                    precision, and FP32 trajectories)
+      porous        steady pored film (300 nm, pitch 100 nm, radius 30 nm,
+                    silicon-like, K_s 40, K_e 4096), 1e8 particles, FP32
+      pulse         surface heat pulse on the 6 x 6-cell pored film, Eq. 3
+                    grid 32 x 64 x 64 at 200 samples, 1e8 particles, FP32"""
+    out = {}
+    cases = [
+        ("slab_fp64", W.gray_slab(n_particles=100_000_000, n_bins=50, precision="fp64"), OPS_SLAB, "fp64"),
+        ("slab_fp32", W.gray_slab(n_particles=100_000_000, n_bins=50, precision="fp32"), OPS_SLAB, "alu"),
+        ("porous", W.porous_film(n_particles=100_000_000), OPS_POROUS, "alu"),
+        ("pulse", W.porous_pulse(n_particles=100_000_000), OPS_PULSE_SEG, "alu"),
+    ]
+    sms = P.le_mc_device_info()[0]
+    sm_hz = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    for name, prob, ops_seg, bound in cases:
+        mat = P.le_mc_create_material(P.material_desc(prob["material"]))
+        geo = P.le_mc_create_geometry(P.geometry_desc(prob["geometry"]))
+        try:
+            k_steps = max(1, min(steps, 5))
+            step_ms, kern_ms, segs, samples, flags, launches = [], [], 0, 0, 0, 0
+            for k in range(warmup + k_steps):
+                rd = P.run_desc(prob["source"], W.with_run(prob, seed=prob["run"]["seed"] + 7000 + k)["run"])
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h = P.le_mc_run(mat, geo, rd, stream)
+                e1.record(stream)
+                t = P.le_mc_read_tallies(h)
+                if k >= warmup:
+                    step_ms.append(e0.elapsed_time(e1))
+                    kern_ms.append(t["kernel_ms"])
+                    segs += t["segments"]
+                    flags |= t["device_flags"]
+                    launches += t["kernel_launches"]
+                    if prob["run"].get("n_samples", 0) > 0:
+                        g = P.le_mc_read_array(h, "grid")
+                        samples += int(np.abs(g.astype(np.int64)).sum())
+                P.le_mc_destroy_run(h)
+        finally:
+            P.le_mc_destroy_geometry(geo)
+            P.le_mc_destroy_material(mat)
+        per_launch_s = statistics.mean(kern_ms) / 1e3
+        seg_launch = segs / k_steps
+        smp_launch = samples / k_steps
+        ops = seg_launch * ops_seg + smp_launch * (OPS_PULSE_SAMPLE if name == "pulse" else 0)
+        entry = {"value": segs / (sum(step_ms) / 1e3), "unit": UNIT, "steps": k_steps, "warmup": warmup,
+                 "ms_per_step": statistics.mean(step_ms), "kernel_ms_per_launch": 1e3 * per_launch_s,
+                 "segments_per_launch": seg_launch, "particles_per_launch": prob["run"]["n_particles"],
+                 "device_flags": flags, "gpu_launches": launches}
+        if bound == "fp64":
+            # FP64 trajectories: the segment's geometric and transcendental
+            # operations run on the FP64 units (Philox stays on the integer
+            # units); GB300's nominal dense FP64 rate is 1.25 TFLOP/s, i.e.
+            # 6.25e11 operations/s counting a fused multiply-add as one (no
+            # measured FP64 peak is available)
+            peak = 6.25e11
+            fp64_ops = seg_launch * (ops_seg - 40)
+            entry["roofline"] = {"bound": "fp64", "achieved": fp64_ops / per_launch_s / 1e12, "peak": peak / 1e12,
+                                 "unit": "Tops/s", "frac": fp64_ops / per_launch_s / peak,
+                                 "ops_per_segment": ops_seg - 40,
+                                 "peak_basis": "nominal GB300 dense FP64, 1.25 TFLOP/s (FMA = 2 flops)"}
+        else:
+            achieved = ops / per_launch_s
+            entry["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                                 "unit": "Tops/s", "frac": achieved / peak_ops, "ops_per_segment": ops_seg,
+                                 "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_hz / 1e6:.0f} MHz"}
+        if name == "pulse":
+            entry["sample_updates_per_launch"] = smp_launch
+            entry["ops_per_sample_update"] = OPS_PULSE_SAMPLE
+            hbm = float(peaks.get("hbm_gbs", 6800.0))
+            gbs = smp_launch * BYTES_PULSE_SAMPLE / per_launch_s / 1e9
+            entry["grid_reductions"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                        "frac": gbs / hbm, "bytes_per_sample_update": BYTES_PULSE_SAMPLE}
+        out[name] = entry
+    return out
+
+
 def run_reference(args, problem, rank, world):
     """Reference arm: the FP64 CPU oracle, one bounded sample per step."""
     if rank != 0:
@@ -342,6 +454,8 @@ def main():
     ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the gray-slab and pored-film (steady, pulse) measurements")
     ap.add_argument("--served-seconds", type=float, default=60.0,
                     help="length of the request stream of the served form (0 = skip)")
     args = ap.parse_args()
@@ -424,9 +538,13 @@ def main():
 
     # ---- end to end through the C ABI, host descriptors and results -------
     e2e_steps = max(3, min(args.steps, 10))
-    n_modes = 3000
-    h2d = n_modes * (8 + 16 + 8 + 8)  # FP32 + FP64 mode properties, two alias tables
-    d2h = 2 * 8 + 7 * 8 + 2 * 8       # sums, counters, queue head and flags
+    n_modes = P.le_mc_material_table(P.material_desc(prob["material"]))[0].size
+    # le_mc_create_material uploads per mode: (Lambda, v) in FP32 and FP64
+    # and three alias tables (emission, Eq. 2, initial condition) of 8 bytes
+    h2d = n_modes * (8 + 16 + 3 * 8)
+    # le_mc_read_tallies reads sums, counters, queue head and flags, and the
+    # long-first list counts (runs of >= 4096 particles)
+    d2h = 2 * 8 + 7 * 8 + 2 * 8 + (3 * 4 if args.n_particles >= 4096 else 0)
     e2e_segs = 0
     if dist is not None:
         dist.barrier()
@@ -450,15 +568,19 @@ def main():
     P.le_mc_destroy_geometry(geo)
     P.le_mc_destroy_material(mat)
 
+    peaks, peak_src = _peaks()
+    sms, name = P.le_mc_device_info()
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_ops = sms * LANES_PER_SM * sm_mhz * 1e6
+    configs = None
+    if not args.no_configs and rank == 0:
+        configs = config_measurements(P, torch, dev, stream, flush, args.steps, max(3, args.warmup), peak_ops, peaks)
+
     if rank != 0:
         dist.destroy_process_group()
         return
 
-    peaks, peak_src = _peaks()
-    sms, name = P.le_mc_device_info()
     clocks = sampler.summary()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_ops = sms * LANES_PER_SM * sm_mhz * 1e6
     per_launch_s = statistics.mean(kern_ms) / 1e3
     segs_per_launch = segs / args.steps
     achieved = segs_per_launch * OPS_PER_SEGMENT / per_launch_s
@@ -486,6 +608,8 @@ def main():
         "clocks": clocks,
         "device_flags": flags,
     }
+    if configs is not None:
+        line["configs"] = configs
     if not args.no_batched:
         line["batched"] = batched_measurement(P, torch, dev, stream, args.steps, launch)
         # whole-launch rate (the dominant kernel is the same trace kernel)
