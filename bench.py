@@ -77,6 +77,12 @@ OPS_SLAB = 84 - 4 + 22
 #     products, 6 multiply-adds: 10), outcome selects for the cylinder and the
 #     faces (6) and periodic re-insertion (4)                                 +48
 OPS_POROUS = 84 + 48
+#   pored film with 8 x 8 steady maps: the pored film's segment plus the map
+#     cell range (2 products, 2 floors, 2 clamps, 2 reciprocals, per axis an
+#     end-point estimate and its exact check: 12) and the deferred job record
+#     (12 shared stores); the per-cell work (merge search, interval, two FP64
+#     reductions) is not counted, so this fraction is a lower bound       +28
+OPS_POROUS_MAPS = OPS_POROUS + 28
 #   surface pulse: the pored film's segment plus the segment end time (rcp,
 #     multiply-add), the sample index range (2 products, 2 ceilings, 2 clamps,
 #     2 compares) and the deferred job record (11 shared stores): +21 per
@@ -332,6 +338,8 @@ def config_measurements(P, torch, dev, stream, flush, steps, warmup, peak_ops, p
                     precision, and FP32 trajectories)
       porous        steady pored film (300 nm, pitch 100 nm, radius 30 nm,
                     silicon-like, K_s 40, K_e 4096), 1e8 particles, FP32
+      porous_maps   the same with steady 8 x 8 maps of T and q_z over the unit
+                    cell (32 batch groups)
       pulse         surface heat pulse on the 6 x 6-cell pored film, Eq. 3
                     grid 32 x 64 x 64 at 200 samples, 1e8 particles, FP32"""
     out = {}
@@ -339,6 +347,7 @@ def config_measurements(P, torch, dev, stream, flush, steps, warmup, peak_ops, p
         ("slab_fp64", W.gray_slab(n_particles=100_000_000, n_bins=50, precision="fp64"), OPS_SLAB, "fp64"),
         ("slab_fp32", W.gray_slab(n_particles=100_000_000, n_bins=50, precision="fp32"), OPS_SLAB, "alu"),
         ("porous", W.porous_film(n_particles=100_000_000), OPS_POROUS, "alu"),
+        ("porous_maps", W.porous_film(n_particles=100_000_000, map=(8, 8), n_batch=32), OPS_POROUS_MAPS, "alu"),
         ("pulse", W.porous_pulse(n_particles=100_000_000), OPS_PULSE_SEG, "alu"),
     ]
     sms = P.le_mc_device_info()[0]
@@ -403,6 +412,9 @@ def config_measurements(P, torch, dev, stream, flush, steps, warmup, peak_ops, p
             entry["grid_reductions"] = {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
                                         "frac": gbs / hbm, "bytes_per_sample_update": BYTES_PULSE_SAMPLE}
         out[name] = entry
+    if "porous" in out and "porous_maps" in out:
+        out["porous_maps"]["cost_vs_plain"] = (out["porous_maps"]["kernel_ms_per_launch"] /
+                                               out["porous"]["kernel_ms_per_launch"])
     return out
 
 

@@ -30,6 +30,43 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk)
     return c;
 }
 
+// The random words of one flight of one particle: Philox4x32-10 of counter
+// (n, 0, pid, inst).  The first round's product of the pid word and the
+// words it meets there (the zero word, the instance word, the first round
+// keys) do not change along a history, so they are formed once per particle
+// (philox_lane) and each flight starts from them (philox_flight): one
+// multiplication and one XOR fewer per flight, the same words.
+struct PhiloxLane {
+    uint32_t a;  // mulhi(0xCD9E8D57, pid) ^ 0 ^ k0[0]
+    uint32_t b;  // mullo(0xCD9E8D57, pid)
+    uint32_t c;  // inst ^ k1[0]
+};
+
+__device__ __forceinline__ PhiloxLane philox_lane(uint32_t pid, uint32_t inst, const RoundKeys& rk)
+{
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * pid;
+    PhiloxLane l;
+    l.a = (uint32_t)(p1 >> 32) ^ rk.k0[0];
+    l.b = (uint32_t)p1;
+    l.c = inst ^ rk.k1[0];
+    return l;
+}
+
+__device__ __forceinline__ uint4 philox_flight(uint32_t n, const PhiloxLane& l, const RoundKeys& rk)
+{
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * n;
+    uint4 c = make_uint4(l.a, l.b, (uint32_t)(p0 >> 32) ^ l.c, (uint32_t)p0);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        const unsigned long long q0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long q1 = (unsigned long long)0xCD9E8D57u * c.z;
+        const uint32_t hi0 = (uint32_t)(q0 >> 32), lo0 = (uint32_t)q0;
+        const uint32_t hi1 = (uint32_t)(q1 >> 32), lo1 = (uint32_t)q1;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+    }
+    return c;
+}
+
 template <typename R>
 struct DMath;
 
@@ -55,6 +92,23 @@ struct DMath<float> {
     }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
     static __device__ __forceinline__ float big() { return 3.0e38f; }
+    // The value of x as a double, assembled from its bits on the integer
+    // units: GB300's FP64 units are narrow (a conversion there costs a warp
+    // as much as dozens of FP32 operations), and an FP32 kernel only needs
+    // the exact widening for its FP64 tally reductions.  Exact for zeros,
+    // normal numbers, infinities and NaNs; a subnormal (which these kernels
+    // flush to zero, -ftz=true) would be mis-scaled.
+    static __device__ __forceinline__ double to_f64(float x)
+    {
+        const uint32_t u = __float_as_uint(x);
+        const uint32_t sgn = u & 0x80000000u, mag = u & 0x7FFFFFFFu;
+        // exponent rebias 127 -> 1023 is + 896 in the exponent field
+        uint32_t hi = sgn | ((mag >> 3) + (896u << 20));
+        hi = mag == 0u ? sgn : hi;
+        hi = mag >= 0x7F800000u ? (sgn | 0x7FF00000u | ((mag >> 3) & 0x000FFFFFu)) : hi;
+        const uint32_t lo = mag == 0u ? 0u : (u << 29);
+        return __hiloint2double((int)hi, (int)lo);
+    }
 };
 
 // FP64 trajectories: u = (r + 1/2) 2^-32 and the libm functions.
@@ -76,6 +130,7 @@ struct DMath<double> {
     }
     static __device__ __forceinline__ double floor_(double x) { return floor(x); }
     static __device__ __forceinline__ double big() { return 1.0e300; }
+    static __device__ __forceinline__ double to_f64(double x) { return x; }
 };
 
 // Mode draw from an alias table: column j = floor(r n / 2^32), kept when the

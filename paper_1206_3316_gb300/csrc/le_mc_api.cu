@@ -483,18 +483,19 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     }
     fill_consts(P);
 
-    // (the steady maps live in global memory only; slab profiles also have a
-    // shared-memory copy per block)
-    const int smem_prof = has_map ? 0 : (int)h->prof_len;
+    // slab profiles of FP32 kernels: a per-block FP32 copy in shared memory
+    // when it is small enough (steady maps, the H_j split and FP64 profiles
+    // are reduced in global memory)
+    const bool prof_smem = fp32 && profile && !has_map && h->prof_len <= (size_t)kProfSmemMax;
+    P.prof_smem = prof_smem ? 1 : 0;
+    const int smem_prof = prof_smem ? (int)h->prof_len : 0;
     // launch shape: persistent grid of (SMs x resident blocks).  By default
     // 512 threads per block, or 256 when that keeps more warps resident (a
     // kernel instance whose registers leave room for only one 512-thread
     // block per SM)
     auto shape_for = [&](int t, size_t* sm_bytes, int* resident) {
-        cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, smem_prof,
-                                                (int)h->hj_len, sm_bytes)
-                               : smem_trace_f64(G.kind, r.source, profile, m->n_modes, t, smem_prof,
-                                                (int)h->hj_len, sm_bytes);
+        cudaError_t err = fp32 ? smem_trace_f32(G.kind, r.source, profile, m->n_modes, t, smem_prof, 0, sm_bytes)
+                               : smem_trace_f64(G.kind, r.source, profile, m->n_modes, t, smem_prof, 0, sm_bytes);
         if (err == cudaSuccess)
             err = fp32 ? occupancy_trace_for_f32(P, profile, t, *sm_bytes, resident)
                        : occupancy_trace_for_f64(P, profile, t, *sm_bytes, resident);

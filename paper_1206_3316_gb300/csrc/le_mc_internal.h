@@ -70,6 +70,12 @@ struct Consts {
 
 constexpr int kBatchSmemMax = 512;
 
+// Slab profiles of FP32 kernels: FP32 shared-memory copy of at most this
+// many entries ([4][n_batch][n_bins_x + 1]), each warp draining its share of
+// the entries into the FP64 sums every kProfDrainEvery loop iterations.
+constexpr int kProfSmemMax = 12288;
+constexpr int kProfDrainEvery = 32;
+
 // Extreme particles: emission mean free path above kExtremeFactor times the
 // long-first cut (1024 film thicknesses by default), at most kExtCap per
 // launch (the rest join the ordinary long-first list).  They only matter in
@@ -114,6 +120,7 @@ struct TraceParams {
     Consts<double> c64;
     // run
     uint32_t n_particles, key0, key1, inst, max_scatter, max_events, max_collisions;
+    uint32_t scat_cap;  // max_scatter, or 2^32 - 1 when there is no scattering cap
     // slab profile: [4][n_batch][n_bins_x + 1] (T direct, T difference,
     // q direct, q difference), FP64; or, in pored films, the steady maps
     // [2][n_batch][map_nz][map_ny] (sum of s x time, sum of s x z
@@ -121,6 +128,10 @@ struct TraceParams {
     int32_t n_bins_x, n_batch;
     int32_t map_ny, map_nz;
     double* prof;
+    // FP32 kernels with a slab profile of at most kProfSmemMax entries keep
+    // a per-block FP32 copy in shared memory that their warps drain into
+    // prof (0 = every contribution is reduced into prof directly)
+    int32_t prof_smem;
     // flux by scattering index: [2][n_hj] (sum s h, sum h^2)
     int32_t n_hj;
     double* hj;

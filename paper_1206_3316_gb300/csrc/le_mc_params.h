@@ -57,6 +57,7 @@ inline void fill_run(TraceParams& P, const le_mc_run_desc& r)
     P.key1 = (uint32_t)(r.seed >> 32);
     P.inst = r.instance_id;
     P.max_scatter = r.max_scatter;
+    P.scat_cap = r.max_scatter > 0u ? r.max_scatter : 0xFFFFFFFFu;
     P.max_events = r.max_events;
     P.max_collisions = r.max_collisions;
 }

@@ -99,6 +99,18 @@ struct SampleJobs {
     int k0[32], sign[32], cell[32];  // cell: unit cell cy | cz << 16
 };
 
+// Steady-map kernels defer the map cells of a segment in the same way: each
+// lane leaves its segment's start (y, z), the reciprocals of its direction
+// components (0 when a component is 0), its length, its time and z-flux
+// weights per unit length, its first map cell, its counts of map-cell
+// boundaries crossed along y and z and its batch group; the warp then adds
+// the contributions of every crossed cell of every lane, one cell per lane.
+template <typename R>
+struct MapJobs {
+    R y[32], z[32], ry[32], rz[32], seg[32], wT[32], wQ[32];
+    int j0[32], k0[32], nyc[32], nzc[32], g[32];
+};
+
 template <typename R, int GEOM, int SRC, bool BATCH = false>
 using BufferOf = EmitBuffer<R, GEOM == LE_MC_GEOM_POROUS, SRC == LE_MC_SRC_PULSE, BATCH>;
 
@@ -329,6 +341,8 @@ __device__ __forceinline__ bool emit_particle(const TraceParams& P, const EmitCt
     return ok;
 }
 
+constexpr float kLn2f = 0.693147180559945f;
+
 template <typename R, int SRC, bool PROFILE>
 struct FusedTable {
     static constexpr bool value = sizeof(R) == 4 && SRC != LE_MC_SRC_PULSE && SRC != LE_MC_SRC_INITIAL && !PROFILE;
@@ -386,15 +400,14 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     off += (size_t)n_warps * sizeof(Buf);
     SampleJobs<R>* s_jobs = reinterpret_cast<SampleJobs<R>*>(smem + off);
     if constexpr (TRANSIENT) off += (size_t)n_warps * sizeof(SampleJobs<R>);
+    MapJobs<R>* s_mjobs = reinterpret_cast<MapJobs<R>*>(smem + off);
+    if constexpr (PROFILE && POROUS) off += (size_t)n_warps * sizeof(MapJobs<R>);
+    // FP32 slab profile copy of this block (drained into the FP64 sums)
+    constexpr bool PROF32 = PROFILE && !POROUS && sizeof(R) == 4;
+    float* s_prof32 = reinterpret_cast<float*>(smem + off);
+    const int prof32_len = (PROF32 && P.prof_smem) ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
+    off += (size_t)prof32_len * sizeof(float);
     off = (off + 7) & ~(size_t)7;
-    double* s_prof = reinterpret_cast<double*>(smem + off);
-    // slab profile in shared memory (PLANES; the steady maps of POROUS
-    // kernels are added to global memory directly)
-    const int prof_len = (PROFILE && !POROUS) ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
-    off += (size_t)prof_len * sizeof(double);
-    double* s_hj = reinterpret_cast<double*>(smem + off);
-    const int hj_len = 2 * P.n_hj;
-    off += (size_t)hj_len * sizeof(double);
     // batch mode: per-instance sums [n][2] and counters [n][CNT_N] of this block
     const bool inst_in_smem = BATCH && P.n_instances <= kBatchSmemMax;
     const int inst_len = inst_in_smem ? P.n_instances : 0;
@@ -407,17 +420,18 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         load_props<R>(P.props, (uint32_t)i, lam, vg);
         const uint2 e = P.alias_scat[i];
         if constexpr (FUSED) {
+            // (Lambda ln 2: the flight -Lambda ln u is then -(Lambda ln 2) log2 u)
             R lam_a, vg_a;
             load_props<R>(P.props, e.y, lam_a, vg_a);
-            s_fused[i] = make_uint4(e.x, e.y, __float_as_uint((float)lam), __float_as_uint((float)lam_a));
+            s_fused[i] = make_uint4(e.x, e.y, __float_as_uint((float)lam * kLn2f),
+                                    __float_as_uint((float)lam_a * kLn2f));
         } else {
             s_props[2 * i] = lam;
             s_props[2 * i + 1] = vg;
             s_scat[i] = e;
         }
     }
-    for (int i = threadIdx.x; i < prof_len; i += blockDim.x) s_prof[i] = 0.0;
-    for (int i = threadIdx.x; i < hj_len; i += blockDim.x) s_hj[i] = 0.0;
+    for (int i = threadIdx.x; i < prof32_len; i += blockDim.x) s_prof32[i] = 0.0f;
     for (int i = threadIdx.x; i < 2 * inst_len; i += blockDim.x) s_isum[i] = 0.0;
     for (int i = threadIdx.x; i < CNT_N * inst_len; i += blockDim.x) s_icnt[i] = 0ull;
     __syncthreads();
@@ -460,6 +474,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     R x = 0, y = 0, z = 0, ox = 0, oy = 0, oz = 1, t = 0, lam = 1, vg = 1;
     R Lacc = 0, hrun = 0, x0 = 0, t0 = 0;
     uint32_t pid = 0, n_seg = 0, n_scat = 0, n_wall = 0, n_per = 0, mode0 = 0;
+    int pgroup = 0;  // batch group of the particle (profiles and maps), set once per particle
+    PhiloxLane plane = {0u, 0u, 0u};  // per-particle part of the flights' random words
     int cy = 0, cz = 0, sign = 1, fate = FATE_MAX_EVENTS;
     bool alive = false, pending = false;
     // problem of the current particle (batch mode: its instance)
@@ -470,6 +486,35 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     Acc<R> acc_sL, acc_sL2;
     uint32_t c_part = 0, c_seg = 0, c_scat = 0, c_wall = 0, c_per = 0, c_trunc = 0, c_abs = 0;
     uint32_t flags = 0;
+
+    // FP64 tally reduction into global memory: the add is done by the L2's
+    // atomic units, and FP32 kernels widen the value on the integer units, so
+    // no tally arithmetic reaches the (narrow) FP64 pipe of the SM
+    auto red64 = [&](double* dst, R v) {
+        const double d = M::to_f64(v);
+#ifdef LEMC_DEBUG
+        if (!(d == (double)v) && v == v) flags |= FLAG_DEBUG_BOUNDS;
+#endif
+        atomicAdd(dst, d);
+    };
+
+    // Slab profile entry i: into this block's FP32 copy (native shared-memory
+    // adds) when it has one, else straight into the FP64 sums.  Each warp
+    // drains its share of the copy (atomic exchange with 0, then one FP64
+    // reduction per nonzero entry) every kProfDrainEvery loop iterations, so
+    // an FP32 partial sum holds only the few dozen contributions made to its
+    // entry in between; the block drains everything at the end.
+    auto prof_add = [&](size_t i, R v) {
+        if (PROF32 && prof32_len > 0) atomicAdd(&s_prof32[i], (float)v);
+        else red64(P.prof + i, v);
+    };
+    int drain_it = 0;
+    auto drain_prof = [&](int first, int end) {
+        for (int i = first + lane; i < end; i += 32) {
+            const float v = atomicExch(&s_prof32[i], 0.0f);
+            if (v != 0.0f) red64(P.prof + i, (R)v);
+        }
+    };
 
     int cnt = 0;         // emission buffer fill (warp-uniform)
     bool qdone = false;  // particle queue exhausted (warp-uniform)
@@ -566,11 +611,98 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         job_n = 0;
     };
 
+    // Map-cell boundaries crossed by a segment of length seg that starts at
+    // coordinate u (within the unit cell) in map cell c0 of n, with direction
+    // component o and r = 1 / o (0: parallel): crossing a (a = 0, 1, ...) is at
+    // parameter t(a) = ((c0 + s a + [s > 0]) h - u) r, s the direction's
+    // sign; a boundary counts when t(a) < seg and the next cell is on the
+    // map.  The estimate from the end point is corrected by the exact
+    // comparisons (at most one step each way).
+    auto map_crossings = [&](R u, R o, R r, R seg, int c0, int n, R h, R ih) -> int {
+        if (r == R(0)) return 0;
+        const int sg = r > R(0) ? 1 : -1;
+        const int up = r > R(0) ? 1 : 0;
+        const int amax = sg > 0 ? n - 1 - c0 : c0;
+        auto t_of = [&](int a) { return ((R)(c0 + sg * a + up) * h - u) * r; };
+        const R ue = u + o * seg;
+        const int ce = min(max((int)M::floor_(ue * ih), 0), n - 1);
+        int m = min(max(sg > 0 ? ce - c0 : c0 - ce, 0), amax);
+        while (m > 0 && !(t_of(m - 1) < seg)) --m;
+        while (m < amax && t_of(m) < seg) ++m;
+        return m;
+    };
+    // Cell i (0 .. nyc + nzc) of a segment's walk over the map: after a
+    // crossings along y and b = i - a along z, a being the number of y
+    // crossings among the first i in order of parameter (y first on ties),
+    // found by a merge-path binary search; the segment spends the parameter
+    // interval [latest crossing so far, earliest next crossing or seg] in
+    // it, and adds d wT and d wQ to the cell's FP64 sums of batch group g.
+    auto map_item = [&](R y0, R z0, R ry, R rz, R seg, R wT, R wQ, int j0, int k0, int nyc, int nzc, int g, int i) {
+        const int sy = ry > R(0) ? 1 : -1, sz = rz > R(0) ? 1 : -1;
+        const int uy = ry > R(0) ? 1 : 0, uz = rz > R(0) ? 1 : 0;
+        auto ty = [&](int a) { return ry != R(0) ? ((R)(j0 + sy * a + uy) * K.map_dy - y0) * ry : big; };
+        auto tz = [&](int b) { return rz != R(0) ? ((R)(k0 + sz * b + uz) * K.map_dz - z0) * rz : big; };
+        int lo = max(0, i - nzc), hi = min(i, nyc);
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const R tzm = (i - mid < nzc) ? tz(i - mid) : big;
+            if (ty(mid - 1) <= tzm) lo = mid;
+            else hi = mid - 1;
+        }
+        const int a = lo, b = i - lo;
+        const R t_in = fmax(a > 0 ? ty(a - 1) : R(0), b > 0 ? tz(b - 1) : R(0));
+        const R t_out = fmin(fmin(ty(a), tz(b)), seg);
+        const R d = t_out - t_in;
+        if (d > R(0)) {
+            const int ny = P.map_ny;
+            const size_t cells = (size_t)ny * P.map_nz;
+            size_t c = (size_t)(k0 + sz * b) * ny + (size_t)(j0 + sy * a);
+            LEMC_GUARD_INDEX(c, cells);
+            red64(P.prof + (size_t)g * cells + c, d * wT);
+            red64(P.prof + ((size_t)P.n_batch + g) * cells + c, d * wQ);
+        }
+    };
+    // Add every deferred map cell of the warp (all 32 lanes converged): item
+    // j of the warp's total belongs to the first lane whose inclusive prefix
+    // count exceeds j, as for the sample jobs.
+    int mjob_n = 0;
+    auto flush_map_jobs = [&]() {
+        const int total = __reduce_add_sync(FULL, (unsigned)mjob_n);
+        if (total == 0) return;
+        int inc = mjob_n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += v;
+        }
+        const int excl = inc - mjob_n;
+        const MapJobs<R>& J = s_mjobs[threadIdx.x >> 5];
+        __syncwarp();
+        for (int base = 0; base < total; base += 32) {
+            const int j = base + lane;
+            int own = 0;
+#pragma unroll
+            for (int bit = 16; bit > 0; bit >>= 1) {
+                const int v = __shfl_sync(FULL, inc, own + bit - 1);
+                if (v <= j) own += bit;
+            }
+            LEMC_GUARD_INDEX(own, 32);
+            const int own_excl = __shfl_sync(FULL, excl, own);
+            if (j < total)
+                map_item(J.y[own], J.z[own], J.ry[own], J.rz[own], J.seg[own], J.wT[own], J.wQ[own], J.j0[own],
+                         J.k0[own], J.nyc[own], J.nzc[own], J.g[own], j - own_excl);
+        }
+        __syncwarp();
+        mjob_n = 0;
+    };
+
     // ---- one segment: steps II-VI, from the segment's four random words r
     // (counter (n_seg + 1, 0, pid, instance): known before the segment runs)
     auto segment = [&](const uint4 r, const bool coop) {
         // step II: flight to the next relaxation event (as a length)
-        const R ell = lam * M::neg_log(M::uniform(r.x));
+        R ell;
+        if constexpr (FUSED) ell = -(lam * __log2f(M::uniform(r.x)));  // lam holds Lambda ln 2 here
+        else ell = lam * M::neg_log(M::uniform(r.x));
         // step III: first boundary along the ray
         R d_b = big;
         int kind = HIT_NONE;
@@ -679,97 +811,90 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             }
         }
         if constexpr (PROFILE && POROUS) {
-            // steady maps (Eq. 4 per map cell): walk the cells of the (y, z)
-            // map that the segment crosses, adding s x (time over the cell)
-            // and s x (z displacement over the cell) to the run's FP64 map
-            // sums.  Reductions into global memory measured faster here than
-            // FP64 (or fixed-point integer) atomics on shared-memory copies.
-            // Each crossing parameter comes from its own cell boundary, so
-            // the walk accumulates no drift.
+            // steady maps (Eq. 4 per map cell): the segment adds s x (time
+            // over the cell) and s x (z displacement over the cell) to every
+            // cell of the (y, z) map that it crosses.  Here only the cell
+            // range is found: the first cell, and how many cell boundaries
+            // the segment crosses along y and along z before it ends (each
+            // crossing parameter from its own boundary, so nothing drifts);
+            // the cells themselves are added by map_item, converged across
+            // the warp (flush_map_jobs) or, in the assisted rounds, by this
+            // lane alone.
             const int ny = P.map_ny, nz = P.map_nz;
-            const size_t cells = (size_t)ny * nz;
-            // batch group of the particle pair (2i, 2i + 1), so that every
-            // group holds both signs of the gradient source
-            const int g = (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
-            double* mT = P.prof + (size_t)g * cells;
-            double* mQ = P.prof + ((size_t)P.n_batch + g) * cells;
             // (a position on the cell's far faces rounds at most one map cell out)
             LEMC_DEBUG_CHECK(y * K.map_iy > R(-1) && y * K.map_iy < (R)(ny + 1) && z * K.map_iz > R(-1) &&
                              z * K.map_iz < (R)(nz + 1));
-            int j = min(max((int)M::floor_(y * K.map_iy), 0), ny - 1);
-            int k = min(max((int)M::floor_(z * K.map_iz), 0), nz - 1);
-            const bool up_y = oy > R(0), up_z = oz > R(0);
+            const int j0 = min(max((int)M::floor_(y * K.map_iy), 0), ny - 1);
+            const int k0 = min(max((int)M::floor_(z * K.map_iz), 0), nz - 1);
             const R ry = oy != R(0) ? M::div(R(1), oy) : R(0);
             const R rz = oz != R(0) ? M::div(R(1), oz) : R(0);
+            const int nyc = map_crossings(y, oy, ry, seg, j0, ny, K.map_dy, K.map_iy);
+            const int nzc = map_crossings(z, oz, rz, seg, k0, nz, K.map_dz, K.map_iz);
+            const int g = pgroup;
             const R wT = M::div((R)sign, vg), wQ = (R)sign * oz;
-            R t_in = R(0);
-            for (int it = 0; it <= ny + nz; ++it) {
-                const R ty = oy != R(0) ? ((R)(j + (up_y ? 1 : 0)) * K.map_dy - y) * ry : big;
-                const R tz = oz != R(0) ? ((R)(k + (up_z ? 1 : 0)) * K.map_dz - z) * rz : big;
-                const R t_out = fmin(fmin(ty, tz), seg);
-                const R d = t_out - t_in;
-                if (d > R(0)) {
-                    const size_t c = (size_t)k * ny + j;
-                    atomicAdd(&mT[c], (double)(d * wT));
-                    atomicAdd(&mQ[c], (double)(d * wQ));
-                }
-                if (t_out >= seg) break;
-                if (ty <= tz) {
-                    j += up_y ? 1 : -1;
-                    if (j < 0 || j >= ny) break;
-                } else {
-                    k += up_z ? 1 : -1;
-                    if (k < 0 || k >= nz) break;
-                }
-                t_in = t_out;
+            if (coop) {
+                mjob_n = 1 + nyc + nzc;
+                MapJobs<R>& J = s_mjobs[threadIdx.x >> 5];
+                J.y[lane] = y;
+                J.z[lane] = z;
+                J.ry[lane] = ry;
+                J.rz[lane] = rz;
+                J.seg[lane] = seg;
+                J.wT[lane] = wT;
+                J.wQ[lane] = wQ;
+                J.j0[lane] = j0;
+                J.k0[lane] = k0;
+                J.nyc[lane] = nyc;
+                J.nzc[lane] = nzc;
+                J.g[lane] = g;
+            } else {
+                for (int i = 0; i <= nyc + nzc; ++i) map_item(y, z, ry, rz, seg, wT, wQ, j0, k0, nyc, nzc, g, i);
             }
         }
         if constexpr (PROFILE && !POROUS) {
             // time spent in each bin along x, and the displacement along the
             // flux axis made there: x for the walls source (slab), z for the
-            // gradient source (the in-plane flux of a film by depth)
+            // gradient source (the in-plane flux of a film by depth); arrays
+            // [4][n_batch][n_bins_x + 1] (T direct, T difference, q direct, q
+            // difference) of FP64 sums, through prof_add
             const int nb = P.n_bins_x;
             const R dx = L / (R)nb;
-            // batch group: particle ids mod n_batch, or particle pairs (2i,
-            // 2i + 1) for the gradient source, whose even and odd ids carry
-            // opposite signs
-            const int g = AXIS_X ? (int)((pid - P.first) % (uint32_t)P.n_batch)
-                                 : (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
+            const int g = pgroup;
             const size_t stride = (size_t)nb + 1;
-            double* Td = s_prof + (0 * (size_t)P.n_batch + g) * stride;
-            double* Tr = s_prof + (1 * (size_t)P.n_batch + g) * stride;
-            double* qd = s_prof + (2 * (size_t)P.n_batch + g) * stride;
-            double* qr = s_prof + (3 * (size_t)P.n_batch + g) * stride;
+            const size_t Td = (0 * (size_t)P.n_batch + g) * stride;
+            const size_t Tr = (1 * (size_t)P.n_batch + g) * stride;
+            const size_t qd = (2 * (size_t)P.n_batch + g) * stride;
+            const size_t qr = (3 * (size_t)P.n_batch + g) * stride;
             const R lo = fmin(x, x_new), hi = fmax(x, x_new);
             int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
             // (a wall position rounds at most one bin out)
             LEMC_DEBUG_CHECK(k0 >= -1 && k1 <= nb);
             k0 = min(max(k0, 0), nb - 1);
             k1 = min(max(k1, 0), nb - 1);
-            const double s = (double)sign;
+            const R sr = (R)sign;
             if (ox == R(0)) {
-                atomicAdd(&Td[k0], s * (double)(seg / vg));
-                if constexpr (!AXIS_X) atomicAdd(&qd[k0], s * (double)(oz * seg));
+                prof_add(Td + k0, sr * (seg / vg));
+                if constexpr (!AXIS_X) prof_add(qd + k0, sr * (oz * seg));
             } else {
                 const R w = R(1) / (vg * fabs(ox));  // time per unit x
                 // displacement along the flux axis per unit x
                 const R qs = AXIS_X ? (ox > R(0) ? R(1) : R(-1)) : M::div(oz, fabs(ox));
                 if (k0 == k1) {
                     const R len = hi - lo;
-                    atomicAdd(&Td[k0], s * (double)(len * w));
-                    atomicAdd(&qd[k0], s * (double)(len * qs));
+                    prof_add(Td + k0, sr * (len * w));
+                    prof_add(qd + k0, sr * (len * qs));
                 } else {
                     const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
                     const R lb = hi - (R)k1 * dx;        // partial last bin
-                    atomicAdd(&Td[k0], s * (double)(la * w));
-                    atomicAdd(&qd[k0], s * (double)(la * qs));
-                    atomicAdd(&Td[k1], s * (double)(lb * w));
-                    atomicAdd(&qd[k1], s * (double)(lb * qs));
+                    prof_add(Td + k0, sr * (la * w));
+                    prof_add(qd + k0, sr * (la * qs));
+                    prof_add(Td + k1, sr * (lb * w));
+                    prof_add(qd + k1, sr * (lb * qs));
                     if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
-                        atomicAdd(&Tr[k0 + 1], s * (double)(dx * w));
-                        atomicAdd(&Tr[k1], -s * (double)(dx * w));
-                        atomicAdd(&qr[k0 + 1], s * (double)(dx * qs));
-                        atomicAdd(&qr[k1], -s * (double)(dx * qs));
+                        prof_add(Tr + k0 + 1, sr * (dx * w));
+                        prof_add(Tr + k1, -sr * (dx * w));
+                        prof_add(qr + k0 + 1, sr * (dx * qs));
+                        prof_add(qr + k1, -sr * (dx * qs));
                     }
                 }
             }
@@ -790,7 +915,9 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         ++n_seg;
         const bool scat = !hit;
         int wall = -1;
-        if constexpr (DIFF) {
+        if constexpr (DIFF && !POROUS) {
+            // (every boundary of a film is a diffuse wall: folded below)
+        } else if constexpr (DIFF) {
             wall = (hit && kind <= HIT_CYL) ? (int)LE_MC_WALL_DIFFUSE : -1;
         } else if constexpr (GEOM != LE_MC_GEOM_BULK) {
             wall = (kind == HIT_XLO) ? P.wall_lo : ((kind == HIT_XHI) ? P.wall_hi : -1);
@@ -803,10 +930,12 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 wall = (M::uniform(r.y) < p) ? (int)LE_MC_WALL_SPECULAR : (int)LE_MC_WALL_DIFFUSE;
             }
         }
-        const bool on_wall = wall >= 0;
-        const bool absorbed = wall == LE_MC_WALL_BLACK;
-        const bool diffuse = wall == LE_MC_WALL_DIFFUSE;
-        const bool periodic = hit && !on_wall;
+        // a film whose walls are all diffuse: every hit is a diffuse wall
+        constexpr bool FILM_DIFF = DIFF && GEOM == LE_MC_GEOM_PLANES;
+        const bool on_wall = FILM_DIFF ? hit : wall >= 0;
+        const bool absorbed = FILM_DIFF ? false : wall == LE_MC_WALL_BLACK;
+        const bool diffuse = FILM_DIFF ? hit : wall == LE_MC_WALL_DIFFUSE;
+        const bool periodic = FILM_DIFF ? false : hit && !on_wall;
         // Eq. 2 redraw (kept only on a relaxation event)
         if constexpr (FUSED) {
             const unsigned long long mm = (unsigned long long)r.y * (uint32_t)n_modes;
@@ -887,19 +1016,27 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         if constexpr (HJ) {  // flux split by scattering index
             if (P.n_hj > 0 && scat) {
                 if (n_scat - 1u < (uint32_t)P.n_hj) {
-                    atomicAdd(&s_hj[n_scat - 1u], (double)((R)sign * hrun));
-                    atomicAdd(&s_hj[P.n_hj + n_scat - 1u], (double)(hrun * hrun));
+                    red64(&P.hj[n_scat - 1u], (R)sign * hrun);
+                    red64(&P.hj[P.n_hj + n_scat - 1u], hrun * hrun);
                 }
                 hrun = R(0);
             }
         }
-        // step VI and truncation
-        if (absorbed) { fate = FATE_ABSORBED; alive = false; }
-        else if (TRANSIENT && t > K.t_final) { fate = FATE_T_FINAL; alive = false; }
-        else if (P.max_scatter > 0u && n_scat >= P.max_scatter) { fate = FATE_MAX_SCATTER; alive = false; }
-        else if (col_cap && n_scat + n_wall >= P.max_collisions) { fate = FATE_MAX_COLLISIONS; alive = false; }
-        else if (n_seg >= P.max_events) { fate = FATE_MAX_EVENTS; alive = false; }
-        if (!alive) pending = true;
+        // step VI and truncation: one combined test per segment; the fate
+        // (first reason in the order absorption, t_final, scattering cap,
+        // collision cap, segment cap) is only worked out when the particle ends
+        const bool t_out = TRANSIENT && t > K.t_final;
+        const bool s_cap = n_scat >= P.scat_cap;  // scat_cap = max_scatter, or 2^32 - 1 for none
+        const bool c_cap = col_cap && n_scat + n_wall >= P.max_collisions;
+        if (absorbed || t_out || s_cap || c_cap || n_seg >= P.max_events) {
+            fate = absorbed ? FATE_ABSORBED
+                 : t_out    ? FATE_T_FINAL
+                 : s_cap    ? FATE_MAX_SCATTER
+                 : c_cap    ? FATE_MAX_COLLISIONS
+                            : FATE_MAX_EVENTS;
+            alive = false;
+            pending = true;
+        }
     };
 
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
@@ -921,8 +1058,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         c_trunc += (fate == FATE_MAX_SCATTER || fate == FATE_MAX_EVENTS || fate == FATE_MAX_COLLISIONS) ? 1u : 0u;
         c_abs += (fate == FATE_ABSORBED) ? 1u : 0u;
         if (HJ && P.n_hj > 0 && n_scat < (uint32_t)P.n_hj && hrun != R(0)) {
-            atomicAdd(&s_hj[n_scat], (double)((R)sign * hrun));
-            atomicAdd(&s_hj[P.n_hj + n_scat], (double)(hrun * hrun));
+            red64(&P.hj[n_scat], (R)sign * hrun);
+            red64(&P.hj[P.n_hj + n_scat], hrun * hrun);
         }
         if (P.records) {
             le_mc_particle rec;
@@ -1050,6 +1187,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         }
         mode0 = ms & 0x7FFFFFFFu;
         LEMC_GUARD_INDEX(mode0, n_modes);
+        if constexpr (PROFILE) {
+            // batch group of the error bars: particle ids mod n_batch, or
+            // particle pairs (2i, 2i + 1) for the gradient source, whose even
+            // and odd ids carry opposite signs (every group holds both signs)
+            pgroup = AXIS_X ? (int)((pid - P.first) % (uint32_t)P.n_batch)
+                            : (int)(((pid - P.first) >> 1) % (uint32_t)P.n_batch);
+        }
         sign = (ms >> 31) ? -1 : 1;
         if constexpr (FUSED) {
             lam = __uint_as_float(s_fused[mode0].z);
@@ -1057,6 +1201,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             lam = s_props[2 * mode0];
             vg = s_props[2 * mode0 + 1];
         }
+        plane = philox_lane(pid, instw, rk);
         x0 = x;
         t0 = t;
         Lacc = 0;
@@ -1084,6 +1229,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // Phase B: the queue (long-first list, then the natural order).
     for (;;) {
         if constexpr (TRANSIENT) flush_jobs();
+        if constexpr (PROFILE && POROUS) flush_map_jobs();
+        if (PROF32 && prof32_len > 0 && ++drain_it == kProfDrainEvery) {
+            drain_it = 0;
+            const int per = (prof32_len + n_warps - 1) / n_warps;
+            const int w = (int)(threadIdx.x >> 5);
+            drain_prof(w * per, min((w + 1) * per, prof32_len));
+        }
         const unsigned dead = __ballot_sync(FULL, !alive);
         // refill once refill_min lanes are idle (or at once near the end)
         if (dead && (dead == FULL || qdone || __popc(dead) >= refill_min)) {
@@ -1133,9 +1285,19 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             if (!__any_sync(FULL, alive)) break;  // queue exhausted and buffer empty
         }
         if (!alive) continue;
-        segment(philox4x32_10(make_uint4(n_seg + 1u, 0u, pid, instw), rk), true);
+        segment(philox_flight(n_seg + 1u, plane, rk), true);
+        // Kernels of the gradient source (long histories) without deferred
+        // per-warp jobs trace a second segment in the same iteration (the
+        // loop's refill test runs half as often; for the short histories of
+        // the walls source this measured slower).  Every
+        // particle starts at the top of the loop, so its odd-numbered segments
+        // always run in the first copy of the segment code and its even ones
+        // in the second: which copy traces a segment never depends on timing.
+        if constexpr (SRC == LE_MC_SRC_GRADIENT && !(PROFILE && POROUS))
+            if (alive) segment(philox_flight(n_seg + 1u, plane, rk), true);
     }
     if constexpr (TRANSIENT) flush_jobs();
+    if constexpr (PROFILE && POROUS) flush_map_jobs();
 
     // ---- flush: warp shuffles, then one FP64 / u64 atomic per quantity ----
     if constexpr (BATCH) {
@@ -1150,6 +1312,11 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
                 if (s_icnt[i]) atomicAdd(&P.inst_counters[i], s_icnt[i]);
         }
         return;
+    }
+    if (PROF32 && prof32_len > 0) {  // what the warps have not drained yet
+        __syncthreads();
+        for (int i = threadIdx.x; i < prof32_len; i += blockDim.x)
+            if (s_prof32[i] != 0.0f) red64(P.prof + i, (R)s_prof32[i]);
     }
     double v0 = acc_sL.value(), v1 = acc_sL2.value();
 #pragma unroll
@@ -1171,40 +1338,47 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             if (red[i]) atomicAdd(&P.counters[i], red[i]);
         if (fl) atomicOr(P.flags, fl);
     }
-    if (prof_len + hj_len > 0) {
-        __syncthreads();
-        for (int i = threadIdx.x; i < prof_len; i += blockDim.x)
-            if (s_prof[i] != 0.0) atomicAdd(&P.prof[i], s_prof[i]);
-        for (int i = threadIdx.x; i < hj_len; i += blockDim.x)
-            if (s_hj[i] != 0.0) atomicAdd(&P.hj[i], s_hj[i]);
-    }
 }
 
-// Kernel entry points.  Pored-film FP32 kernels are held to 64 registers (two
-// 512-thread blocks per SM) although that spills ~250 bytes per thread:
-// measured on GB300, the doubled occupancy outweighs the spills (steady pored
-// film +7 %, surface pulse +17 %).  The others keep the compiler's own
-// register choice (naming a minimum of one block changes it for the worse),
-// and so do pored-film kernels with steady maps, whose walk over the map
-// cells spills under the cap (measured 7 % faster without it).
+// Kernel entry points.  Some FP32 kernels are held to 64 registers (two
+// 512-thread blocks per SM) although that spills: measured on GB300, the
+// doubled occupancy outweighs the spills for the pored-film kernels (steady
+// pored film +7 %, surface pulse +17 %; ~250 bytes of spills per thread) and
+// for the kernels whose tallies go through memory (slab profiles, steady
+// maps), whose registers would otherwise allow one block per SM.  The others
+// keep the compiler's own register choice (naming a minimum of one block
+// changes it for the worse).
 template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 __global__ void __launch_bounds__(512) trace_kernel(const __grid_constant__ KernelArgs args)
 {
     trace_body<R, GEOM, SRC, PROFILE, BATCH, DIFF>(args);
 }
 
-template <typename R, int SRC, bool PROFILE, bool DIFF = false>
-__global__ void __launch_bounds__(512, 2) trace_kernel_porous(const __grid_constant__ KernelArgs args)
+template <typename R, int GEOM, int SRC, bool PROFILE, bool DIFF = false>
+__global__ void __launch_bounds__(512, 2) trace_kernel_2b(const __grid_constant__ KernelArgs args)
 {
-    trace_body<R, LE_MC_GEOM_POROUS, SRC, PROFILE, false, DIFF>(args);
+    trace_body<R, GEOM, SRC, PROFILE, false, DIFF>(args);
+}
+
+// FP32 film kernels of the gradient source (plain and batched), whose two
+// segments per loop iteration want ~90 registers: held to 80 (no spills),
+// which keeps three 256-thread blocks per SM instead of two (measured 2 %
+// faster on the 1e7-particle film than the compiler's choice, and 4 % faster
+// than 64 registers with spills).
+template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
+__global__ void __maxnreg__(80) trace_kernel_r80(const __grid_constant__ KernelArgs args)
+{
+    trace_body<R, GEOM, SRC, PROFILE, BATCH, DIFF>(args);
 }
 
 // The entry point of a configuration.
 template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 constexpr auto trace_entry()
 {
-    if constexpr (GEOM == LE_MC_GEOM_POROUS && !BATCH && sizeof(R) == 4 && !PROFILE)
-        return trace_kernel_porous<R, SRC, PROFILE, DIFF>;
+    if constexpr (sizeof(R) == 4 && !BATCH && (GEOM == LE_MC_GEOM_POROUS || PROFILE))
+        return trace_kernel_2b<R, GEOM, SRC, PROFILE, DIFF>;
+    else if constexpr (sizeof(R) == 4 && GEOM == LE_MC_GEOM_PLANES && SRC == LE_MC_SRC_GRADIENT && !PROFILE)
+        return trace_kernel_r80<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
     else
         return trace_kernel<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
 }
@@ -1291,9 +1465,12 @@ inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_le
     size_t off = table_bytes<R, SRC, PROFILE>(n_modes);
     off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC, BATCH>);
     if (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL) off += (size_t)(threads / 32) * sizeof(SampleJobs<R>);
+    if (PROFILE && GEOM == LE_MC_GEOM_POROUS) off += (size_t)(threads / 32) * sizeof(MapJobs<R>);
+    // prof_len: entries of the FP32 shared-memory slab profile (0 = none);
+    // steady maps and the H_j split are reduced in global memory
+    if (PROFILE && GEOM != LE_MC_GEOM_POROUS && sizeof(R) == 4) off += (size_t)prof_len * sizeof(float);
     off = (off + 7) & ~(size_t)7;
-    off += (size_t)prof_len * sizeof(double);
-    off += (size_t)hj_len * sizeof(double);
+    (void)hj_len;
     if (BATCH && n_instances <= kBatchSmemMax)
         off += (size_t)n_instances * (2 * sizeof(double) + CNT_N * sizeof(unsigned long long));
     return off;

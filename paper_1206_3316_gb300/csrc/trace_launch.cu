@@ -117,9 +117,9 @@ cudaError_t LEMC_NAME(smem_trace)(int geom, int src, bool profile, int n_modes, 
 // Batch mode: PLANES geometry with the WALLS or GRADIENT source.
 cudaError_t LEMC_NAME(batch_attr)(int src, bool diff, int threads, size_t smem, int* per_sm)
 {
-    auto k = src == LE_MC_SRC_WALLS ? trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>
-             : diff                 ? trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>
-                                    : trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>;
+    auto k = src == LE_MC_SRC_WALLS ? trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>()
+             : diff                 ? trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>()
+                                    : trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>();
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
@@ -131,11 +131,11 @@ cudaError_t LEMC_NAME(batch_launch)(const KernelArgs& a, int src, bool diff, int
 {
     if (blocks <= 0) return cudaSuccess;
     if (src == LE_MC_SRC_WALLS)
-        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true><<<blocks, threads, smem, st>>>(a);
+        trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_WALLS, false, true>()<<<blocks, threads, smem, st>>>(a);
     else if (diff)
-        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true><<<blocks, threads, smem, st>>>(a);
+        trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true, true>()<<<blocks, threads, smem, st>>>(a);
     else
-        trace_kernel<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true><<<blocks, threads, smem, st>>>(a);
+        trace_entry<Real, LE_MC_GEOM_PLANES, LE_MC_SRC_GRADIENT, false, true>()<<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -198,7 +198,8 @@ def homogeneity_pvalues(g, o, n_g, n_o, min_expected=5.0):
             ea = np.append(ea[~small], ea[small].sum())
             eb = np.append(eb[~small], eb[small].sum())
         keep = (ea > 0) & (eb > 0)
-        chi2 = ((a - ea) ** 2 / ea + (b - eb) ** 2 / eb)[keep].sum()
+        a, b, ea, eb = a[keep], b[keep], ea[keep], eb[keep]
+        chi2 = ((a - ea) ** 2 / ea + (b - eb) ** 2 / eb).sum()
         out.append(stats.chi2.sf(chi2, max(int(keep.sum()) - 1, 1)))
     return np.array(out)
 
@@ -212,8 +213,11 @@ def test_pulse_fp32_energy_conservation_and_oracle(P, oracle):
     ns = 40
     prob = W.porous_pulse(n_particles=2_000_000, grid=(4, 12, 12), n_samples=ns, sample_dt=25e-12, t_final=1e-9)
     g = P.simulate(prob, record_particles=True)
-    t0 = g["particles_rec"]["t0"]
-    ts = (np.arange(ns) + 0.5) * 25e-12
+    # a particle is counted from the first sample time at or after its
+    # emission; the FP32 kernel compares its FP32 emission time with the FP32
+    # sample times (k + 1/2) dt, so that is the comparison made here
+    t0 = g["particles_rec"]["t0"].astype(np.float32)
+    ts = (np.arange(ns, dtype=np.float32) + np.float32(0.5)) * np.float32(25e-12)
     emitted = np.searchsorted(np.sort(t0), ts, side="right")
     assert np.array_equal(g["grid"].reshape(ns, -1).sum(axis=1), emitted)
     n_o = 1_000_000

@@ -116,7 +116,11 @@ def test_transient_grid_fp32_error(P, kind):
     moved = np.abs(ga - gb).sum() / max(np.abs(ga).sum(), 1)
     print(f"\n{kind} grid: histories differing {_differ(a['particles_rec'], b['particles_rec']):.3f}; "
           f"cell counts moved {moved:.2e}; total variation per sample max {tv.max():.2e}")
-    assert np.array_equal(ga.reshape(ns, -1).sum(axis=1), gb.reshape(ns, -1).sum(axis=1))  # same emission
+    # same emission up to rounding: an emission time within rounding of a
+    # sample time can fall on either side of it in the two precisions
+    dtot = np.abs(ga.reshape(ns, -1).sum(axis=1) - gb.reshape(ns, -1).sum(axis=1))
+    print(f"  sample totals differ by at most {dtot.max()} of {n}")
+    assert dtot.max() <= 10 + 1e-5 * n
     # as if independent (they are positively correlated, so this is loose)
     pv = homogeneity_pvalues(gb, ga, n, n)
     assert pv.min() > 1e-3 / ns
