@@ -521,6 +521,29 @@ def test_porous_full_size_against_bounds_and_oracle(P, oracle, analytic):
     assert _z(g, o, "kappa") < 3.0
 
 
+def test_porous_bias_below_one_per_mille_against_stored_oracle(P):
+    # config-2 steady: the pored-film conductivity of 1e10 FP32 GPU particles
+    # (three independent instances of 3.3e9) against the FP64 oracle's value
+    # for 1.6e9 particles of an independent stream, stored by
+    # tests/golden/make_oracle_values.py.  The per-particle relative standard
+    # deviation is about 10.6, so this is the size at which 3 sigma of the
+    # difference is below 1e-3 of kappa.
+    import json
+    import os
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_values.json")))["porous_film_kappa"]
+    n = 3_333_333_333
+    runs = [P.simulate(W.with_run(W.porous_film(), n_particles=n, instance_id=i), arrays=False) for i in range(3)]
+    for g in runs:
+        assert g["particles"] == n and g["device_flags"] == 0
+    kappa = np.mean([g["kappa"] for g in runs])
+    se = np.sqrt(np.sum([g["kappa_se"] ** 2 for g in runs])) / 3.0
+    sig = np.hypot(se, ref["kappa_se"])
+    print(f"\npored film, 1e10 GPU particles: kappa {kappa:.5f} +- {se:.5f}; oracle (1.6e9) {ref['kappa']:.5f} +- "
+          f"{ref['kappa_se']:.5f}; difference {kappa / ref['kappa'] - 1:+.2e} (3 sigma {3 * sig / ref['kappa']:.1e})")
+    assert 3.0 * sig < 1e-3 * ref["kappa"]
+    assert abs(kappa - ref["kappa"]) < 3.0 * sig
+
+
 def test_pulse_full_size_conserves_every_particle(P, oracle):
     # config-2 transient at full size: with adiabatic walls every particle is
     # counted exactly once at every sample after the pulse has been emitted
