@@ -42,7 +42,7 @@ extern "C" {
 #define LE_MC_API
 #endif
 
-#define LE_MC_ABI_VERSION 4
+#define LE_MC_ABI_VERSION 5
 #define LE_MC_MAX_BRANCHES 4
 #define LE_MC_MAX_MODES 4096        /* mode tables live in shared memory       */
 #define LE_MC_MAX_BINS_X 256        /* slab profile bins                       */
@@ -454,14 +454,22 @@ LE_MC_API le_mc_status le_mc_batch_destroy(le_mc_batch b);
 
 /* ---- serving: continuous batching of simulation requests -------------------
  * Not in the paper.  A worker thread owned by the server admits submitted
- * requests into slots while a slot and device memory are free, traces each
- * request in epochs (le_mc_run over consecutive particle-id ranges) on the
- * slot's own stream so that requests overlap on the GPU, and retires a
- * request once the relative standard error of its primary estimate (kappa
- * for GRADIENT, Psi for WALLS) is at or below its target, or its particle
- * budget is spent.  A request's epoch sizes depend only on its own
+ * requests into slots while a slot and device memory are free.  An admitted
+ * request's parameters, tables and running tallies stay in device memory
+ * until it retires.  Its particles are traced in epochs over consecutive
+ * particle-id ranges; each epoch is published as work items to a ring that
+ * one resident persistent kernel drains, so the particles of every admitted
+ * request (slabs, films, pored films and bulk, each with its own material)
+ * are interleaved inside that kernel.  The kernel leaves on its own after
+ * idle_exit_ms without work and is launched again when work arrives.  A
+ * request retires once the relative standard error of its primary estimate
+ * (kappa for GRADIENT, Psi for WALLS) is at or below its target, or its
+ * particle budget is spent.  A request's epoch sizes depend only on its own
  * statistics, so its particle set, and therefore its result, is the same
- * whether it runs alone or among others (up to FP64 summation order). */
+ * whether it runs alone or among others (up to FP64 summation order).
+ * Served requests: steady WALLS (PLANES) or GRADIENT sources, FP32
+ * trajectories, isotropic relaxation events, black, diffuse or specular
+ * walls and pores, no arrays. */
 typedef struct le_mc_server_s* le_mc_server;
 
 typedef struct {
@@ -471,13 +479,16 @@ typedef struct {
                                     * (0 = half of the free memory at creation)    */
     uint64_t pilot_particles;      /* first epoch of every request (0 = 65536)      */
     uint64_t max_epoch_particles;  /* largest epoch of one request (0 = 2^24)       */
+    int32_t idle_exit_ms;          /* the resident kernel leaves after this long
+                                    * without work, 0..60000 (0 = 250)            */
+    int32_t pad2;
 } le_mc_server_config;
 
 enum { LE_MC_REQ_QUEUED = 0, LE_MC_REQ_RUNNING = 1, LE_MC_REQ_DONE = 2, LE_MC_REQ_FAILED = 3 };
 
 typedef struct {
     int32_t state;                 /* LE_MC_REQ_*                                   */
-    int32_t epochs;                /* le_mc_run calls made for the request          */
+    int32_t epochs;                /* epochs traced for the request                 */
     double submit_s, start_s, done_s; /* server clock, seconds since creation        */
     double rel_err;                /* achieved relative std error of the estimate   */
     le_mc_tallies tallies;         /* over every particle traced for the request    */
@@ -488,6 +499,7 @@ typedef struct {
     uint64_t segments, particles;  /* traced by completed epochs                    */
     uint64_t hbm_in_use;           /* bytes held by admitted requests (estimate)    */
     double uptime_s;
+    uint64_t kernel_launches;      /* launches of the resident kernel so far         */
 } le_mc_server_counters;
 
 /* Starts the worker thread on the current device.  Errors: INVALID, NOMEM, CUDA. */

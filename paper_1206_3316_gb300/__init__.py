@@ -120,8 +120,8 @@ class Server:
     ``n_particles`` is the particle budget; ``poll`` returns its state and,
     once done, its normalised tallies over every particle traced."""
 
-    def __init__(self, max_slots=8, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0):
-        self.h = le_mc_server_create(max_slots, hbm_budget_bytes, pilot_particles, max_epoch_particles)
+    def __init__(self, max_slots=8, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0, idle_exit_ms=0):
+        self.h = le_mc_server_create(max_slots, hbm_budget_bytes, pilot_particles, max_epoch_particles, idle_exit_ms)
 
     def submit(self, problem, target_rel_err):
         return le_mc_server_submit(self.h, material_desc(problem["material"]), geometry_desc(problem["geometry"]),

@@ -98,7 +98,8 @@ class LaunchConfig(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("max_slots", C.c_int32), ("pad", C.c_int32), ("hbm_budget_bytes", C.c_uint64),
-                ("pilot_particles", C.c_uint64), ("max_epoch_particles", C.c_uint64)]
+                ("pilot_particles", C.c_uint64), ("max_epoch_particles", C.c_uint64), ("idle_exit_ms", C.c_int32),
+                ("pad2", C.c_int32)]
 
 
 class RequestStatus(C.Structure):
@@ -108,7 +109,8 @@ class RequestStatus(C.Structure):
 
 class ServerCounters(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "failed", "active", "queued", "segments",
-                                          "particles", "hbm_in_use")] + [("uptime_s", C.c_double)]
+                                          "particles", "hbm_in_use")] + [("uptime_s", C.c_double),
+                                                                         ("kernel_launches", C.c_uint64)]
 
 
 REQUEST_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
@@ -450,10 +452,11 @@ def le_mc_batch_destroy(b):
     _check(lib.le_mc_batch_destroy(b), "le_mc_batch_destroy")
 
 
-def le_mc_server_create(max_slots=0, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0):
+def le_mc_server_create(max_slots=0, hbm_budget_bytes=0, pilot_particles=0, max_epoch_particles=0, idle_exit_ms=0):
     c = ServerConfig()
     c.max_slots, c.hbm_budget_bytes = int(max_slots), int(hbm_budget_bytes)
     c.pilot_particles, c.max_epoch_particles = int(pilot_particles), int(max_epoch_particles)
+    c.idle_exit_ms = int(idle_exit_ms)
     h = _H()
     _check(lib.le_mc_server_create(C.byref(c), C.byref(h)), "le_mc_server_create")
     return h

@@ -30,7 +30,8 @@ SOURCES = [("trace_launch.cu", "trace_f32", ["-DLEMC_PREC_BITS=32"]),
            ("trace_launch.cu", "trace_f64", ["-DLEMC_PREC_BITS=64"]),
            ("le_mc_api.cu", "le_mc_api", []), ("le_mc_batch.cu", "le_mc_batch", []),
            ("le_mc_server.cu", "le_mc_server", []), ("le_mc_noalloc.cu", "le_mc_noalloc", []),
-           ("le_mc_diag.cu", "le_mc_diag", []), ("le_mc_host.cpp", "le_mc_host", [])]
+           ("le_mc_diag.cu", "le_mc_diag", []), ("serve_kernel.cu", "serve_kernel", []),
+           ("le_mc_host.cpp", "le_mc_host", [])]
 
 
 def nvcc():

@@ -745,7 +745,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const int wtype = (kind == HIT_XLO) ? P.wall_lo : P.wall_hi;
             if (wtype == LE_MC_WALL_BLACK && fabsf(d_b - ell) <= 8.0f * 1.1920929e-7f * fmaxf(d_b, ell)) {
                 const double u = (double)M::uniform(r.x);
-                const double ell64 = (double)lam * -log(u);
+                // (a fused table holds Lambda ln 2, the flight is then -(Lambda ln 2) log2 u)
+                const double ell64 = FUSED ? (double)lam * -log2(u) : (double)lam * -log(u);
                 const double d64 = ((ox > 0.0f) ? ((double)Lp - (double)x) : (double)x) / fabs((double)ox);
                 hit = d64 <= ell64;
             }

@@ -1,8 +1,10 @@
-"""GPU tests of the request server (continuous batching).
+"""GPU tests of the request server (continuous batching in one resident
+kernel).
 
 A request's epochs depend only on its own statistics, so the particles it
 traces, and its result, are the same whether it runs alone or among other
-requests: integer counters exactly, FP64 sums up to summation order.
+requests: integer counters exactly, FP64 sums up to summation order.  The
+resident kernel traces the same particles as le_mc_run for the request.
 """
 import numpy as np
 import pytest
@@ -59,6 +61,9 @@ def test_results_same_alone_and_in_mix(P):
         mixed = [srv.poll(i) for i in ids]
         stats = srv.stats()
     assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    # the requests were interleaved inside the resident kernel: submitted
+    # together, they were all traced by one launch of it
+    assert stats["kernel_launches"] == 1, stats
     for (prob, target), a, m in zip(reqs, alone, mixed):
         assert a["state"] == m["state"] == "done"
         for k in INTS:
@@ -67,6 +72,28 @@ def test_results_same_alone_and_in_mix(P):
         key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
         assert m[key] == pytest.approx(a[key], rel=sum_order_rtol(a, prob["run"]["precision"], key))
         assert m["rel_err"] <= target or m["particles"] == prob["run"]["n_particles"]
+
+
+def test_served_results_match_le_mc_run(P):
+    # the resident kernel traces the particles le_mc_run traces for the same
+    # request (same ids, random words, frames and rules, FP32 trajectories):
+    # over the particles a served request used, the two agree in their
+    # counters and estimates up to the rare histories that rounding parts
+    reqs = [r for r in _mix()[:4]]
+    with P.Server(max_slots=4) as srv:
+        ids = [srv.submit(prob, target) for prob, target in reqs]
+        srv.wait_all(300)
+        served = [srv.poll(i) for i in ids]
+    for (prob, target), s in zip(reqs, served):
+        n = int(s["particles"])
+        g = P.simulate(W.with_run(prob, n_particles=n), arrays=False)
+        key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
+        for k in ("segments", "scatters", "wall_hits", "periodic"):
+            assert abs(s[k] - g[k]) <= 1e-3 * max(g[k], 1), (k, s[k], g[k])
+        # (histories parted by rounding are independent samples: with a fraction
+        # f of them the difference has a standard deviation of sqrt(2 f) sigma)
+        assert abs(s[key] - g[key]) < 1.5 * g[key + "_se"], (key, s[key], g[key], g[key + "_se"])
+        assert s["device_flags"] == 0
 
 
 def test_served_film_matches_pin(P, analytic):
@@ -90,11 +117,15 @@ def test_cancel_and_invalid(P):
         srv.wait_all(120)
         assert srv.poll(big)["state"] == "failed"
         assert all(srv.poll(q)["state"] == "failed" for q in queued)
-        ok = srv.submit(W.gray_slab(n_particles=100_000, n_bins=0), 0.05)
+        ok = srv.submit(W.gray_slab(n_particles=100_000, n_bins=0, precision="fp32"), 0.05)
         srv.wait_all(120)
         assert srv.poll(ok)["state"] == "done"
         with pytest.raises(P.LeMcError):
-            srv.submit(W.gray_slab(n_particles=100, n_bins=10), 0.01)  # arrays are not served
+            srv.submit(W.gray_slab(n_particles=100, n_bins=10, precision="fp32"), 0.01)  # arrays are not served
+        with pytest.raises(P.LeMcError):
+            srv.submit(W.gray_slab(n_particles=100, n_bins=0, precision="fp64"), 0.01)  # FP32 trajectories only
+        with pytest.raises(P.LeMcError):
+            srv.submit(W.silicon_film(n_particles=100, specularity=0.5), 0.01)  # partially specular walls
         with pytest.raises(P.LeMcError):
             srv.submit(W.gray_slab(n_particles=100, n_bins=0), 0.0)
         with pytest.raises(P.LeMcError):

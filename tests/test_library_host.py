@@ -43,7 +43,7 @@ def test_struct_layouts(P):
     for i, cls in enumerate((Bd.MaterialDesc, Bd.GeometryDesc, Bd.RunDesc, Bd.Tallies, Bd.Particle)):
         assert P.lib.le_mc_struct_size(i) == ctypes.sizeof(cls)
     assert Bd.PARTICLE_DTYPE.itemsize == ctypes.sizeof(Bd.Particle)
-    assert P.le_mc_abi_version() == 4
+    assert P.le_mc_abi_version() == 5
 
 
 def test_no_device_is_reported_not_faked(P):

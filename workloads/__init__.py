@@ -211,7 +211,8 @@ def batched_films(n_instances=256, seed=2012, n_min=1e4, n_max=1e7, L_min=10e-9,
 def served_stream(duration_s=60.0, rate_hz=50.0, seed=2012, n_min=1e5, n_max=1e8,
                   targets=(0.01, 0.003)):
     """Poisson request stream mixing slab, film and porous-film problems with
-    random sizes, T_eq in [100, 400] K and target relative standard errors."""
+    random sizes, T_eq in [100, 400] K and target relative standard errors
+    (FP32 trajectories with FP64 tallies, as the request server traces them)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     t = 0.0
     reqs = []
@@ -225,7 +226,7 @@ def served_stream(duration_s=60.0, rate_hz=50.0, seed=2012, n_min=1e5, n_max=1e8
         target = float(targets[int(rng.integers(0, len(targets)))])
         if kind == 0:
             kn = float(math.exp(rng.uniform(math.log(0.1), math.log(10.0))))
-            p = gray_slab(n_particles=budget, kn=kn, n_bins=0)
+            p = gray_slab(n_particles=budget, kn=kn, n_bins=0, precision="fp32")
             p["material"]["T_eq"] = T_eq
         elif kind == 1:
             L = float(math.exp(rng.uniform(math.log(10e-9), math.log(100e-6))))
