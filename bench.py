@@ -619,7 +619,7 @@ def main():
         "gpu_launches": launches,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12, "unit": "Tops/s",
                      "frac": achieved / peak_ops, "traffic": traffic,
-                     "kernel": "trace_kernel<float, PLANES, GRADIENT>",
+                     "kernel": "trace_kernel_r80<float, PLANES, GRADIENT, all-diffuse>",
                      "ops_per_segment": OPS_PER_SEGMENT,
                      "peak_basis": f"{sms} SMs x {LANES_PER_SM} lanes x {sm_mhz:.0f} MHz ({peak_src} sm_max_mhz)"},
         "clocks": clocks,

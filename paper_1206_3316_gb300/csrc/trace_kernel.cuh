@@ -1361,11 +1361,13 @@ __global__ void __launch_bounds__(512, 2) trace_kernel_2b(const __grid_constant_
     trace_body<R, GEOM, SRC, PROFILE, false, DIFF>(args);
 }
 
-// FP32 film kernels of the gradient source (plain and batched), whose two
-// segments per loop iteration want ~90 registers: held to 80 (no spills),
-// which keeps three 256-thread blocks per SM instead of two (measured 2 %
-// faster on the 1e7-particle film than the compiler's choice, and 4 % faster
-// than 64 registers with spills).
+// FP32 kernels of the gradient source that trace two flights per loop
+// iteration (films, plain and batched, and the steady pored film), which want
+// ~90 registers, and the pored film's steady maps: held to 80, which keeps
+// three 256-thread blocks per SM instead of two (film: no spills, 2 % faster
+// than the compiler's choice and 4 % faster than 64 registers with spills;
+// pored film: 60 bytes of spills instead of 270 at 64 registers, 3.6 %
+// faster; maps: 4.5 % faster).
 template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 __global__ void __maxnreg__(80) trace_kernel_r80(const __grid_constant__ KernelArgs args)
 {
@@ -1376,10 +1378,11 @@ __global__ void __maxnreg__(80) trace_kernel_r80(const __grid_constant__ KernelA
 template <typename R, int GEOM, int SRC, bool PROFILE, bool BATCH = false, bool DIFF = false>
 constexpr auto trace_entry()
 {
-    if constexpr (sizeof(R) == 4 && !BATCH && (GEOM == LE_MC_GEOM_POROUS || PROFILE))
-        return trace_kernel_2b<R, GEOM, SRC, PROFILE, DIFF>;
-    else if constexpr (sizeof(R) == 4 && GEOM == LE_MC_GEOM_PLANES && SRC == LE_MC_SRC_GRADIENT && !PROFILE)
+    if constexpr (sizeof(R) == 4 && SRC == LE_MC_SRC_GRADIENT && (!PROFILE || GEOM == LE_MC_GEOM_POROUS) &&
+                  (GEOM == LE_MC_GEOM_PLANES || (GEOM == LE_MC_GEOM_POROUS && !BATCH)))
         return trace_kernel_r80<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
+    else if constexpr (sizeof(R) == 4 && !BATCH && (GEOM == LE_MC_GEOM_POROUS || PROFILE))
+        return trace_kernel_2b<R, GEOM, SRC, PROFILE, DIFF>;
     else
         return trace_kernel<R, GEOM, SRC, PROFILE, BATCH, DIFF>;
 }
