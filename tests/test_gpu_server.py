@@ -130,3 +130,31 @@ def test_cancel_and_invalid(P):
             srv.submit(W.gray_slab(n_particles=100, n_bins=0), 0.0)
         with pytest.raises(P.LeMcError):
             srv.poll(10 ** 9)
+
+
+def test_resident_kernel_relaunch_gives_the_same_results(P):
+    # With a 1 ms idle timeout the resident kernel leaves between requests
+    # submitted one after another and is launched again for each; the
+    # results equal those of a server whose kernel stays up (the particle
+    # set of a request does not depend on which launch traces it).
+    import time
+    reqs = _mix()[:4]
+    out = {}
+    for idle_ms in (1, 60000):
+        res = []
+        with P.Server(max_slots=2, idle_exit_ms=idle_ms) as srv:
+            for prob, target in reqs:
+                rid = srv.submit(prob, target)
+                srv.wait_all(300)
+                res.append(srv.poll(rid))
+                time.sleep(0.05)  # longer than the short idle timeout
+            launches = srv.stats()["kernel_launches"]
+        out[idle_ms] = (res, launches)
+    (short, n_short), (long_, n_long) = out[1], out[60000]
+    assert n_long == 1 and n_short >= len(reqs), (n_short, n_long)
+    for (prob, target), a, b in zip(reqs, short, long_):
+        assert a["state"] == b["state"] == "done"
+        for k in INTS:
+            assert a[k] == b[k], k
+        key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
+        assert a[key] == pytest.approx(b[key], rel=sum_order_rtol(b, prob["run"]["precision"], key))
