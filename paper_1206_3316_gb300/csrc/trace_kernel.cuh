@@ -727,11 +727,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         // step III: first boundary along the ray
         R d_b = big;
         int kind = HIT_NONE;
+        R wpos = R(0);  // position of the x wall ahead
         if constexpr (GEOM != LE_MC_GEOM_BULK) {
             // distance to the wall ahead; a flight parallel to the walls gets
             // an infinite (or NaN, never <= ell) distance and no hit
             const bool up = ox > R(0);
-            d_b = M::div(up ? (Lp - x) : x, fabs(ox));
+            wpos = up ? Lp : R(0);
+            d_b = M::div(fabs(wpos - x), fabs(ox));
             kind = up ? HIT_XHI : HIT_XLO;
         }
         if constexpr (POROUS) {
@@ -777,8 +779,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             seg = hit ? d_b : fminf(ell, d_b);  // a relaxation decided in FP64 happens on this side of the wall
         }
         R x_new = x + ox * seg;
-        if (hit && kind == HIT_XLO) x_new = R(0);
-        if (hit && kind == HIT_XHI) x_new = Lp;
+        if (hit && (kind == HIT_XLO || kind == HIT_XHI)) x_new = wpos;
 
         // end time of the segment, computed once: the sample windows [t, t_b)
         // of consecutive segments must tile time exactly (no sample lost or
@@ -1032,8 +1033,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         ox = nox;
         oy = noy;
         oz = noz;
+        // (every segment ends in exactly one of a relaxation event, a wall
+        // and a periodic face, so the wall count is n_seg - n_scat - n_per,
+        // formed when the particle ends)
         n_scat += scat ? 1u : 0u;
-        n_wall += on_wall ? 1u : 0u;
         n_per += periodic ? 1u : 0u;
         if constexpr (HJ) {  // flux split by scattering index
             if (P.n_hj > 0 && scat) {
@@ -1049,7 +1052,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         // collision cap, segment cap) is only worked out when the particle ends
         const bool t_out = TRANSIENT && t > K.t_final;
         const bool s_cap = n_scat >= P.scat_cap;  // scat_cap = max_scatter, or 2^32 - 1 for none
-        const bool c_cap = col_cap && n_scat + n_wall >= P.max_collisions;
+        const bool c_cap = col_cap && n_seg - n_per >= P.max_collisions;  // relaxation events + wall hits
         if (absorbed || t_out || s_cap || c_cap || n_seg >= P.max_events) {
             fate = absorbed ? FATE_ABSORBED
                  : t_out    ? FATE_T_FINAL
@@ -1063,6 +1066,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
 
     // totals of a finished particle (step V, Eq. 4) into the lane accumulators
     auto finish = [&]() {
+        n_wall = n_seg - n_scat - n_per;
         if constexpr (BATCH) {
             if (bidx != cur_b) {
                 flush_lane(cur_b);
@@ -1252,7 +1256,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         t0 = t;
         Lacc = 0;
         hrun = 0;
-        n_seg = n_scat = n_wall = n_per = 0;
+        n_seg = n_scat = n_per = 0;
         alive = true;
     };
 
