@@ -483,12 +483,12 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     }
     fill_consts(P);
 
-    // slab profiles of FP32 kernels: a per-block FP32 copy in shared memory
-    // when it is small enough (steady maps, the H_j split and FP64 profiles
-    // are reduced in global memory)
-    const bool prof_smem = fp32 && profile && !has_map && h->prof_len <= (size_t)kProfSmemMax;
-    P.prof_smem = prof_smem ? 1 : 0;
-    const int smem_prof = prof_smem ? (int)h->prof_len : 0;
+    // slab profiles and steady maps of FP32 kernels: a per-block FP32 copy in
+    // shared memory when it is small enough (the H_j split and FP64 profiles
+    // are reduced in global memory); for maps only where it costs no
+    // resident warps (checked below)
+    bool prof_smem = fp32 && profile && h->prof_len <= (size_t)(has_map ? kMapSmemMax : kProfSmemMax);
+    int smem_prof = prof_smem ? (int)h->prof_len : 0;
     // launch shape: persistent grid of (SMs x resident blocks).  By default
     // 512 threads per block, or 256 when that keeps more warps resident (a
     // kernel instance whose registers leave room for only one 512-thread
@@ -516,6 +516,22 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
             per_sm = per_sm2;
         }
     }
+    if (e == cudaSuccess && prof_smem && has_map) {
+        // the map copy must not lower the resident warps of this shape
+        const int keep = smem_prof;
+        smem_prof = 0;
+        size_t smem0 = 0;
+        int per_sm0 = 0;
+        e = shape_for(threads, &smem0, &per_sm0);
+        if (e == cudaSuccess && per_sm0 > per_sm) {
+            prof_smem = false;
+            smem = smem0;
+            per_sm = per_sm0;
+        } else {
+            smem_prof = keep;
+        }
+    }
+    P.prof_smem = prof_smem ? 1 : 0;
     int sms = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess && per_sm < 1) e = cudaErrorInvalidConfiguration;

@@ -70,10 +70,13 @@ struct Consts {
 
 constexpr int kBatchSmemMax = 512;
 
-// Slab profiles of FP32 kernels: FP32 shared-memory copy of at most this
-// many entries ([4][n_batch][n_bins_x + 1]), each warp draining its share of
-// the entries into the FP64 sums every kProfDrainEvery loop iterations.
+// Slab profiles and steady maps of FP32 kernels: FP32 shared-memory copy of
+// at most kProfSmemMax entries ([4][n_batch][n_bins_x + 1]) or kMapSmemMax
+// entries ([2][n_batch][map_nz][map_ny]; used only where it costs no resident
+// warps), each warp draining its share of the entries into the FP64 sums
+// every kProfDrainEvery loop iterations.
 constexpr int kProfSmemMax = 12288;
+constexpr int kMapSmemMax = 8192;
 constexpr int kProfDrainEvery = 32;
 
 // Extreme particles: emission mean free path above kExtremeFactor times the
@@ -128,9 +131,9 @@ struct TraceParams {
     int32_t n_bins_x, n_batch;
     int32_t map_ny, map_nz;
     double* prof;
-    // FP32 kernels with a slab profile of at most kProfSmemMax entries keep
-    // a per-block FP32 copy in shared memory that their warps drain into
-    // prof (0 = every contribution is reduced into prof directly)
+    // FP32 kernels with a slab profile or steady maps small enough keep a
+    // per-block FP32 copy in shared memory that their warps drain into prof
+    // (0 = every contribution is reduced into prof directly)
     int32_t prof_smem;
     // flux by scattering index: [2][n_hj] (sum s h, sum h^2)
     int32_t n_hj;

@@ -100,16 +100,21 @@ struct SampleJobs {
 };
 
 // Steady-map kernels defer the map cells of a segment in the same way: each
-// lane leaves its segment's start (y, z), the reciprocals of its direction
-// components (0 when a component is 0), its length, its time and z-flux
-// weights per unit length, its first map cell, its counts of map-cell
-// boundaries crossed along y and z and its batch group; the warp then adds
-// the contributions of every crossed cell of every lane, one cell per lane.
+// lane leaves, per map axis, the parameter of its segment's first cell-
+// boundary crossing and the parameter step between crossings (the a-th
+// crossing along y at ty0 + a dty; ty0 = +inf and dty = 0 for a segment
+// parallel to the axis), its length, its time and z-flux weights per unit
+// length, and one word packing its first map cell (j0, k0), its counts of
+// map-cell boundaries crossed along y and z (nyc, nzc; each below the 64
+// cells an axis may have), its batch group g (below 64) and the directions
+// of travel along y and z (negative: bits 30, 31); the warp then adds the
+// contributions of every crossed cell of every lane, one cell per lane.
 template <typename R>
 struct MapJobs {
-    R y[32], z[32], ry[32], rz[32], seg[32], wT[32], wQ[32];
-    int j0[32], k0[32], nyc[32], nzc[32], g[32];
+    R ty0[32], dty[32], tz0[32], dtz[32], seg[32], wT[32], wQ[32];
+    uint32_t pk[32];  // j0 | k0 << 6 | nyc << 12 | nzc << 18 | g << 24 | (sy < 0) << 30 | (sz < 0) << 31
 };
+static_assert(LE_MC_MAX_MAP <= 64 && LE_MC_MAX_BATCH <= 64, "map-job fields are packed in 6 bits each");
 
 // The lane tallies of the steady FP32 pored-film kernel (its two compensated
 // sums and seven counters, touched once per particle) live in shared memory,
@@ -416,10 +421,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     if constexpr (TRANSIENT) off += (size_t)n_warps * sizeof(SampleJobs<R>);
     MapJobs<R>* s_mjobs = reinterpret_cast<MapJobs<R>*>(smem + off);
     if constexpr (PROFILE && POROUS) off += (size_t)n_warps * sizeof(MapJobs<R>);
-    // FP32 slab profile copy of this block (drained into the FP64 sums)
-    constexpr bool PROF32 = PROFILE && !POROUS && sizeof(R) == 4;
+    // FP32 copy of this block's slab profile or steady maps (drained into
+    // the FP64 sums), when the host found room for it
+    constexpr bool PROF32 = PROFILE && sizeof(R) == 4;
     float* s_prof32 = reinterpret_cast<float*>(smem + off);
-    const int prof32_len = (PROF32 && P.prof_smem) ? 4 * P.n_batch * (P.n_bins_x + 1) : 0;
+    const int prof32_len = (PROF32 && P.prof_smem)
+                               ? (POROUS ? 2 * P.n_batch * P.map_ny * P.map_nz : 4 * P.n_batch * (P.n_bins_x + 1))
+                               : 0;
     off += (size_t)prof32_len * sizeof(float);
     off = (off + 7) & ~(size_t)7;
     // batch mode: per-instance sums [n][2] and counters [n][CNT_N] of this block
@@ -519,12 +527,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         atomicAdd(dst, d);
     };
 
-    // Slab profile entry i: into this block's FP32 copy (native shared-memory
-    // adds) when it has one, else straight into the FP64 sums.  Each warp
-    // drains its share of the copy (atomic exchange with 0, then one FP64
-    // reduction per nonzero entry) every kProfDrainEvery loop iterations, so
-    // an FP32 partial sum holds only the few dozen contributions made to its
-    // entry in between; the block drains everything at the end.
+    // Slab profile or map entry i: into this block's FP32 copy (a shared-
+    // memory add, which the hardware carries out as a compare-and-swap loop)
+    // when it has one, else straight into the FP64 sums.  Each warp drains
+    // its share of the copy (atomic exchange with 0, then one FP64 reduction
+    // per nonzero entry) every kProfDrainEvery loop iterations, so an FP32
+    // partial sum holds only the few dozen contributions made to its entry in
+    // between; the block drains everything at the end.
     auto prof_add = [&](size_t i, R v) {
         if (PROF32 && prof32_len > 0) atomicAdd(&s_prof32[i], (float)v);
         else red64(P.prof + i, v);
@@ -657,12 +666,13 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // crossings among the first i in order of parameter (y first on ties),
     // found by a merge-path binary search; the segment spends the parameter
     // interval [latest crossing so far, earliest next crossing or seg] in
-    // it, and adds d wT and d wQ to the cell's FP64 sums of batch group g.
-    auto map_item = [&](R y0, R z0, R ry, R rz, R seg, R wT, R wQ, int j0, int k0, int nyc, int nzc, int g, int i) {
-        const int sy = ry > R(0) ? 1 : -1, sz = rz > R(0) ? 1 : -1;
-        const int uy = ry > R(0) ? 1 : 0, uz = rz > R(0) ? 1 : 0;
-        auto ty = [&](int a) { return ry != R(0) ? ((R)(j0 + sy * a + uy) * K.map_dy - y0) * ry : big; };
-        auto tz = [&](int b) { return rz != R(0) ? ((R)(k0 + sz * b + uz) * K.map_dz - z0) * rz : big; };
+    // it, and adds d wT and d wQ to the cell's sums of batch group g.
+    auto map_item = [&](R ty0, R dty, R tz0, R dtz, R seg, R wT, R wQ, uint32_t pk, int i) {
+        const int j0 = (int)(pk & 63u), k0 = (int)((pk >> 6) & 63u);
+        const int nyc = (int)((pk >> 12) & 63u), nzc = (int)((pk >> 18) & 63u), g = (int)((pk >> 24) & 63u);
+        const int sy = (pk >> 30) & 1u ? -1 : 1, sz = (pk >> 31) ? -1 : 1;
+        auto ty = [&](int a) { return ty0 + (R)a * dty; };
+        auto tz = [&](int b) { return tz0 + (R)b * dtz; };
         int lo = max(0, i - nzc), hi = min(i, nyc);
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -675,12 +685,12 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         const R t_out = fmin(fmin(ty(a), tz(b)), seg);
         const R d = t_out - t_in;
         if (d > R(0)) {
-            const int ny = P.map_ny;
-            const size_t cells = (size_t)ny * P.map_nz;
-            size_t c = (size_t)(k0 + sz * b) * ny + (size_t)(j0 + sy * a);
+            // (entries of [2][n_batch][map_nz][map_ny]: below 2^19)
+            const int ny = P.map_ny, cells = ny * P.map_nz;
+            int c = (k0 + sz * b) * ny + (j0 + sy * a);
             LEMC_GUARD_INDEX(c, cells);
-            red64(P.prof + (size_t)g * cells + c, d * wT);
-            red64(P.prof + ((size_t)P.n_batch + g) * cells + c, d * wQ);
+            prof_add((size_t)(g * cells + c), d * wT);
+            prof_add((size_t)((P.n_batch + g) * cells + c), d * wQ);
         }
     };
     // Add every deferred map cell of the warp (all 32 lanes converged): item
@@ -710,8 +720,8 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             LEMC_GUARD_INDEX(own, 32);
             const int own_excl = __shfl_sync(FULL, excl, own);
             if (j < total)
-                map_item(J.y[own], J.z[own], J.ry[own], J.rz[own], J.seg[own], J.wT[own], J.wQ[own], J.j0[own],
-                         J.k0[own], J.nyc[own], J.nzc[own], J.g[own], j - own_excl);
+                map_item(J.ty0[own], J.dty[own], J.tz0[own], J.dtz[own], J.seg[own], J.wT[own], J.wQ[own], J.pk[own],
+                         j - own_excl);
         }
         __syncwarp();
         mjob_n = 0;
@@ -855,23 +865,27 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const int nzc = map_crossings(z, oz, rz, seg, k0, nz, K.map_dz, K.map_iz);
             const int g = pgroup;
             const R wT = M::div((R)sign, vg), wQ = (R)sign * oz;
+            // crossing parameters: the a-th y boundary crossed lies at
+            // (j0 + sy a + uy) dy, reached at ty0 + a dty
+            const R ty0 = ry != R(0) ? ((R)(j0 + (ry > R(0) ? 1 : 0)) * K.map_dy - y) * ry : big;
+            const R dty = ry != R(0) ? K.map_dy * fabs(ry) : R(0);
+            const R tz0 = rz != R(0) ? ((R)(k0 + (rz > R(0) ? 1 : 0)) * K.map_dz - z) * rz : big;
+            const R dtz = rz != R(0) ? K.map_dz * fabs(rz) : R(0);
+            const uint32_t pk = (uint32_t)j0 | ((uint32_t)k0 << 6) | ((uint32_t)nyc << 12) | ((uint32_t)nzc << 18) |
+                                ((uint32_t)g << 24) | (ry < R(0) ? (1u << 30) : 0u) | (rz < R(0) ? (1u << 31) : 0u);
             if (coop) {
                 mjob_n = 1 + nyc + nzc;
                 MapJobs<R>& J = s_mjobs[threadIdx.x >> 5];
-                J.y[lane] = y;
-                J.z[lane] = z;
-                J.ry[lane] = ry;
-                J.rz[lane] = rz;
+                J.ty0[lane] = ty0;
+                J.dty[lane] = dty;
+                J.tz0[lane] = tz0;
+                J.dtz[lane] = dtz;
                 J.seg[lane] = seg;
                 J.wT[lane] = wT;
                 J.wQ[lane] = wQ;
-                J.j0[lane] = j0;
-                J.k0[lane] = k0;
-                J.nyc[lane] = nyc;
-                J.nzc[lane] = nzc;
-                J.g[lane] = g;
+                J.pk[lane] = pk;
             } else {
-                for (int i = 0; i <= nyc + nzc; ++i) map_item(y, z, ry, rz, seg, wT, wQ, j0, k0, nyc, nzc, g, i);
+                for (int i = 0; i <= nyc + nzc; ++i) map_item(ty0, dty, tz0, dtz, seg, wT, wQ, pk, i);
             }
         }
         if constexpr (PROFILE && !POROUS) {
@@ -1549,9 +1563,9 @@ inline size_t trace_smem_bytes(int n_modes, int threads, int prof_len, int hj_le
     off += (size_t)(threads / 32) * sizeof(BufferOf<R, GEOM, SRC, BATCH>);
     if (SRC == LE_MC_SRC_PULSE || SRC == LE_MC_SRC_INITIAL) off += (size_t)(threads / 32) * sizeof(SampleJobs<R>);
     if (PROFILE && GEOM == LE_MC_GEOM_POROUS) off += (size_t)(threads / 32) * sizeof(MapJobs<R>);
-    // prof_len: entries of the FP32 shared-memory slab profile (0 = none);
-    // steady maps and the H_j split are reduced in global memory
-    if (PROFILE && GEOM != LE_MC_GEOM_POROUS && sizeof(R) == 4) off += (size_t)prof_len * sizeof(float);
+    // prof_len: entries of the FP32 shared-memory copy of the slab profile or
+    // steady maps (0 = none); the H_j split is reduced in global memory
+    if (PROFILE && sizeof(R) == 4) off += (size_t)prof_len * sizeof(float);
     off = (off + 7) & ~(size_t)7;
     (void)hj_len;
     if (BATCH && n_instances <= kBatchSmemMax)
