@@ -648,12 +648,11 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     // sign; a boundary counts when t(a) < seg and the next cell is on the
     // map.  The estimate from the end point is corrected by the exact
     // comparisons (at most one step each way).
-    auto map_crossings = [&](R u, R o, R r, R seg, int c0, int n, R h, R ih) -> int {
+    auto map_crossings = [&](R u, R o, R r, R t0, R dt, R seg, int c0, int n, R ih) -> int {
         if (r == R(0)) return 0;
         const int sg = r > R(0) ? 1 : -1;
-        const int up = r > R(0) ? 1 : 0;
         const int amax = sg > 0 ? n - 1 - c0 : c0;
-        auto t_of = [&](int a) { return ((R)(c0 + sg * a + up) * h - u) * r; };
+        auto t_of = [&](int a) { return t0 + (R)a * dt; };  // as the walk evaluates them
         const R ue = u + o * seg;
         const int ce = min(max((int)M::floor_(ue * ih), 0), n - 1);
         int m = min(max(sg > 0 ? ce - c0 : c0 - ce, 0), amax);
@@ -848,9 +847,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             // over the cell) and s x (z displacement over the cell) to every
             // cell of the (y, z) map that it crosses.  Here only the cell
             // range is found: the first cell, and how many cell boundaries
-            // the segment crosses along y and along z before it ends (each
-            // crossing parameter from its own boundary, so nothing drifts);
-            // the cells themselves are added by map_item, converged across
+            // the segment crosses along y and along z before it ends (the
+            // a-th crossing's parameter is formed directly as t0 + a dt, one
+            // rounding, so nothing drifts, and counted with the same values
+            // the walk uses); the cells are added by map_item, converged across
             // the warp (flush_map_jobs) or, in the assisted rounds, by this
             // lane alone.
             const int ny = P.map_ny, nz = P.map_nz;
@@ -861,16 +861,16 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const int k0 = min(max((int)M::floor_(z * K.map_iz), 0), nz - 1);
             const R ry = oy != R(0) ? M::div(R(1), oy) : R(0);
             const R rz = oz != R(0) ? M::div(R(1), oz) : R(0);
-            const int nyc = map_crossings(y, oy, ry, seg, j0, ny, K.map_dy, K.map_iy);
-            const int nzc = map_crossings(z, oz, rz, seg, k0, nz, K.map_dz, K.map_iz);
-            const int g = pgroup;
-            const R wT = M::div((R)sign, vg), wQ = (R)sign * oz;
             // crossing parameters: the a-th y boundary crossed lies at
             // (j0 + sy a + uy) dy, reached at ty0 + a dty
             const R ty0 = ry != R(0) ? ((R)(j0 + (ry > R(0) ? 1 : 0)) * K.map_dy - y) * ry : big;
             const R dty = ry != R(0) ? K.map_dy * fabs(ry) : R(0);
             const R tz0 = rz != R(0) ? ((R)(k0 + (rz > R(0) ? 1 : 0)) * K.map_dz - z) * rz : big;
             const R dtz = rz != R(0) ? K.map_dz * fabs(rz) : R(0);
+            const int nyc = map_crossings(y, oy, ry, ty0, dty, seg, j0, ny, K.map_iy);
+            const int nzc = map_crossings(z, oz, rz, tz0, dtz, seg, k0, nz, K.map_iz);
+            const int g = pgroup;
+            const R wT = M::div((R)sign, vg), wQ = (R)sign * oz;
             const uint32_t pk = (uint32_t)j0 | ((uint32_t)k0 << 6) | ((uint32_t)nyc << 12) | ((uint32_t)nzc << 18) |
                                 ((uint32_t)g << 24) | (ry < R(0) ? (1u << 30) : 0u) | (rz < R(0) ? (1u << 31) : 0u);
             if (coop) {
