@@ -643,11 +643,12 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
 
     // Map-cell boundaries crossed by a segment of length seg that starts at
     // coordinate u (within the unit cell) in map cell c0 of n, with direction
-    // component o and r = 1 / o (0: parallel): crossing a (a = 0, 1, ...) is at
-    // parameter t(a) = ((c0 + s a + [s > 0]) h - u) r, s the direction's
-    // sign; a boundary counts when t(a) < seg and the next cell is on the
-    // map.  The estimate from the end point is corrected by the exact
-    // comparisons (at most one step each way).
+    // component o and r = 1 / o (0: parallel): crossing a (a = 0, 1, ...),
+    // at coordinate (c0 + s a + [s > 0]) h (s the direction's sign), is
+    // reached at parameter t(a) = t0 + a dt, with t0 = ((c0 + [s > 0]) h -
+    // u) r and dt = h |r|; a boundary counts when t(a) < seg and the next
+    // cell is on the map.  The estimate from the end point is corrected by
+    // the comparisons (at most one step each way).
     auto map_crossings = [&](R u, R o, R r, R t0, R dt, R seg, int c0, int n, R ih) -> int {
         if (r == R(0)) return 0;
         const int sg = r > R(0) ? 1 : -1;

@@ -97,3 +97,20 @@ def test_map_size_limits(P):
     has = big["map_solid"] > 0
     assert np.all(np.isfinite(big["map_T"][has])) and np.all(np.isnan(big["map_T"][~has]))
     assert big["segments"] == g["segments"] and big["device_flags"] == 0
+
+
+def test_fine_map_aggregates_to_coarse(P):
+    # The same particles mapped on 16 x 16 and on 8 x 8 cells: each coarse
+    # cell's sums are the sums over its 2 x 2 fine cells.  With 32 batch
+    # groups the coarse maps (4096 entries) collect in the kernel's FP32
+    # shared-memory copy and the fine ones (16384) go straight to the FP64
+    # sums, so the two accumulation paths are checked against each other.
+    fine = P.simulate(W.porous_film(n_particles=2_000_000, map=(16, 16), n_batch=32))
+    coarse = P.simulate(W.porous_film(n_particles=2_000_000, map=(8, 8), n_batch=32))
+    assert fine["segments"] == coarse["segments"] and fine["device_flags"] == coarse["device_flags"] == 0
+    for k in ("map_T", "map_q"):
+        vf = np.nan_to_num(fine[k] * fine["map_solid"]) * (1.0 / 16) ** 2
+        vc = np.nan_to_num(coarse[k] * coarse["map_solid"]) * (1.0 / 8) ** 2
+        agg = vf.reshape(8, 2, 8, 2).sum(axis=(1, 3))
+        # (FP32 crossing parameters differ by rounding between the two grids)
+        np.testing.assert_allclose(agg, vc, rtol=1e-4, atol=1e-5 * np.abs(vc).max(), err_msg=k)
