@@ -1352,27 +1352,28 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
         if (!alive) continue;
         if constexpr (SRC == LE_MC_SRC_GRADIENT && !(PROFILE && POROUS)) {
             // Kernels of the gradient source (long histories) without deferred
-            // per-warp jobs trace up to four segments per iteration: the
-            // loop's refill test runs a quarter as often, and the random words
-            // of two flights are formed together ahead of them (the counters
-            // are known in advance), two independent Philox chains whose
-            // latencies overlap.  The words of a flight the particle does not
-            // live to take are discarded.  (Two flights per iteration, then
-            // three, then four measured 2.56 -> 2.49 -> 2.40 -> 2.38 ms on the
-            // 1e7-particle film; for the short histories of the walls source
-            // a second flight measured slower.)  Every particle starts at the
-            // top of the loop, so its segment k always runs in copy k mod 4 of
-            // the segment code: which copy traces a segment never depends on
-            // timing.
-            const uint4 r1 = philox_flight(n_seg + 1u, plane, rk);
-            const uint4 r2 = philox_flight(n_seg + 2u, plane, rk);
-            segment(r1, true);
-            if (alive) segment(r2, true);
-            if (alive) {
-                const uint4 r3 = philox_flight(n_seg + 1u, plane, rk);
-                const uint4 r4 = philox_flight(n_seg + 2u, plane, rk);
-                segment(r3, true);
-                if (alive) segment(r4, true);
+            // per-warp jobs trace up to 2 x kFlightPairs segments per
+            // iteration: the loop's refill test runs that much less often, and
+            // the random words of each pair of flights are formed together
+            // ahead of them (the counters are known in advance), two
+            // independent Philox chains whose latencies overlap.  The words of
+            // a flight the particle does not live to take are discarded.
+            // (1e7-particle film, trace kernel: 1, 2, 3, 4, 6, 8, 10, 12
+            // flights per iteration 2.84, 2.56, 2.40, 2.32, 2.25, 2.21, 2.20,
+            // 2.23 ms; the 2e7-particle pored film 13.0 ms at 4 and 8, 12.9
+            // at 6.  For the short histories of the walls source a second
+            // flight measured slower.)  The pairs are unrolled, and
+            // every particle starts at the top of the loop, so its segment k
+            // always runs in copy k mod (2 kFlightPairs) of the segment code:
+            // which copy traces a segment never depends on timing.
+            constexpr int kFlightPairs = POROUS ? 3 : 4;
+#pragma unroll
+            for (int pr = 0; pr < kFlightPairs; ++pr) {
+                if (pr > 0 && !alive) break;
+                const uint4 ra = philox_flight(n_seg + 1u, plane, rk);
+                const uint4 rb = philox_flight(n_seg + 2u, plane, rk);
+                segment(ra, true);
+                if (alive) segment(rb, true);
             }
         } else {
             segment(philox_flight(n_seg + 1u, plane, rk), true);
