@@ -489,6 +489,10 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
     const R L = K.L;
     const R pitch = K.pitch, half = K.half, rad = K.rad, rad2 = K.rad2;
     const R big = M::big();
+    // slab-profile bin width and bins per unit length (kernel-uniform; a bin
+    // index is floor(x / dx), formed as a product)
+    const R prof_dx = (PROFILE && !POROUS && P.n_bins_x > 0) ? L / (R)P.n_bins_x : R(1);
+    const R prof_ib = (PROFILE && !POROUS && P.n_bins_x > 0) ? (R)P.n_bins_x / L : R(1);
     // anisotropic relaxation-event direction law (kernel-uniform)
     const bool aniso = !DIFF && P.aniso != 0;
     const R hg = K.g;
@@ -896,7 +900,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             // [4][n_batch][n_bins_x + 1] (T direct, T difference, q direct, q
             // difference) of FP64 sums, through prof_add
             const int nb = P.n_bins_x;
-            const R dx = L / (R)nb;
+            const R dx = prof_dx;
             const int g = pgroup;
             const size_t stride = (size_t)nb + 1;
             const size_t Td = (0 * (size_t)P.n_batch + g) * stride;
@@ -904,7 +908,7 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             const size_t qd = (2 * (size_t)P.n_batch + g) * stride;
             const size_t qr = (3 * (size_t)P.n_batch + g) * stride;
             const R lo = fmin(x, x_new), hi = fmax(x, x_new);
-            int k0 = (int)M::floor_(lo / dx), k1 = (int)M::floor_(hi / dx);
+            int k0 = (int)M::floor_(lo * prof_ib), k1 = (int)M::floor_(hi * prof_ib);
             // (a wall position rounds at most one bin out)
             LEMC_DEBUG_CHECK(k0 >= -1 && k1 <= nb);
             k0 = min(max(k0, 0), nb - 1);
