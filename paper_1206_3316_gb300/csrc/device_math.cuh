@@ -116,7 +116,9 @@ template <>
 struct DMath<double> {
     static __device__ __forceinline__ double uniform(uint32_t r)
     {
-        return ((double)r + 0.5) * (1.0 / 4294967296.0);
+        // r 2^-32 + 2^-33 in one fused multiply-add: every step is exact,
+        // so the value is (r + 1/2) 2^-32 to the bit
+        return fma((double)r, 1.0 / 4294967296.0, 1.0 / 8589934592.0);
     }
     static __device__ __forceinline__ double neg_log(double u) { return -log(u); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }

@@ -913,30 +913,41 @@ __device__ __forceinline__ void trace_body(const KernelArgs& args)
             LEMC_DEBUG_CHECK(k0 >= -1 && k1 <= nb);
             k0 = min(max(k0, 0), nb - 1);
             k1 = min(max(k1, 0), nb - 1);
-            const R sr = (R)sign;
+            // signed contributions: in FP64 kernels a product by +-1 is a
+            // flip of the sign bit on the integer units (the FP64 pipe is
+            // narrow), bit for bit the same value
+            auto sgn = [&](R v, int s) -> R {
+                if constexpr (sizeof(R) == 8)
+                    return __longlong_as_double(__double_as_longlong(v) ^ (s < 0 ? (long long)(1ull << 63) : 0ll));
+                else
+                    return (R)s * v;
+            };
             if (ox == R(0)) {
-                prof_add(Td + k0, sr * (seg / vg));
-                if constexpr (!AXIS_X) prof_add(qd + k0, sr * (oz * seg));
+                prof_add(Td + k0, sgn(seg / vg, sign));
+                if constexpr (!AXIS_X) prof_add(qd + k0, sgn(oz * seg, sign));
             } else {
                 const R w = R(1) / (vg * fabs(ox));  // time per unit x
-                // displacement along the flux axis per unit x
-                const R qs = AXIS_X ? (ox > R(0) ? R(1) : R(-1)) : M::div(oz, fabs(ox));
+                // displacement along the flux axis per unit x: +-1 for the
+                // walls source (x itself), oz / |ox| for the gradient source
+                const R qs = AXIS_X ? R(1) : M::div(oz, fabs(ox));
+                const int sq = AXIS_X ? (ox > R(0) ? sign : -sign) : sign;
                 if (k0 == k1) {
                     const R len = hi - lo;
-                    prof_add(Td + k0, sr * (len * w));
-                    prof_add(qd + k0, sr * (len * qs));
+                    prof_add(Td + k0, sgn(len * w, sign));
+                    prof_add(qd + k0, sgn(AXIS_X ? len : len * qs, sq));
                 } else {
                     const R la = (R)(k0 + 1) * dx - lo;  // partial first bin
                     const R lb = hi - (R)k1 * dx;        // partial last bin
-                    prof_add(Td + k0, sr * (la * w));
-                    prof_add(qd + k0, sr * (la * qs));
-                    prof_add(Td + k1, sr * (lb * w));
-                    prof_add(qd + k1, sr * (lb * qs));
+                    prof_add(Td + k0, sgn(la * w, sign));
+                    prof_add(qd + k0, sgn(AXIS_X ? la : la * qs, sq));
+                    prof_add(Td + k1, sgn(lb * w, sign));
+                    prof_add(qd + k1, sgn(AXIS_X ? lb : lb * qs, sq));
                     if (k1 > k0 + 1) {  // whole bins k0+1 .. k1-1
-                        prof_add(Tr + k0 + 1, sr * (dx * w));
-                        prof_add(Tr + k1, -sr * (dx * w));
-                        prof_add(qr + k0 + 1, sr * (dx * qs));
-                        prof_add(qr + k1, -sr * (dx * qs));
+                        const R tw = dx * w, qw = AXIS_X ? dx : dx * qs;
+                        prof_add(Tr + k0 + 1, sgn(tw, sign));
+                        prof_add(Tr + k1, sgn(tw, -sign));
+                        prof_add(qr + k0 + 1, sgn(qw, sq));
+                        prof_add(qr + k1, sgn(qw, -sq));
                     }
                 }
             }
