@@ -92,23 +92,29 @@ double rel_error(const Request& q)
 uint64_t next_epoch(const Request& q, uint64_t pilot, uint64_t cap)
 {
     const uint64_t left = q.budget - q.n_done;
-    uint64_t want;
+    // the wish is formed and bounded in double: for a target far below the
+    // error reached (the particles needed scale as the squared ratio) it can
+    // exceed what a 64-bit integer holds, and a conversion of such a value,
+    // or a rounding up that wraps, must not turn it into an empty epoch
+    double want_d;
     if (q.n_done == 0) {
-        want = pilot;
+        want_d = (double)pilot;
     } else {
         const double re = rel_error(q);
         if (!isfinite(re)) {
-            want = q.n_done;
+            want_d = (double)q.n_done;
         } else {
             const double ratio = re / q.target;
             const double total = (double)q.n_done * ratio * ratio * 1.05;
-            want = total > (double)q.n_done ? (uint64_t)ceil(total - (double)q.n_done) : 1;
+            want_d = total > (double)q.n_done ? ceil(total - (double)q.n_done) : 1.0;
         }
     }
+    const uint64_t lim = cap < left ? cap : left;
+    if (!(want_d < (double)lim)) want_d = (double)lim;  // (also catches NaN)
+    uint64_t want = want_d > 1.0 ? (uint64_t)want_d : 1;  // <= lim < 2^32
     const uint64_t quantum = 1ull << 15;
     want = (want + quantum - 1) / quantum * quantum;
-    if (want > cap) want = cap;
-    if (want > left) want = left;
+    if (want > lim) want = lim;
     return want;
 }
 
@@ -120,8 +126,9 @@ uint64_t footprint_of(int n_modes) { return (uint64_t)n_modes * (48 + 16) + 1024
 // Particles per work item.  An item is what one warp traces before it claims
 // again, so it bounds how long a new request's first items can wait: items
 // hold about kItemSegments segments (~1 ms of a warp) by the request's own
-// segments per particle (known after its pilot epoch; 256 particles before
-// that), and an epoch is cut into at least one item per warp so that even
+// segments per particle (known after its pilot epoch; before that, 256
+// particles or one item per warp, whichever is larger), and an epoch is cut
+// into at least one item per warp so that even
 // one request spreads over the GPU; never fewer than kItemMin particles (two
 // per lane: a claim reads the ring in host memory) nor more than kItemMax.
 constexpr double kItemSegments = 1.6e5;
@@ -475,7 +482,12 @@ void le_mc_server_s::run()
                 const double spp = q->counters[CNT_PARTICLES] > 0
                                        ? (double)q->counters[CNT_SEGMENTS] / (double)q->counters[CNT_PARTICLES]
                                        : 0.0;
-                uint64_t item = spp > 0.0 ? (uint64_t)(kItemSegments / spp) : 256;
+                // (before the pilot epoch has measured its segments per
+                // particle: 256 particles, or one item per warp when the epoch
+                // is larger than that, so a large first epoch is not cut
+                // into tens of thousands of claims)
+                uint64_t item = spp > 0.0 ? (uint64_t)(kItemSegments / spp)
+                                          : std::max<uint64_t>(256, q->n_next / warps);
                 item = std::min(item, std::max<uint64_t>(q->n_next / warps, 1));
                 q->item = std::min(kItemMax, std::max(kItemMin, (item + 31) / 32 * 32));
                 q->inflight = true;

@@ -158,3 +158,21 @@ def test_resident_kernel_relaunch_gives_the_same_results(P):
             assert a[k] == b[k], k
         key = "psi" if prob["source"]["kind"] == "walls" else "kappa"
         assert a[key] == pytest.approx(b[key], rel=sum_order_rtol(b, prob["run"]["precision"], key))
+
+
+def test_unreachable_target_runs_to_its_budget(P):
+    # A target far below what the budget can reach: after the pilot epoch the
+    # particles the target asks for exceed what a 64-bit integer holds; the
+    # request must still run in epochs to its budget and finish (its epochs
+    # are bounded in floating point before any conversion).
+    prob = W.silicon_film(n_particles=300_000, thickness=100e-9)
+    with P.Server(max_slots=2) as srv:
+        rid = srv.submit(prob, 1e-12)
+        try:
+            srv.wait_all(120)
+        except P.LeMcError:
+            srv.cancel(rid)  # (so that closing the server does not wait on it)
+            raise
+        r = srv.poll(rid)
+    assert r["state"] == "done" and r["particles"] == 300_000, r
+    assert r["rel_err"] > 1e-12 and r["epochs"] >= 2
