@@ -445,7 +445,7 @@ le_mc_status le_mc_run(le_mc_material m, le_mc_geometry g, const le_mc_run_desc*
     memset(&a, 0, sizeof(a));
     TraceParams& P = a.p;
     const bool fp32 = r.precision == LE_MC_PREC_FP32;
-    MaterialView mv;
+    MaterialView mv{};
     material_view(m, &mv);
     fill_material(P, mv, fp32);
     const le_mc_geometry_desc& G = g->desc;

@@ -172,7 +172,7 @@ le_mc_status le_mc_batch_create(le_mc_material m, int32_t n, const le_mc_geometr
     if (!out) return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "out is null");
     *out = nullptr;
     if (!m || !geoms || !runs || n < 1) return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "null argument or n < 1");
-    MaterialView mv;
+    MaterialView mv{};
     if (!material_view(m, &mv)) return set_error(LE_MC_ERR_INVALID, "le_mc_batch_create", "bad material");
     const char* why = "";
     unsigned long long total = 0;

@@ -99,7 +99,7 @@ le_mc_status le_mc_run_noalloc(le_mc_material m, le_mc_geometry g, const le_mc_r
 {
     if (!m || !g || !desc || !d_sums || !d_counters)
         return set_error(LE_MC_ERR_INVALID, "le_mc_run_noalloc", "null argument");
-    MaterialView mv;
+    MaterialView mv{};
     le_mc_geometry_desc G;
     if (!material_view(m, &mv) || !geometry_view(g, &G))
         return set_error(LE_MC_ERR_INVALID, "le_mc_run_noalloc", "bad handle");

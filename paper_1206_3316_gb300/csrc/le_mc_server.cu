@@ -289,7 +289,7 @@ le_mc_status le_mc_server_s::admit(Request* q)
 {
     le_mc_status st = le_mc_create_material(&q->mdesc, &q->mat);
     if (st != LE_MC_OK) return st;
-    MaterialView mv;
+    MaterialView mv{};
     material_view(q->mat, &mv);
     q->msums = mv.sums;
     // Eq. 2 table: (threshold, alias, Lambda_j ln 2, Lambda_alias ln 2), the
